@@ -1,0 +1,122 @@
+"""Seeded synthetic inputs for the diffusion-absorption solver.
+
+This module generates data only; it holds none of the solver's arithmetic and
+is the one module that both the CUDA path's tests/benchmarks and the CPU oracle
+consume. The paper's own inputs (Monte Carlo tissue volumes, Sec. 2.5.1) are not
+available, so the fields below stand in for them with the shapes and value
+distributions of the workloads that are benchmarked:
+
+* ``grf``: a Gaussian random field on the vertex grid with squared-exponential
+  covariance ``std^2 exp(-r^2 / (2 corr^2))``. The kernel is separable, so the
+  field is drawn exactly as ``std * (Lz x Ly x Lx) xi`` where ``L_d = V sqrt(Lam)``
+  comes from the 1-D covariance matrix of axis d (negative eigenvalues clipped
+  to zero; eigenvalues below 1e-12 of the largest dropped, which changes the
+  field by far less than FP64 rounding of the solver).
+* ``unit_cube``: the small unit-cube case, 33^3 at h = 1/32: D = exp(g), g a GRF
+  with corr 0.2, std 0.5, mean 0; mu constant 0.1; q i.i.d. U[0,1]; the JVP
+  tangent on q is N(0,1); the VJP cotangent is N(0,1).
+* ``tissue``: tissue-like coefficients in mm (Eq. 19): mus' = 1.0 exp(g1),
+  mua = 0.01 exp(g2), g1, g2 GRFs (corr 5 mm, std 0.3), D = 1/(3 (mua + mus')),
+  h = 0.5 mm; q a Gaussian blob (sigma 3 mm, peak 1) centred uniformly at
+  least 3 sigma from the boundary; the cotangent is N(0,1) on a random 10% of
+  interior vertices and 0 elsewhere; the tangent is dq ~ N(0,1),
+  dD = 0.1 D xi1, dmu = 0.1 mu xi2 with xi ~ N(0,1).
+
+Random streams come from ``numpy.random.SeedSequence(seed).spawn`` with one
+child per role, each driving a PCG64 generator, so every role is reproducible
+on its own.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ROLES = ("g1", "g2", "q", "w_mask", "w", "dq", "dD", "dmu")
+
+
+def _rngs(seed: int) -> dict:
+    ss = np.random.SeedSequence(seed)
+    return {name: np.random.Generator(np.random.PCG64(s)) for name, s in zip(ROLES, ss.spawn(len(ROLES)))}
+
+
+def _axis_factor(n: int, h: float, corr: float) -> np.ndarray:
+    x = np.arange(n) * h
+    C = np.exp(-((x[:, None] - x[None, :]) ** 2) / (2.0 * corr * corr))
+    lam, V = np.linalg.eigh(C)
+    lam = np.clip(lam, 0.0, None)
+    keep = lam > 1e-12 * lam.max()
+    return V[:, keep] * np.sqrt(lam[keep])
+
+
+def grf(shape, h: float, corr: float, std: float, rng: np.random.Generator) -> np.ndarray:
+    """Zero-mean SE-covariance Gaussian random field on a (nz, ny, nx) vertex grid."""
+    nz, ny, nx = shape
+    Lz, Ly, Lx = (_axis_factor(n, h, corr) for n in (nz, ny, nx))
+    xi = rng.standard_normal((Lz.shape[1], Ly.shape[1], Lx.shape[1]))
+    t = np.tensordot(xi, Lx, axes=([2], [1]))          # (rz, ry, nx)
+    t = np.tensordot(t, Ly, axes=([1], [1]))           # (rz, nx, ny)
+    t = np.tensordot(t, Lz, axes=([0], [1]))           # (nx, ny, nz)
+    return np.ascontiguousarray(std * t.transpose(2, 1, 0))
+
+
+def interior_mask(shape) -> np.ndarray:
+    m = np.zeros(shape, dtype=bool)
+    m[1:-1, 1:-1, 1:-1] = True
+    return m
+
+
+def unit_cube(n: int = 33, seed: int = 0, shape=None) -> dict:
+    """Unit-cube workload: D = exp(GRF(0.2, 0.5)), mu = 0.1, q ~ U[0,1], h = 1/(n-1)."""
+    shape = tuple(shape) if shape is not None else (n, n, n)
+    h = 1.0 / (max(shape) - 1)
+    r = _rngs(seed)
+    D = np.exp(grf(shape, h, 0.2, 0.5, r["g1"]))
+    mu = np.full(shape, 0.1)
+    q = r["q"].uniform(0.0, 1.0, size=shape)
+    w = r["w"].standard_normal(shape)
+    dq = r["dq"].standard_normal(shape)
+    dD = 0.1 * D * r["dD"].standard_normal(shape)
+    dmu = 0.1 * mu * r["dmu"].standard_normal(shape)
+    return dict(name="unit_cube", shape=shape, h=h, D=D, mu=mu, q=q, w=w, dq=dq, dD=dD, dmu=dmu)
+
+
+def tissue(n: int = 129, seed: int = 0, shape=None, h: float = 0.5) -> dict:
+    """Tissue-like workload in mm (Eq. 19 coefficients), Gaussian-blob source."""
+    shape = tuple(shape) if shape is not None else (n, n, n)
+    r = _rngs(seed)
+    mus = 1.0 * np.exp(grf(shape, h, 5.0, 0.3, r["g1"]))
+    mua = 0.01 * np.exp(grf(shape, h, 5.0, 0.3, r["g2"]))
+    D = 1.0 / (3.0 * (mua + mus))
+    mu = mua
+    sig = 3.0
+    ext = [(s - 1) * h for s in shape]
+    lo = [min(3 * sig, e / 2) for e in ext]
+    c = [r["q"].uniform(l, e - l) for l, e in zip(lo, ext)]   # (z, y, x) centre
+    z, y, x = (np.arange(s) * h for s in shape)
+    q = (np.exp(-((z - c[0]) ** 2) / (2 * sig * sig))[:, None, None]
+         * np.exp(-((y - c[1]) ** 2) / (2 * sig * sig))[None, :, None]
+         * np.exp(-((x - c[2]) ** 2) / (2 * sig * sig))[None, None, :])
+    inner = interior_mask(shape)
+    sel = (r["w_mask"].random(shape) < 0.10) & inner
+    w = np.where(sel, r["w"].standard_normal(shape), 0.0)
+    dq = r["dq"].standard_normal(shape)
+    dD = 0.1 * D * r["dD"].standard_normal(shape)
+    dmu = 0.1 * mu * r["dmu"].standard_normal(shape)
+    return dict(name="tissue", shape=shape, h=h, D=np.ascontiguousarray(D), mu=np.ascontiguousarray(mu),
+                q=np.ascontiguousarray(q), w=w, dq=dq, dD=dD, dmu=dmu)
+
+
+def constant(shape, h: float, D: float = 1.0, mu: float = 0.1) -> dict:
+    """Constant coefficients (used for closed-form checks)."""
+    return dict(shape=tuple(shape), h=h, D=np.full(shape, float(D)), mu=np.full(shape, float(mu)))
+
+
+def sine_mode(shape, p) -> np.ndarray:
+    """prod_d sin(p_d pi x_d) with x_d = i_d / (n_d - 1); zero on the boundary."""
+    nz, ny, nx = shape
+    pz, py, px = p
+    z = np.sin(pz * np.pi * np.arange(nz) / (nz - 1))
+    y = np.sin(py * np.pi * np.arange(ny) / (ny - 1))
+    x = np.sin(px * np.pi * np.arange(nx) / (nx - 1))
+    s = z[:, None, None] * y[None, :, None] * x[None, None, :]
+    s[0], s[-1], s[:, 0], s[:, -1], s[:, :, 0], s[:, :, -1] = 0, 0, 0, 0, 0, 0
+    return s
