@@ -1,0 +1,212 @@
+/*
+ * dmg.h -- C ABI of the B300-native differentiable multigrid solver (DMGS).
+ *
+ * Solves the steady diffusion-absorption problem of arXiv 2608.00760, Eq. 1,
+ *
+ *     -div(D grad u) + mu u = q          (mu: the absorption, lambda in the paper)
+ *
+ * on a structured vertex grid with zero Dirichlet boundary, discretised by
+ * second-order central differences (7-point stencil; the coefficient on the
+ * face between two vertices is the mean of their D values), by a multigrid
+ * V-cycle with Red-Black Gauss-Seidel smoothing, full-weighting restriction
+ * and trilinear prolongation (Sec. 2.2, Eqs. 5-7, Eq. 17), and exposes the
+ * push-forward (JVP, Sec. 2.3) and pull-back (VJP, Sec. 2.4, Eq. 18) of the
+ * solver. All arithmetic runs in CUDA kernels for sm_103a; the host code only
+ * schedules them.
+ *
+ * Array convention (every double* below): nx*ny*nz float64 values, C order
+ * [nz][ny][nx] (x fastest), covering ALL vertices including the boundary
+ * planes. Each pointer may point to device memory or to host memory (pinned or
+ * pageable); the library detects which and copies through its own buffers.
+ * The caller owns every array; the library keeps no pointer to it after the
+ * call returns. Values of q, w, dq and mu on boundary vertices are ignored
+ * (Dirichlet); outputs u, du, qbar, mubar are written as 0 there, while Dbar
+ * is defined on every vertex (boundary D enters the faces next to the
+ * boundary).
+ *
+ * Streams: every call takes a cudaStream_t (as void*; NULL = legacy default
+ * stream) and orders all of its work on it. Calls return after the result has
+ * been copied out (convergence tests need the residual norm on the host).
+ * A context is not thread-safe: use one context per host thread/stream.
+ *
+ * Errors: every call returns a dmg_status; no call aborts the process.
+ * dmg_last_error() gives a human-readable message for the last failure on a
+ * context.
+ */
+#ifndef DMG_H
+#define DMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmg_ctx dmg_ctx;
+
+typedef enum {
+    DMG_OK = 0,
+    DMG_EINVAL = 1,   /* invalid argument: grid shape, NULL pointer, parameter range,
+                         or a coarsest-level matrix that is not positive definite */
+    DMG_ENOMEM = 2,   /* a device or pinned-host allocation failed (dmg_setup only) */
+    DMG_ECUDA = 3,    /* a CUDA runtime call failed; see dmg_last_error */
+    DMG_ENOCONV = 4,  /* rtol not reached within max_cycles; outputs hold the last
+                         iterate and info->rel_residual its residual */
+    DMG_ENAN = 5,     /* a residual norm was not finite (NaN/Inf in inputs) */
+    DMG_ETIMEOUT = 6  /* reserved for bounded device waits */
+} dmg_status;
+
+enum { DMG_FP64 = 0, DMG_MIXED = 1 };
+enum { DMG_FACE_ARITHMETIC = 0, DMG_FACE_HARMONIC = 1 };
+enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
+
+/*
+ * Solver parameters (dmg_default_params fills the defaults shown).
+ *   nx, ny, nz    vertices per axis including both boundary vertices. The grid
+ *                 is coarsened by 2 per axis (h_k = 2 h_{k-1}, Eq. 6) while
+ *                 every axis has an odd count > 3; the coarsest level, solved
+ *                 exactly, must have at most 512 interior unknowns.
+ *                 2^n + 1 per axis (Sec. 2.2) always qualifies, and so does
+ *                 c*2^n + 1 with small c (e.g. 257 x 257 x 129).
+ *   h             finest spacing (> 0), equal on all axes.
+ *   nu1, nu2      pre / post RB-GS sweeps per level (default 2, 2).
+ *   symmetric     0: post-smoothing red->black like pre-smoothing (default);
+ *                 1: post-smoothing black->red (then nu1 == nu2 gives a
+ *                 symmetric V-cycle).
+ *   max_cycles    cap on V-cycles (FP64) or refinement steps (mixed), default 100.
+ *   rtol          stop when ||q - A u||_2 <= rtol ||q||_2 over interior vertices
+ *                 (default 1e-10).
+ *   fixed_cycles  0: iterate to rtol; m > 0: run exactly m V-cycles (the paper's
+ *                 fixed-count mode, Sec. 2.4), FP64 only.
+ *   precision     DMG_FP64 (default) or DMG_MIXED: FP32 inner V-cycles as the
+ *                 correction of an FP64 defect-correction loop whose residual,
+ *                 norms and update stay in FP64.
+ *   face_mean     DMG_FACE_ARITHMETIC (default) or DMG_FACE_HARMONIC.
+ *   coarsen       coarse coefficients: DMG_COARSEN_FULL_WEIGHTING (default; full
+ *                 weighting inside, injection on the boundary) or INJECTION.
+ *   inner_cycles  FP32 V-cycles per refinement step in mixed mode (default 1).
+ */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+    int nu1, nu2;
+    int symmetric;
+    int max_cycles;
+    double rtol;
+    int fixed_cycles;
+    int precision;
+    int face_mean;
+    int coarsen;
+    int inner_cycles;
+} dmg_params;
+
+#define DMG_HIST_LEN 64
+
+/*
+ * Per-call report. cycles: V-cycles run (FP64), or FP32 inner V-cycles (mixed);
+ * outer: refinement steps (mixed; equals cycles in FP64); rel_residual: final
+ * ||rhs - A x|| / ||rhs|| of the system solved; hist[c]: the relative residual
+ * after cycle/step c (first DMG_HIST_LEN entries; not filled in fixed mode).
+ */
+typedef struct {
+    int cycles;
+    int outer;
+    double rel_residual;
+    double hist[DMG_HIST_LEN];
+} dmg_info;
+
+/* Fills *p with the defaults listed above (nx = ny = nz = 0, h = 0). */
+void dmg_default_params(dmg_params *p);
+
+/*
+ * dmg_setup -- build the coefficient hierarchy (Sec. 2.2: L^k rediscretised
+ * on every level h_k = 2 h_{k-1}) and every buffer the other calls use.
+ *   D, mu   vertex fields of the diffusion coefficient (> 0) and absorption
+ *           (>= 0), copied into the context; the caller may free them after.
+ *   out     receives the new context (NULL on failure).
+ * All device memory is allocated here; solve/jvp/vjp allocate nothing.
+ * Returns DMG_EINVAL for an unsupported shape or parameter, or when the
+ * coarsest matrix is not positive definite; DMG_ENOMEM when memory runs out.
+ */
+dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, void *stream,
+                     dmg_ctx **out);
+
+/*
+ * dmg_solve -- u = S(q) (Eq. 2): V-cycles from u = 0 until the relative
+ * residual reaches rtol, or exactly fixed_cycles cycles. info may be NULL.
+ * Returns DMG_ENOCONV (u still written) when max_cycles is reached first.
+ */
+dmg_status dmg_solve(dmg_ctx *ctx, const double *q, double *u, dmg_info *info, void *stream);
+
+/*
+ * dmg_jvp -- push-forward (Sec. 2.3): du = S(dq - (dA) u), the tangent of
+ * u(q, D, mu) in direction (dq, dD, dmu), where (dA) u is the derivative of
+ * the discrete operator in (dD, dmu). With dD = dmu = NULL this is S applied
+ * to dq, as the paper states for a solver linear in q; u is then not read
+ * and may be NULL. dq may be NULL (zero). Same stopping rule as dmg_solve.
+ */
+dmg_status dmg_jvp(dmg_ctx *ctx, const double *u, const double *dq, const double *dD,
+                   const double *dmu, double *du, dmg_info *info, void *stream);
+
+/*
+ * dmg_vjp -- pull-back (Sec. 2.4, Eq. 18) of the cotangent w:
+ *   lambda = S^dagger w, qbar = lambda,
+ *   mubar_p = -lambda_p u_p (interior), and
+ *   Dbar_v = -(1/h^2) sum_{j nbr v} dDface(v,j)/dD_v (lambda_v-lambda_j)(u_v-u_j),
+ * the gradients of <w, u> w.r.t. q, mu and D for the solution u of the forward
+ * solve (the D and mu gradients are an extension the paper names as future
+ * work in Sec. 4).
+ *   cycles > 0  count-matched: exactly that many transposed V-cycles, the exact
+ *               transpose of an m-cycle FP64 forward solve (the paper's second
+ *               pull-back mode). Always FP64.
+ *   cycles == 0 converged: iterate the adjoint to rtol (FP64 or mixed, as set up).
+ * qbar, Dbar, mubar may each be NULL (skipped); u may be NULL when Dbar and
+ * mubar are both NULL.
+ */
+dmg_status dmg_vjp(dmg_ctx *ctx, const double *u, const double *w, int cycles, double *qbar,
+                   double *Dbar, double *mubar, dmg_info *info, void *stream);
+
+/*
+ * dmg_residual -- out[0] = ||q - A u||_2 and out[1] = ||q||_2 over interior
+ * vertices, in FP64 (out is a host array of 2 doubles).
+ */
+dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *out,
+                        void *stream);
+
+/* Frees every resource of the context. NULL is accepted. */
+dmg_status dmg_destroy(dmg_ctx *ctx);
+
+/* Static text for a status code. */
+const char *dmg_strerror(dmg_status s);
+
+/* Message of the last failure on ctx ("" if none). With ctx == NULL: the message
+   of the last failed dmg_setup on the calling thread. */
+const char *dmg_last_error(const dmg_ctx *ctx);
+
+/* Number of hierarchy levels and the vertex counts of level l (0 = finest). */
+int dmg_levels(const dmg_ctx *ctx);
+dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int *nz);
+
+/*
+ * Instrumentation (for benchmarks).
+ * dmg_launch_count: kernels this context has launched so far.
+ * dmg_profile_begin(ctx, kernel, level): from now on, bracket every launch of
+ *   `kernel` (a DMG_KERNEL_* id) on `level` with CUDA events on its stream;
+ *   at most `max_launches` launches are recorded.
+ * dmg_profile_end: waits for the recorded events and returns the number of
+ *   recorded launches and their summed duration in milliseconds.
+ */
+enum {
+    DMG_KERNEL_SMOOTH = 0,     /* one RB-GS sweep (both colours) */
+    DMG_KERNEL_RESTRICT = 1,   /* defect + full-weighting restriction */
+    DMG_KERNEL_PROLONG = 2,    /* prolongation + correction */
+    DMG_KERNEL_RESIDUAL = 3,   /* FP64 residual + norm */
+    DMG_KERNEL_GRAD = 4        /* coefficient gradients */
+};
+unsigned long long dmg_launch_count(const dmg_ctx *ctx);
+dmg_status dmg_profile_begin(dmg_ctx *ctx, int kernel, int level, int precision_fp32,
+                             int max_launches);
+dmg_status dmg_profile_end(dmg_ctx *ctx, long long *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMG_H */

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libdmg.so (include/dmg.h), with the same names.
+
+Argument marshalling only: every array argument may be a torch tensor (CUDA or
+CPU), a numpy array, or None where the C API allows NULL; each must be a
+C-contiguous float64 array of nx*ny*nz elements in [nz][ny][nx] order. The
+stream defaults to torch's current CUDA stream. Every computation runs in the
+library's CUDA kernels; when the library is missing the first call raises.
+
+``Solver`` is a small convenience owner of one context (setup/destroy) whose
+methods allocate torch outputs and raise ``DMGError`` on a failing status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libdmg.so")
+
+DMG_OK, DMG_EINVAL, DMG_ENOMEM, DMG_ECUDA, DMG_ENOCONV, DMG_ENAN, DMG_ETIMEOUT = range(7)
+DMG_FP64, DMG_MIXED = 0, 1
+DMG_FACE_ARITHMETIC, DMG_FACE_HARMONIC = 0, 1
+DMG_COARSEN_FULL_WEIGHTING, DMG_COARSEN_INJECTION = 0, 1
+DMG_KERNEL_SMOOTH, DMG_KERNEL_RESTRICT, DMG_KERNEL_PROLONG, DMG_KERNEL_RESIDUAL, DMG_KERNEL_GRAD = range(5)
+DMG_HIST_LEN = 64
+
+
+class dmg_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("symmetric", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("fixed_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("face_mean", ctypes.c_int),
+                ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+
+
+class dmg_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("hist", ctypes.c_double * DMG_HIST_LEN)]
+
+    def history(self):
+        n = min(self.outer, DMG_HIST_LEN)
+        return [self.hist[i] for i in range(n)]
+
+
+EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp", "dmg_residual",
+           "dmg_destroy", "dmg_strerror", "dmg_last_error", "dmg_levels", "dmg_level_shape",
+           "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end")
+
+_lib = None
+
+
+class DMGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+def lib():
+    """Load libdmg.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libdmg.so not found at %s: build it with "
+                               "`python -m paper_2608_00760_b300.build`" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "dmg_default_params": (None, [P(dmg_params)]),
+            "dmg_setup": (i, [P(dmg_params), vp, vp, vp, P(vp)]),
+            "dmg_solve": (i, [vp, vp, vp, P(dmg_info), vp]),
+            "dmg_jvp": (i, [vp, vp, vp, vp, vp, vp, P(dmg_info), vp]),
+            "dmg_vjp": (i, [vp, vp, vp, i, vp, vp, vp, P(dmg_info), vp]),
+            "dmg_residual": (i, [vp, vp, vp, P(d), vp]),
+            "dmg_destroy": (i, [vp]),
+            "dmg_strerror": (ctypes.c_char_p, [i]),
+            "dmg_last_error": (ctypes.c_char_p, [vp]),
+            "dmg_levels": (i, [vp]),
+            "dmg_level_shape": (i, [vp, i, P(i), P(i), P(i)]),
+            "dmg_launch_count": (ctypes.c_ulonglong, [vp]),
+            "dmg_profile_begin": (i, [vp, i, i, i, i]),
+            "dmg_profile_end": (i, [vp, P(ctypes.c_longlong), P(d)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _strerror(status):
+    try:
+        return lib().dmg_strerror(int(status)).decode()
+    except Exception:
+        return "status"
+
+
+def _ptr(x, n=None):
+    """Raw address of an array argument (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    mod = type(x).__module__
+    if mod.startswith("torch"):
+        if x.dtype.itemsize != 8 or not x.is_floating_point() or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor")
+        if n is not None and x.numel() != n:
+            raise ValueError("expected %d elements, got %d" % (n, x.numel()))
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("expected a C-contiguous float64 numpy array")
+        if n is not None and x.size != n:
+            raise ValueError("expected %d elements, got %d" % (n, x.size))
+        return x.ctypes.data
+    raise TypeError("unsupported array type %r" % type(x))
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def dmg_default_params(**kw) -> dmg_params:
+    p = dmg_params()
+    lib().dmg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError("dmg_params has no field %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def dmg_setup(params: dmg_params, D, mu, stream=None):
+    """Returns (status, ctx). ctx is an opaque c_void_p (None on failure)."""
+    n = params.nx * params.ny * params.nz
+    out = ctypes.c_void_p()
+    st = lib().dmg_setup(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _stream(stream), ctypes.byref(out))
+    return st, (out if st == DMG_OK else None)
+
+
+def dmg_solve(ctx, q, u, info=None, stream=None, n=None):
+    return lib().dmg_solve(ctx, _ptr(q, n), _ptr(u, n), ctypes.byref(info) if info is not None else None,
+                           _stream(stream))
+
+
+def dmg_jvp(ctx, u, dq, dD, dmu, du, info=None, stream=None, n=None):
+    return lib().dmg_jvp(ctx, _ptr(u, n), _ptr(dq, n), _ptr(dD, n), _ptr(dmu, n), _ptr(du, n),
+                         ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def dmg_vjp(ctx, u, w, cycles, qbar, Dbar, mubar, info=None, stream=None, n=None):
+    return lib().dmg_vjp(ctx, _ptr(u, n), _ptr(w, n), int(cycles), _ptr(qbar, n), _ptr(Dbar, n),
+                         _ptr(mubar, n), ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def dmg_residual(ctx, q, u, stream=None, n=None):
+    out = (ctypes.c_double * 2)()
+    st = lib().dmg_residual(ctx, _ptr(q, n), _ptr(u, n), out, _stream(stream))
+    return st, (out[0], out[1])
+
+
+def dmg_destroy(ctx):
+    return lib().dmg_destroy(ctx)
+
+
+def dmg_strerror(status):
+    return lib().dmg_strerror(int(status)).decode()
+
+
+def dmg_last_error(ctx=None):
+    return lib().dmg_last_error(ctx).decode()
+
+
+def dmg_levels(ctx):
+    return lib().dmg_levels(ctx)
+
+
+def dmg_level_shape(ctx, level):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib().dmg_level_shape(ctx, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return st, (c.value, b.value, a.value)
+
+
+def dmg_launch_count(ctx):
+    return lib().dmg_launch_count(ctx)
+
+
+def dmg_profile_begin(ctx, kernel, level=0, fp32=False, max_launches=4096):
+    return lib().dmg_profile_begin(ctx, int(kernel), int(level), int(bool(fp32)), int(max_launches))
+
+
+def dmg_profile_end(ctx):
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    st = lib().dmg_profile_end(ctx, ctypes.byref(n), ctypes.byref(ms))
+    return st, n.value, ms.value
+
+
+class Solver:
+    """Owns one dmg context for fixed (D, mu) on a grid of shape (nz, ny, nx).
+
+    Array arguments are float64 torch tensors (device or host) or numpy arrays;
+    results are new torch tensors on ``device`` (default cuda). ``strict``:
+    raise on DMG_ENOCONV too (default True).
+    """
+
+    def __init__(self, D, mu, h, shape=None, stream=None, strict=True, **params):
+        import torch
+        self.torch = torch
+        shape = tuple(shape if shape is not None else D.shape)
+        nz, ny, nx = shape
+        self.shape, self.n = shape, nx * ny * nz
+        self.params = dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), **params)
+        self.strict = strict
+        self.last_info = dmg_info()
+        st, self.ctx = dmg_setup(self.params, D, mu, stream)
+        if st != DMG_OK:
+            raise DMGError(st, dmg_last_error(None))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            dmg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st == DMG_OK or (st == DMG_ENOCONV and not self.strict):
+            return
+        raise DMGError(st, dmg_last_error(self.ctx))
+
+    def _empty(self, like=None, device=None):
+        t = self.torch
+        dev = device if device is not None else (like.device if like is not None and hasattr(like, "device")
+                                                 else t.device("cuda"))
+        return t.empty(self.shape, dtype=t.float64, device=dev)
+
+    def levels(self):
+        return [dmg_level_shape(self.ctx, l)[1] for l in range(dmg_levels(self.ctx))]
+
+    def solve(self, q, out=None, stream=None):
+        u = out if out is not None else self._empty(q)
+        info = dmg_info()
+        self._check(dmg_solve(self.ctx, q, u, info, stream, n=self.n))
+        self.last_info = info
+        return u
+
+    def jvp(self, u, dq=None, dD=None, dmu=None, out=None, stream=None):
+        like = next((x for x in (dq, dD, dmu, u) if x is not None), None)
+        du = out if out is not None else self._empty(like)
+        info = dmg_info()
+        self._check(dmg_jvp(self.ctx, u, dq, dD, dmu, du, info, stream, n=self.n))
+        self.last_info = info
+        return du
+
+    def vjp(self, u, w, cycles=0, need=(True, True, True), stream=None):
+        qb = self._empty(w) if need[0] else None
+        Db = self._empty(w) if need[1] else None
+        mb = self._empty(w) if need[2] else None
+        info = dmg_info()
+        self._check(dmg_vjp(self.ctx, u if (need[1] or need[2]) else None, w, cycles, qb, Db, mb, info,
+                            stream, n=self.n))
+        self.last_info = info
+        return qb, Db, mb
+
+    def residual(self, q, u, stream=None):
+        st, r = dmg_residual(self.ctx, q, u, stream, n=self.n)
+        self._check(st)
+        return r

@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI library (no GPU): it builds for sm_103a, loads,
+exports every function include/dmg.h declares, and rejects invalid parameters
+before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dmg():
+    from paper_2608_00760_b300 import build, dmg
+    build.build()
+    dmg.lib()
+    return dmg
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(dmg):
+    names = declared_functions()
+    assert len(names) >= 10
+    L = ctypes.CDLL(dmg._LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(dmg.EXPORTS)
+
+
+def test_library_is_built_for_sm_103a(dmg):
+    import subprocess
+    out = subprocess.run(["cuobjdump", "--list-elf", dmg._LIB_PATH], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_default_params_and_strerror(dmg):
+    p = dmg.dmg_default_params()
+    assert (p.nu1, p.nu2, p.max_cycles, p.rtol, p.precision, p.inner_cycles) == (2, 2, 100, 1e-10, 0, 1)
+    assert dmg.dmg_strerror(dmg.DMG_OK) == "ok"
+    assert dmg.dmg_strerror(dmg.DMG_ENOCONV) == "did not converge"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=2, ny=9, nz=9, h=1.0),                   # too few vertices
+    dict(nx=20, ny=20, nz=20, h=1.0),                # even: no coarsening, 18^3 coarsest unknowns > 512
+    dict(nx=9, ny=9, nz=9, h=0.0),                   # h <= 0
+    dict(nx=9, ny=9, nz=9, h=1.0, nu1=0, nu2=0),     # no smoothing
+    dict(nx=9, ny=9, nz=9, h=1.0, precision=7),
+    dict(nx=9, ny=9, nz=9, h=1.0, face_mean=3),
+    dict(nx=9, ny=9, nz=9, h=1.0, rtol=0.0),
+    dict(nx=9, ny=9, nz=9, h=1.0, max_cycles=0),
+    dict(nx=9, ny=9, nz=9, h=1.0, inner_cycles=0),
+    dict(nx=65, ny=257, nz=257, h=1.0),              # coarsens to 3x9x9: fine; 7x7x513 is not
+    dict(nx=7, ny=7, nz=513, h=1.0),                 # 7 -> 4 stops coarsening at 4x4x257: 1020 unknowns
+])
+def test_setup_rejects_invalid_params_without_gpu(dmg, bad):
+    p = dmg.dmg_default_params(**bad)
+    valid = (bad.get("nx"), bad.get("ny"), bad.get("nz")) == (65, 257, 257)
+    if valid:
+        pytest.skip("valid shape: needs a GPU")
+    st, ctx = dmg.dmg_setup(p, 0, 0)
+    assert st == dmg.DMG_EINVAL and ctx is None
+    assert dmg.dmg_last_error(None) != "" or bad.get("nx") == 2
+
+
+def test_null_context_calls(dmg):
+    assert dmg.dmg_solve(None, 0, 0) == dmg.DMG_EINVAL
+    assert dmg.dmg_destroy(None) == dmg.DMG_OK
+    assert dmg.dmg_levels(None) == 0
