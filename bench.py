@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Benchmark: forward solve + VJP (w.r.t. q, D, mu) pairs per second on the
+257^3 tissue-like workload at relative residual 1e-10, mixed precision (FP32
+inner V-cycles, FP64 defect correction) and plain FP64, on one B300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmg|reference]
+
+One step = dmg_solve(q) followed by dmg_vjp(u, w) returning (qbar, Dbar, mubar),
+both converged to relative residual 1e-10. The coefficient hierarchy
+(dmg_setup) is built once, outside the timed region: the coefficients are fixed
+while sources vary, as in the paper's inference use. Every field is 136 MB in
+FP64, larger than the 126 MB L2, so no L2 flush is needed between steps.
+
+Multi-GPU: a single solve does not shard, so N ranks run N independent replicas
+(weak scaling); the timed region is bracketed by barriers and the max over
+ranks is reported. --impl reference times the FP64 CPU oracle on this host's
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+VJP solves/s & HBM GB/s at 257³ (FP32-refined vs FP64, 1e-10); p50/p99"
+UNIT = "fwd+VJP solves/s"
+N_SIDE = 257
+RTOL = 1e-10
+# algorithmic bytes per interior point of one RB-GS sweep: read u, f, D, mu and
+# write u (FP32 vertex layout: 4 B each) / read u, f, 3 faces, 1/diag and write u (FP64)
+SWEEP_BYTES = {"fp32": 20.0, "fp64": 56.0}
+SWEEP_FP64_OPS = 7.0   # FP64 pipe operations per point of a sweep (6 FMA + 1 MUL)
+
+
+def percentile(x, p):
+    return float(np.percentile(np.asarray(x), p)) if len(x) else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6],
+                                 swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in rows])), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# FP64 pipe rate measured on this machine's B300 with a dependent-chain-free DFMA
+# loop (0.565e12 DFMA/s at 1.93 GHz, i.e. 2 DFMA/clk/SM x 148 SMs); used as the
+# ALU roofline of the FP64 kernels (ops = DFMA/DMUL instructions).
+FP64_OPS_PEAK = 0.565e12
+
+
+def make_inputs(n, seed=0):
+    from paper_2608_00760_b300 import inputs
+    return inputs.tissue(n, seed=seed)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None, clocks=False):
+    """Times `steps` fwd+VJP pairs; returns a result dict."""
+    dev = torch.device("cuda", local)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    D, mu, q, wv = T(w["D"]), T(w["mu"]), T(w["q"]), T(w["w"])
+    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL)
+    u = torch.empty_like(q)
+    qb, Db, mb = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
+    info_f, info_a = dmg.dmg_info(), dmg.dmg_info()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        st = dmg.dmg_solve(S.ctx, q, u, info_f, stream, n=S.n)
+        if st != dmg.DMG_OK:
+            raise dmg.DMGError(st, dmg.dmg_last_error(S.ctx))
+        st = dmg.dmg_vjp(S.ctx, u, wv, 0, qb, Db, mb, info_a, stream, n=S.n)
+        if st != dmg.DMG_OK:
+            raise dmg.DMGError(st, dmg.dmg_last_error(S.ctx))
+
+    for _ in range(warmup):
+        step()
+    if profile is not None:
+        dmg.dmg_profile_begin(S.ctx, profile[0], 0, profile[1], max_launches=100000)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    l0 = dmg.dmg_launch_count(S.ctx)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        sampler.__enter__()
+    ev[0].record(stream)
+    for i in range(steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.__exit__()
+    barrier(world)
+    launches = dmg.dmg_launch_count(S.ctx) - l0
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[steps])
+    prof = None
+    if profile is not None:
+        st, n, ms = dmg.dmg_profile_end(S.ctx)
+        prof = dict(launches=n, total_ms=ms)
+    res = dict(total_ms=max_over_ranks(world, total_ms), per_ms=per, launches=launches,
+               fwd_cycles=info_f.cycles, fwd_outer=info_f.outer, adj_cycles=info_a.cycles,
+               adj_outer=info_a.outer, fwd_rel=info_f.rel_residual, adj_rel=info_a.rel_residual,
+               prof=prof, clocks=sampler.summary() if sampler else None, solver=S,
+               out=(u, qb, Db, mb))
+    return res
+
+
+def run_e2e(dmg, torch, w, precision, steps, warmup, world, local):
+    """Same pairs through the C ABI with pinned HOST buffers: every step copies
+    q, u, w host->device and u, qbar, Dbar, mubar device->host inside the call."""
+    dev = torch.device("cuda", local)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, rtol=RTOL)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    qh, wh = pin(w["q"]), pin(w["w"])
+    uh, qbh, Dbh, mbh = (torch.empty(w["shape"], dtype=torch.float64).pin_memory() for _ in range(4))
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        st = dmg.dmg_solve(S.ctx, qh, uh, None, stream, n=S.n)
+        assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+        st = dmg.dmg_vjp(S.ctx, uh, wh, 0, qbh, Dbh, mbh, None, stream, n=S.n)
+        assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+
+    for _ in range(warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    barrier(world)
+    el = max_over_ranks(world, el)
+    nbytes = 8 * int(np.prod(w["shape"]))
+    S.close()
+    return dict(seconds=el, h2d=3 * nbytes, d2h=4 * nbytes)
+
+
+def cpu_baseline_sample(w, m_fwd, m_adj):
+    """Times the FP64 CPU oracle (single-threaded C) on a bounded sample of the
+    workload -- one forward V-cycle, one transposed V-cycle, the residual norm
+    and the coefficient gradients at the full grid -- and scales it to one
+    fwd+VJP pair of m_fwd + m_adj cycles."""
+    import oracle
+    H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
+    shape = w["shape"]
+    z = np.zeros(shape)
+    t0 = time.perf_counter()
+    u1 = H.vcycle(w["q"], z)
+    t1 = time.perf_counter()
+    H.rel_residual(w["q"], u1)
+    t2 = time.perf_counter()
+    l1 = H.vcycle(w["w"], z, transposed=True)
+    t3 = time.perf_counter()
+    oracle.grad(w["D"], w["h"], u1, l1)
+    t4 = time.perf_counter()
+    t_pair = m_fwd * (t1 - t0 + t2 - t1) + m_adj * (t3 - t2 + t2 - t1) + (t4 - t3)
+    sample = ("1 forward + 1 transposed V(2,2) cycle, 1 residual norm and 1 gradient evaluation of the FP64 "
+              "oracle at %s (%.1f s), scaled to %d + %d cycles per fwd+VJP pair" %
+              ("x".join(map(str, shape)), t4 - t0, m_fwd, m_adj))
+    return dict(value=1.0 / t_pair, unit=UNIT, cores=1, kind="oracle", sample=sample,
+                seconds_per_pair=t_pair)
+
+
+def reference_arm(args, rank):
+    """The oracle as it stands, on this host's cores, on the same workload: every
+    step is one forward V-cycle plus its residual norm at the full grid (about
+    5 s single-threaded); one transposed cycle and one gradient evaluation are
+    timed once, and the pair time is m_fwd forward cycles + m_adj transposed
+    cycles + one gradient, with the cycle counts the oracle itself needs on the
+    same recipe at 129^3 (the V-cycle's contraction is h-independent)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2608_00760_b300 import inputs
+    oracle.build()
+    small = inputs.tissue(129, seed=0)
+    Hs = oracle.Hierarchy(small["D"], small["mu"], small["h"])
+    _, m_fwd, _ = Hs.solve(small["q"], rtol=RTOL)
+    _, m_adj, _ = Hs.adjoint(small["w"], rtol=RTOL)
+    w = make_inputs(args.size)
+    H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
+    z = np.zeros(w["shape"])
+
+    def fwd_cycle():
+        t0 = time.perf_counter()
+        u1 = H.vcycle(w["q"], z)
+        H.rel_residual(w["q"], u1)
+        return time.perf_counter() - t0, u1
+
+    for _ in range(args.warmup):
+        fwd_cycle()
+    times = []
+    for _ in range(args.steps):
+        t, u1 = fwd_cycle()
+        times.append(t)
+    t0 = time.perf_counter()
+    l1 = H.vcycle(w["w"], z, transposed=True)
+    H.rel_residual(w["w"], l1)
+    t_adj = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.grad(w["D"], w["h"], u1, l1)
+    t_grad = time.perf_counter() - t0
+    t_fwd = float(np.mean(times))
+    t_pair = m_fwd * t_fwd + m_adj * t_adj + t_grad
+    v = 1.0 / t_pair
+    sample = ("each step: 1 forward V(2,2) cycle + residual norm of the FP64 oracle at %d^3 (mean %.2f s); "
+              "pair = %d forward cycles + %d transposed cycles (%.2f s each, timed once) + 1 gradient (%.2f s); "
+              "cycle counts from the oracle's own 129^3 solves" % (args.size, t_fwd, m_fwd, m_adj, t_adj, t_grad))
+    out = dict(metric=METRIC, value=v, unit=UNIT, impl="reference", n_gpus=args.gpus, steps=args.steps,
+               warmup=args.warmup, ms_per_step=1e3 * t_pair, higher_is_better=True,
+               scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+               config=dict(workload="tissue-like %d^3 fwd+VJP(q,D,mu), rtol 1e-10" % args.size,
+                           grid=[args.size] * 3, h_mm=0.5, rtol=RTOL, precision="fp64 (CPU oracle, single thread)"),
+               cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample),
+               e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dmg", choices=["dmg", "reference"])
+    ap.add_argument("--size", type=int, default=N_SIDE)
+    ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args, int(os.environ.get("RANK", "0")))
+        return
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+
+    import torch
+    from paper_2608_00760_b300 import dmg
+    dmg.lib()
+    torch.cuda.set_device(local)
+    w = make_inputs(args.size)
+    npts = int(np.prod(w["shape"]))
+    nint = int(np.prod([s - 2 for s in w["shape"]]))
+    peaks, peak_src = load_peaks()
+
+    results = {}
+    precisions = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.only]
+    for prec in precisions:
+        p = dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64
+        prof = (dmg.DMG_KERNEL_SMOOTH, prec == "mixed")
+        results[prec] = run_arm(dmg, torch, w, p, args.steps, args.warmup, world, local, profile=prof,
+                                clocks=(prec == precisions[0]))
+
+    head = results[precisions[0]]
+    S = head["solver"]
+    ms = head["total_ms"] / args.steps
+    value = world * args.steps / (head["total_ms"] / 1e3)
+
+    def roofline(res, prec):
+        pr = res["prof"]
+        if not pr or not pr["launches"]:
+            return None
+        dur = pr["total_ms"] / pr["launches"] / 1e3
+        if prec == "mixed":
+            byt = SWEEP_BYTES["fp32"] * nint
+            ach = byt / dur / 1e9
+            pk = peaks.get("hbm_gbs", 6400.0)
+            return dict(kernel="rbgs_sweep_fp32_level0", bound="hbm", achieved=ach, peak=pk, unit="GB/s",
+                        frac=ach / pk, traffic=None, peak_source=peak_src + " hbm_gbs",
+                        launches=pr["launches"], avg_us=dur * 1e6, algorithmic_bytes=byt)
+        ops = SWEEP_FP64_OPS * nint
+        ach = ops / dur / 1e12
+        return dict(kernel="rbgs_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK / 1e12,
+                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=None,
+                    peak_source="measured DFMA rate (probe)", launches=pr["launches"], avg_us=dur * 1e6,
+                    algorithmic_fp64_ops=ops)
+
+    def gbs(res, prec):
+        # algorithmic HBM bytes of one pair divided by its time (see the design notes for the per-cycle bytes)
+        per_cycle = 272.0 if prec == "fp64" else 136.0
+        outer = 56.0 if prec == "mixed" else 0.0
+        cyc = res["fwd_cycles"] + res["adj_cycles"]
+        byt = npts * (per_cycle * cyc + outer * (res["fwd_outer"] + res["adj_outer"]) + 40.0)
+        return byt / (res["total_ms"] / args.steps / 1e3) / 1e9
+
+    out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+               dtype="f32-inner/f64-outer" if precisions[0] == "mixed" else "f64", data="synthetic",
+               config=dict(workload="tissue-like %d^3 fwd+VJP(q,D,mu), rtol 1e-10" % args.size,
+                           grid=list(w["shape"]), h_mm=w["h"], rtol=RTOL, precision=precisions[0],
+                           parallelism="replicas" if world > 1 else "single-gpu",
+                           l2="inputs larger than L2 (each FP64 field %.0f MB > 126 MB); no flush" % (8 * npts / 1e6),
+                           setup="dmg_setup once per coefficient field, outside the timed region"),
+               p50_ms=percentile(head["per_ms"], 50), p99_ms=percentile(head["per_ms"], 99),
+               hbm_gbs_algorithmic=gbs(head, precisions[0]),
+               cycles=dict(fwd=head["fwd_cycles"], adj=head["adj_cycles"], fwd_outer=head["fwd_outer"],
+                           adj_outer=head["adj_outer"], fwd_rel=head["fwd_rel"], adj_rel=head["adj_rel"]),
+               gpu_launches=head["launches"], gpu_launches_per_step=head["launches"] / args.steps,
+               roofline=roofline(head, precisions[0]), clocks=head["clocks"])
+    for prec in precisions[1:]:
+        r = results[prec]
+        out[prec] = dict(value=world * args.steps / (r["total_ms"] / 1e3), unit=UNIT,
+                         ms_per_step=r["total_ms"] / args.steps, p50_ms=percentile(r["per_ms"], 50),
+                         p99_ms=percentile(r["per_ms"], 99), hbm_gbs_algorithmic=gbs(r, prec),
+                         cycles=dict(fwd=r["fwd_cycles"], adj=r["adj_cycles"]), gpu_launches=r["launches"],
+                         roofline=roofline(r, prec))
+    if "mixed" in results and "fp64" in results:
+        a, b = results["mixed"]["out"], results["fp64"]["out"]
+        out["mixed_vs_fp64_rel_err"] = {k: float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
+                                        for k, x, y in zip(("u", "qbar", "Dbar", "mubar"), a, b)}
+    for r in results.values():
+        r["solver"].close()
+        r.pop("out", None)
+
+    if not args.no_e2e:
+        e = run_e2e(dmg, torch, w, dmg.DMG_MIXED if precisions[0] == "mixed" else dmg.DMG_FP64,
+                    max(2, args.steps // 4), 1, world, local)
+        ns = max(2, args.steps // 4)
+        out["e2e"] = dict(value=world * ns / e["seconds"], unit=UNIT, h2d_bytes_per_step=e["h2d"],
+                          d2h_bytes_per_step=e["d2h"], steps=ns, api="dmg_solve + dmg_vjp with pinned host buffers")
+    else:
+        out["e2e"] = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m_f = results.get("fp64", head)["fwd_cycles"]
+        m_a = results.get("fp64", head)["adj_cycles"]
+        out["cpu_baseline"] = cpu_baseline_sample(w, m_f, m_a)
+        out["cpu_baseline"].pop("seconds_per_pair", None)
+    else:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
