@@ -171,6 +171,33 @@ dmg_status dmg_vjp(dmg_ctx *ctx, const double *u, const double *w, int cycles, d
 dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *out,
                         void *stream);
 
+/*
+ * dmg_residual_static -- out[0] = ||q - A u||_2 and out[1] = ||q||_2 over
+ * interior vertices in FP64, like dmg_residual, but with no context and
+ * without allocating any device memory. The paper has no counterpart: this is
+ * for callers that are not allowed to allocate device memory, e.g. code
+ * running inside a host framework that owns the whole device pool through its
+ * own allocator, or a latency-critical loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree. Such callers cannot run
+ * dmg_setup either, so this call works from their arrays alone.
+ *   p          only nx, ny, nz, h and face_mean are read.
+ *   D, mu, q, u  device memory of the current device, C order [nz][ny][nx],
+ *              all vertices; boundary values of q and u are ignored.
+ *   out        2 doubles, host or device memory.
+ * The reduction's scratch is a fixed 4 MB file-scope device array that every
+ * GPU which loads the library holds until the process exits. It bounds the
+ * grid: (ny-2)*(nz-2) <= 262144 interior rows (513^3 fits); larger grids get
+ * DMG_EINVAL with the reason in dmg_last_error(NULL).
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams
+ * or host threads) race and must be serialised by the caller. Each call writes
+ * every scratch slot it reads, so no clearing is needed between calls. The
+ * call returns after out is written (it synchronises the stream).
+ */
+dmg_status dmg_residual_static(const dmg_params *p, const double *D, const double *mu,
+                               const double *q, const double *u, double *out, void *stream);
+
 /* Frees every resource of the context. NULL is accepted. */
 dmg_status dmg_destroy(dmg_ctx *ctx);
 
@@ -178,7 +205,8 @@ dmg_status dmg_destroy(dmg_ctx *ctx);
 const char *dmg_strerror(dmg_status s);
 
 /* Message of the last failure on ctx ("" if none). With ctx == NULL: the message
-   of the last failed dmg_setup on the calling thread. */
+   of the last failed context-free call (dmg_setup, dmg_residual_static) on the
+   calling thread. */
 const char *dmg_last_error(const dmg_ctx *ctx);
 
 /* Number of hierarchy levels and the vertex counts of level l (0 = finest). */

@@ -525,6 +525,10 @@ dmg_status guarded(dmg_ctx *c, F fn) {
 
 }  // namespace
 
+// Sets the message dmg_last_error(NULL) returns on this thread; used by the
+// context-free entry point in noalloc.cu.
+void dmg_detail_set_noctx_error(const char *msg) { snprintf(g_setup_err, sizeof(g_setup_err), "%s", msg); }
+
 // ==================================================================================
 // C ABI
 

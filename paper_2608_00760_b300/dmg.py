@@ -45,7 +45,7 @@ class dmg_info(ctypes.Structure):
 
 EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp", "dmg_residual",
            "dmg_destroy", "dmg_strerror", "dmg_last_error", "dmg_levels", "dmg_level_shape",
-           "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end")
+           "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static")
 
 _lib = None
 
@@ -81,6 +81,7 @@ def lib():
             "dmg_launch_count": (ctypes.c_ulonglong, [vp]),
             "dmg_profile_begin": (i, [vp, i, i, i, i]),
             "dmg_profile_end": (i, [vp, P(ctypes.c_longlong), P(d)]),
+            "dmg_residual_static": (i, [P(dmg_params), vp, vp, vp, vp, P(d), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -167,6 +168,16 @@ def dmg_vjp(ctx, u, w, cycles, qbar, Dbar, mubar, info=None, stream=None, n=None
 def dmg_residual(ctx, q, u, stream=None, n=None):
     out = (ctypes.c_double * 2)()
     st = lib().dmg_residual(ctx, _ptr(q, n), _ptr(u, n), out, _stream(stream))
+    return st, (out[0], out[1])
+
+
+def dmg_residual_static(params: dmg_params, D, mu, q, u, stream=None):
+    """Context-free, allocation-free residual norm: (status, (||q - A u||, ||q||)).
+    D, mu, q, u must be device arrays of the current device."""
+    n = params.nx * params.ny * params.nz
+    out = (ctypes.c_double * 2)()
+    st = lib().dmg_residual_static(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _ptr(q, n), _ptr(u, n), out,
+                                   _stream(stream))
     return st, (out[0], out[1])
 
 
