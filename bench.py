@@ -150,12 +150,12 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
-def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None, clocks=False):
+def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None, clocks=False, inner=1):
     """Times `steps` fwd+VJP pairs; returns a result dict."""
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     D, mu, q, wv = T(w["D"]), T(w["mu"]), T(w["q"]), T(w["w"])
-    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL)
+    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL, inner_cycles=inner)
     u = torch.empty_like(q)
     qb, Db, mb = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
     info_f, info_a = dmg.dmg_info(), dmg.dmg_info()
@@ -172,7 +172,7 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
     for _ in range(warmup):
         step()
     if profile is not None:
-        dmg.dmg_profile_begin(S.ctx, profile[0], 0, profile[1], max_launches=100000)
+        dmg.dmg_profile_begin(S.ctx, profile[0], 0, profile[1], max_launches=4096)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     l0 = dmg.dmg_launch_count(S.ctx)
     barrier(world)
@@ -203,12 +203,12 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
     return res
 
 
-def run_e2e(dmg, torch, w, precision, steps, warmup, world, local):
+def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
     """Same pairs through the C ABI with pinned HOST buffers: every step copies
     q, u, w host->device and u, qbar, Dbar, mubar device->host inside the call."""
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, rtol=RTOL)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, rtol=RTOL, inner_cycles=inner)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     qh, wh = pin(w["q"]), pin(w["w"])
     uh, qbh, Dbh, mbh = (torch.empty(w["shape"], dtype=torch.float64).pin_memory() for _ in range(4))
@@ -327,6 +327,7 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step (mixed)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args, int(os.environ.get("RANK", "0")))
@@ -349,7 +350,7 @@ def main():
         p = dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64
         prof = (dmg.DMG_KERNEL_SMOOTH, prec == "mixed")
         results[prec] = run_arm(dmg, torch, w, p, args.steps, args.warmup, world, local, profile=prof,
-                                clocks=(prec == precisions[0]))
+                                clocks=(prec == precisions[0]), inner=args.inner if prec == "mixed" else 1)
 
     head = results[precisions[0]]
     S = head["solver"]
@@ -389,6 +390,7 @@ def main():
                config=dict(workload="tissue-like %d^3 fwd+VJP(q,D,mu), rtol 1e-10" % args.size,
                            grid=list(w["shape"]), h_mm=w["h"], rtol=RTOL, precision=precisions[0],
                            parallelism="replicas" if world > 1 else "single-gpu",
+                           inner_cycles=args.inner if precisions[0] == "mixed" else None,
                            l2="inputs larger than L2 (each FP64 field %.0f MB > 126 MB); no flush" % (8 * npts / 1e6),
                            setup="dmg_setup once per coefficient field, outside the timed region"),
                p50_ms=percentile(head["per_ms"], 50), p99_ms=percentile(head["per_ms"], 99),
@@ -414,7 +416,7 @@ def main():
 
     if not args.no_e2e:
         e = run_e2e(dmg, torch, w, dmg.DMG_MIXED if precisions[0] == "mixed" else dmg.DMG_FP64,
-                    max(2, args.steps // 4), 1, world, local)
+                    max(2, args.steps // 4), 1, world, local, inner=args.inner)
         ns = max(2, args.steps // 4)
         out["e2e"] = dict(value=world * ns / e["seconds"], unit=UNIT, h2d_bytes_per_step=e["h2d"],
                           d2h_bytes_per_step=e["d2h"], steps=ns, api="dmg_solve + dmg_vjp with pinned host buffers")

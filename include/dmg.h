@@ -82,7 +82,8 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *   face_mean     DMG_FACE_ARITHMETIC (default) or DMG_FACE_HARMONIC.
  *   coarsen       coarse coefficients: DMG_COARSEN_FULL_WEIGHTING (default; full
  *                 weighting inside, injection on the boundary) or INJECTION.
- *   inner_cycles  FP32 V-cycles per refinement step in mixed mode (default 1).
+ *   inner_cycles  FP32 V-cycles per refinement step in mixed mode (default 3:
+ *                 each step then gains ~3 decades, far above the FP32 floor).
  */
 typedef struct {
     int nx, ny, nz;

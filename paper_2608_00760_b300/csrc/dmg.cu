@@ -7,6 +7,7 @@
 // derivative kernels. It computes nothing itself.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,6 +40,14 @@ struct Level {
     float *u32 = nullptr, *f32 = nullptr, *r32 = nullptr, *Dh32 = nullptr, *mu32 = nullptr;
 };
 
+// an instantiated CUDA graph, the kernels one replay launches, and the profiling
+// event pairs each replay records
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+    std::vector<int> prof;
+};
+
 }  // namespace
 
 struct dmg_ctx {
@@ -48,17 +57,28 @@ struct dmg_ctx {
     int nc = 0;                       // coarsest interior unknowns
     double *Ainv = nullptr;           // coarsest inverse (FP64)
     float *Ainv32 = nullptr;
+    double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
-    double *red = nullptr;            // reduction results (device, 4 doubles)
+    double *red = nullptr;            // reduction results (device, 4 doubles; slot 3 = kernel error flag)
     double *hred = nullptr;           // pinned host copy of red
+    dmgk::MixScalars *ms = nullptr;   // device scalars of the mixed-precision loop
     std::vector<void *> dev_allocs;
     unsigned long long launches = 0;
     char err[512] = {0};
-    // profiling
-    int prof_kernel = -1, prof_level = 0, prof_fp32 = 0, prof_max = 0, prof_n = 0;
-    std::vector<cudaEvent_t> prof_ev;
+    // CUDA graphs of the repeated steps, captured on first use on cap_stream:
+    // [0] forward, [1] transposed
+    cudaStream_t cap_stream = nullptr;
+    Graph g_mix[2], g_cyc[2], g_fix[2];
+    // profiling: event pairs bracketing launches of one kernel on one level
+    int prof_kernel = -1, prof_level = 0, prof_fp32 = 0;
+    std::vector<cudaEvent_t> prof_ev;   // 2 per pair
+    std::vector<int> prof_free;         // unused pairs
+    std::vector<int> prof_direct;       // pairs recorded by direct launches since the last harvest
+    std::vector<int> *prof_sink = nullptr;
+    long long prof_count = 0;
+    double prof_ms = 0.0;
 };
 
 namespace {
@@ -90,11 +110,14 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // interior launch: block (32, 8), grid over interior x/y, one z-plane per blockIdx.z
 inline dim3 blk() { return dim3(32, 8, 1); }
-inline dim3 grid_int(const Geom &g, int xdiv = 1) {
-    int nxi = (g.nx - 2 + xdiv - 1) / xdiv;
-    return dim3((nxi + 31) / 32, (g.ny - 2 + 7) / 8, g.nz - 2);
+// per-vertex kernels: blockIdx.x = 2 * (32-wide chunk of the half-row) + parity
+inline dim3 grid_int(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nz - 2); }
+inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nz); }
+// half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
+inline dim3 grid_half(const Geom &g) {
+    const int rows = 8 * dmgk::kRowsPerThread;
+    return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + rows - 1) / rows, g.nz - 2);
 }
-inline dim3 grid_all(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz); }
 
 dmg_status check_launch(dmg_ctx *c, const char *what) {
     c->launches++;
@@ -118,50 +141,90 @@ dmg_status dalloc(dmg_ctx *c, T **p, size_t n) {
 }
 
 // --- profiling hooks -------------------------------------------------------
+// A ProfScope brackets the launches of one kernel (kind, level, precision)
+// with an event pair; in a graph capture the records become event nodes that
+// every replay re-records, and the pair is harvested after each replay.
 struct ProfScope {
     dmg_ctx *c;
     cudaStream_t s;
-    bool on;
+    int idx = -1;
     ProfScope(dmg_ctx *c_, int kernel, int level, int fp32, cudaStream_t s_) : c(c_), s(s_) {
-        on = c->prof_kernel == kernel && c->prof_level == level && c->prof_fp32 == fp32 &&
-             c->prof_n < c->prof_max;
-        if (on) cudaEventRecord(c->prof_ev[2 * c->prof_n], s);
+        if (c->prof_kernel == kernel && c->prof_level == level && c->prof_fp32 == fp32 && !c->prof_free.empty()) {
+            idx = c->prof_free.back();
+            c->prof_free.pop_back();
+            cudaEventRecordWithFlags(c->prof_ev[2 * idx], s, cudaEventRecordExternal);
+        }
     }
     ~ProfScope() {
-        if (on) {
-            cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], s);
-            c->prof_n++;
+        if (idx >= 0) {
+            cudaEventRecordWithFlags(c->prof_ev[2 * idx + 1], s, cudaEventRecordExternal);
+            (c->prof_sink ? c->prof_sink : &c->prof_direct)->push_back(idx);
         }
     }
 };
 
-// --- staging between the caller's contiguous arrays and the padded layout ---
-dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, cudaStream_t s) {
+// add the durations of completed pairs; release them unless a graph owns them
+void prof_harvest(dmg_ctx *c, std::vector<int> &pairs, bool release) {
+    for (int idx : pairs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ev[2 * idx], c->prof_ev[2 * idx + 1]) == cudaSuccess) {
+            c->prof_ms += ms;
+            c->prof_count++;
+        } else {
+            cudaGetLastError();
+        }
+        if (release) c->prof_free.push_back(idx);
+    }
+    if (release) pairs.clear();
+}
+
+void graphs_reset(dmg_ctx *c) {
+    for (Graph *set : {c->g_mix, c->g_cyc, c->g_fix})
+        for (int t = 0; t < 2; t++) {
+            if (set[t].exec) cudaGraphExecDestroy(set[t].exec);
+            for (int idx : set[t].prof) c->prof_free.push_back(idx);
+            set[t] = Graph();
+        }
+}
+
+// --- staging between the caller's contiguous arrays and the split layout -------
+// Device (or managed) caller arrays are read/written in place by the gather and
+// scatter kernels; host arrays go through the contiguous staging buffer.
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline unsigned n_vertex_blocks(const Geom &g) {
+    return (unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256);
+}
+
+dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s) {
     const Geom &g = c->L[0].g;
-    CUDA_TRY(c, cudaMemcpy2DAsync(dst, (size_t)g.sy * sizeof(double), src, (size_t)g.nx * sizeof(double),
-                                  (size_t)g.nx * sizeof(double), (size_t)g.ny * g.nz, cudaMemcpyDefault, s));
-    return DMG_OK;
+    size_t bytes = (size_t)g.nx * g.ny * g.nz * sizeof(double);
+    const double *from = src;
+    if (!is_device_ptr(src)) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->stage, src, bytes, cudaMemcpyHostToDevice, s));
+        from = c->stage;
+    }
+    dmgk::k_gather<<<n_vertex_blocks(g), 256, 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
+    return check_launch(c, "gather");
 }
 
 dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s) {
     const Geom &g = c->L[0].g;
-    CUDA_TRY(c, cudaMemcpy2DAsync(dst, (size_t)g.nx * sizeof(double), src, (size_t)g.sy * sizeof(double),
-                                  (size_t)g.nx * sizeof(double), (size_t)g.ny * g.nz, cudaMemcpyDefault, s));
-    return DMG_OK;
-}
-
-// zero the boundary of a padded level-0 FP64 array that was staged from the caller
-dmg_status zero_boundary(dmg_ctx *c, double *x, cudaStream_t s) {
-    const Geom &g = c->L[0].g;
-    size_t row = (size_t)g.sy * sizeof(double);
-    // planes k = 0 and k = nz-1
-    CUDA_TRY(c, cudaMemsetAsync(x, 0, (size_t)g.sz * sizeof(double), s));
-    CUDA_TRY(c, cudaMemsetAsync(x + (size_t)(g.nz - 1) * g.sz, 0, (size_t)g.sz * sizeof(double), s));
-    // rows j = 0 and j = ny-1 of every plane; columns i = 0 and i = nx-1 of every row
-    CUDA_TRY(c, cudaMemset2DAsync(x, (size_t)g.sz * sizeof(double), 0, row, g.nz, s));
-    CUDA_TRY(c, cudaMemset2DAsync(x + (size_t)(g.ny - 1) * g.sy, (size_t)g.sz * sizeof(double), 0, row, g.nz, s));
-    CUDA_TRY(c, cudaMemset2DAsync(x, row, 0, sizeof(double), (size_t)g.ny * g.nz, s));
-    CUDA_TRY(c, cudaMemset2DAsync(x + (g.nx - 1), row, 0, sizeof(double), (size_t)g.ny * g.nz, s));
+    size_t bytes = (size_t)g.nx * g.ny * g.nz * sizeof(double);
+    if (is_device_ptr(dst)) {
+        dmgk::k_scatter<<<n_vertex_blocks(g), 256, 0, s>>>(g, src, dst);
+        return check_launch(c, "scatter");
+    }
+    dmgk::k_scatter<<<n_vertex_blocks(g), 256, 0, s>>>(g, src, c->stage);
+    TRY(check_launch(c, "scatter"));
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->stage, bytes, cudaMemcpyDeviceToHost, s));
     return DMG_OK;
 }
 
@@ -200,12 +263,30 @@ dmg_status dispatch(dmg_ctx *c, Level &l, Fn fn) {
 template <class T>
 dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
     Level &l = c->L[lev];
+    if constexpr (sizeof(T) == 4) {
+        // four vertices per thread, float4 loads
+        dim3 grid(((l.g.hx / 4) + 31) / 32, (l.g.ny - 2 + 7) / 8, l.g.nz - 2);
+        for (int it = 0; it < nsweeps; it++) {
+            ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, 1, s);
+            for (int h = 0; h < 2; h++) {
+                int color = h == 0 ? first : 1 - first;
+                if (c->p.face_mean == DMG_FACE_HARMONIC)
+                    dmgk::k_smooth_half_v4<true><<<grid, blk(), 0, s>>>(
+                        l.g, l.u32, l.f32, dmgk::VertCoef<float, true>{l.Dh32, l.mu32}, color);
+                else
+                    dmgk::k_smooth_half_v4<false><<<grid, blk(), 0, s>>>(
+                        l.g, l.u32, l.f32, dmgk::VertCoef<float, false>{l.Dh32, l.mu32}, color);
+                TRY(check_launch(c, "smooth_v4"));
+            }
+        }
+        return DMG_OK;
+    }
     for (int it = 0; it < nsweeps; it++) {
         ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
         for (int h = 0; h < 2; h++) {
             int color = h == 0 ? first : 1 - first;
             TRY(dispatch<T>(c, l, [&](auto cf) {
-                dmgk::k_smooth_half<T><<<grid_int(l.g, 2), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color);
+                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color);
                 return check_launch(c, "smooth");
             }));
         }
@@ -232,7 +313,8 @@ template <class T>
 dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
     Level &l = c->L[lev], &cl = c->L[lev + 1];
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
-    dmgk::k_prolong_add<T><<<grid_int(l.g), blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l));
+    dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, cl.g.nz - 1);   // coarse cells
+    dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l));
     return check_launch(c, "prolong");
 }
 
@@ -263,11 +345,33 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
 }
 
 // --- reductions ------------------------------------------------------------------
-dmg_status finish_reduce(dmg_ctx *c, int nslots, cudaStream_t s, double *out) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, nslots * sizeof(double), cudaMemcpyDeviceToHost, s));
+// copy the reduction slots (and the kernel error flag) to pinned host memory
+dmg_status enqueue_readback(dmg_ctx *c, cudaStream_t s) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return DMG_OK;
+}
+
+// wait for the stream, check the kernel error flag, return nslots results
+dmg_status sync_read(dmg_ctx *c, int nslots, cudaStream_t s, double *out) {
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    prof_harvest(c, c->prof_direct, true);
+    int kerr = 0;
+    memcpy(&kerr, c->hred + 3, sizeof(int));
+    if (kerr != 0) return fail(c, DMG_ETIMEOUT, "a bounded device wait ran out (kernel error flag %d)", kerr);
     for (int i = 0; i < nslots; i++) out[i] = c->hred[i];
     return DMG_OK;
+}
+
+// end of an API call: wait for the stream, harvest direct profiling pairs
+dmg_status end_call(dmg_ctx *c, cudaStream_t s) {
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    prof_harvest(c, c->prof_direct, true);
+    return DMG_OK;
+}
+
+dmg_status finish_reduce(dmg_ctx *c, int nslots, cudaStream_t s, double *out) {
+    TRY(enqueue_readback(c, s));
+    return sync_read(c, nslots, s, out);
 }
 
 // ||x||_2^2 over interior of a level-0 FP64 array -> red[slot]
@@ -278,18 +382,55 @@ dmg_status norm2_async(dmg_ctx *c, const double *x, int slot, cudaStream_t s) {
     return check_launch(c, "reduce");
 }
 
-// ||f - A u||^2 (FP64, level 0) -> red[slot]; optional r32 = (r * r32_scale)
-dmg_status resid_norm_async(dmg_ctx *c, const double *u, const double *f, float *r32, double r32_scale,
-                            int slot, cudaStream_t s) {
+// ||f - A u||^2 (FP64, level 0) -> red[slot]; with r32: the FP32 right-hand side
+// r * 2^-ms->e_prev
+dmg_status resid_norm_async(dmg_ctx *c, const double *u, const double *f, float *r32, int slot, cudaStream_t s) {
     Level &l = c->L[0];
     {
         ProfScope ps(c, DMG_KERNEL_RESIDUAL, 0, 0, s);
-        dmgk::k_resid_norm<double><<<kNormBlocks, 256, 0, s>>>(l.g, u, f, coef64(l), (double *)nullptr, r32,
-                                                               r32_scale, c->partial);
+        dmgk::k_resid_norm<double><<<kNormBlocks, 256, 0, s>>>(l.g, u, f, coef64(l), (double *)nullptr, r32, c->ms,
+                                                               c->partial);
         TRY(check_launch(c, "resid_norm"));
     }
     dmgk::k_reduce_final<<<1, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot);
     return check_launch(c, "reduce");
+}
+
+// --- CUDA graphs ---------------------------------------------------------------------
+// Capture body(stream) once on the context's capture stream; kernels launched
+// while capturing are counted per replay instead of as launches.
+template <class Body>
+dmg_status capture(dmg_ctx *c, Graph &G, Body body) {
+    if (G.exec) return DMG_OK;
+    cudaStream_t cs = c->cap_stream;
+    unsigned long long l0 = c->launches;
+    std::vector<int> *saved = c->prof_sink;
+    c->prof_sink = &G.prof;
+    CUDA_TRY(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    dmg_status st = body(cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    c->prof_sink = saved;
+    G.launches = c->launches - l0;
+    c->launches = l0;
+    if (st != DMG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, DMG_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        G.exec = nullptr;
+        return fail(c, DMG_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+    }
+    return DMG_OK;
+}
+
+dmg_status replay(dmg_ctx *c, Graph &G, cudaStream_t s) {
+    CUDA_TRY(c, cudaGraphLaunch(G.exec, s));
+    c->launches += G.launches;
+    return DMG_OK;
 }
 
 void info_reset(dmg_info *info) {
@@ -298,9 +439,12 @@ void info_reset(dmg_info *info) {
 }
 
 // Plain FP64 iteration on level 0: u_0 = 0, then V-cycles on A u_0 = f_0.
-// fixed > 0: exactly `fixed` cycles; else until rtol or max_cycles.
+// fixed > 0: exactly `fixed` cycles; else until rtol or max_cycles. One graph
+// replay per cycle (the cycle, and in tolerance mode the residual norm and its
+// read-back).
 dmg_status iterate64(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cudaStream_t s) {
     Level &l = c->L[0];
+    const int t = transposed ? 1 : 0;
     CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
     double nf2;
     TRY(norm2_async(c, l.f, 0, s));
@@ -309,66 +453,87 @@ dmg_status iterate64(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cud
     double nf = std::sqrt(nf2);
     if (info) { info->cycles = 0; info->outer = 0; info->rel_residual = 0.0; }
     if (nf == 0.0) return DMG_OK;
-    int ncyc = fixed > 0 ? fixed : c->p.max_cycles;
     double rel = 1.0;
     int cyc = 0;
-    for (cyc = 1; cyc <= ncyc; cyc++) {
-        TRY(vcycle<double>(c, 0, transposed, s));
-        if (fixed > 0 && cyc < ncyc) continue;
+    if (fixed > 0) {
+        TRY(capture(c, c->g_fix[t], [&](cudaStream_t cs) { return vcycle<double>(c, 0, transposed, cs); }));
+        for (cyc = 1; cyc <= fixed; cyc++) TRY(replay(c, c->g_fix[t], s));
+        cyc = fixed;
         double rn2;
-        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0.0, 0, s));
+        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, s));
         TRY(finish_reduce(c, 1, s, &rn2));
+        prof_harvest(c, c->g_fix[t].prof, false);
+        rel = std::sqrt(rn2) / nf;
+        if (info) { info->cycles = cyc; info->outer = cyc; info->rel_residual = rel; }
+        if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite");
+        return DMG_OK;
+    }
+    TRY(capture(c, c->g_cyc[t], [&](cudaStream_t cs) -> dmg_status {
+        TRY(vcycle<double>(c, 0, transposed, cs));
+        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, cs));
+        return enqueue_readback(c, cs);
+    }));
+    for (cyc = 1; cyc <= c->p.max_cycles; cyc++) {
+        double rn2;
+        TRY(replay(c, c->g_cyc[t], s));
+        TRY(sync_read(c, 1, s, &rn2));
+        prof_harvest(c, c->g_cyc[t].prof, false);
         if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite after cycle %d", cyc);
         rel = std::sqrt(rn2) / nf;
-        if (info && fixed == 0 && cyc - 1 < DMG_HIST_LEN) info->hist[cyc - 1] = rel;
-        if (fixed == 0 && rel <= c->p.rtol) break;
+        if (info && cyc - 1 < DMG_HIST_LEN) info->hist[cyc - 1] = rel;
+        if (rel <= c->p.rtol) break;
     }
-    if (cyc > ncyc) cyc = ncyc;
+    if (cyc > c->p.max_cycles) cyc = c->p.max_cycles;
     if (info) { info->cycles = cyc; info->outer = cyc; info->rel_residual = rel; }
-    if (fixed == 0 && rel > c->p.rtol)
+    if (rel > c->p.rtol)
         return fail(c, DMG_ENOCONV, "relative residual %.3e > rtol %.3e after %d cycles", rel, c->p.rtol, cyc);
     return DMG_OK;
 }
 
 // Mixed precision defect correction on level 0 (FP64 u_0, f_0): each step runs
-// inner_cycles FP32 V-cycles on A e = r / scale and updates u_0 += scale * e in
-// FP64; residual, norms and update stay in FP64.
+// inner_cycles FP32 V-cycles on A e = r * 2^-e_cur from e = 0, then updates
+// u_0 += e * 2^e_cur and forms the next FP64 residual and its norm. Residual,
+// norms and update stay in FP64; the scale exponents live on the device, so a
+// whole step is one graph replay.
 dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream_t s) {
     Level &l = c->L[0];
+    const int t = transposed ? 1 : 0;
     CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
     double nf2;
     TRY(norm2_async(c, l.f, 0, s));
+    dmgk::k_mix_init<<<1, 1, 0, s>>>(c->red, 0, c->ms);
+    TRY(check_launch(c, "mix_init"));
+    dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
+    TRY(check_launch(c, "to_f32"));
     TRY(finish_reduce(c, 1, s, &nf2));
     if (!std::isfinite(nf2)) return fail(c, DMG_ENAN, "right-hand side is not finite");
     double nf = std::sqrt(nf2);
     if (info) { info->cycles = 0; info->outer = 0; info->rel_residual = 0.0; }
     if (nf == 0.0) return DMG_OK;
-    double scale = nf;                 // divisor carried by the FP32 right-hand side
-    dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, 1.0 / scale, l.f32);
-    TRY(check_launch(c, "to_f32"));
-    double last = nf, rel = 1.0;
-    int step = 0, inner = 0;
-    for (step = 1; step <= c->p.max_cycles; step++) {
-        CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), s));
-        for (int ic = 0; ic < c->p.inner_cycles; ic++) {
-            TRY(vcycle<float>(c, 0, transposed, s));
-            inner++;
-        }
-        dmgk::k_update<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.u, l.u32, scale);
+    TRY(capture(c, c->g_mix[t], [&](cudaStream_t cs) -> dmg_status {
+        CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), cs));
+        for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
+        dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms);
         TRY(check_launch(c, "update"));
+        TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, cs));
+        dmgk::k_mix_next<<<1, 1, 0, cs>>>(c->red, 0, c->ms);
+        TRY(check_launch(c, "mix_next"));
+        return enqueue_readback(c, cs);
+    }));
+    double rel = 1.0;
+    int step = 0;
+    for (step = 1; step <= c->p.max_cycles; step++) {
         double rn2;
-        TRY(resid_norm_async(c, l.u, l.f, l.f32, 1.0 / last, 0, s));
-        TRY(finish_reduce(c, 1, s, &rn2));
+        TRY(replay(c, c->g_mix[t], s));
+        TRY(sync_read(c, 1, s, &rn2));
+        prof_harvest(c, c->g_mix[t].prof, false);
         if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite after step %d", step);
-        scale = last;
-        last = std::sqrt(rn2);
-        rel = last / nf;
+        rel = std::sqrt(rn2) / nf;
         if (info && step - 1 < DMG_HIST_LEN) info->hist[step - 1] = rel;
-        if (rel <= c->p.rtol) break;
-        if (last == 0.0) break;
+        if (rel <= c->p.rtol || rn2 == 0.0) break;
     }
     if (step > c->p.max_cycles) step = c->p.max_cycles;
-    if (info) { info->cycles = inner; info->outer = step; info->rel_residual = rel; }
+    if (info) { info->cycles = step * c->p.inner_cycles; info->outer = step; info->rel_residual = rel; }
     if (rel > c->p.rtol)
         return fail(c, DMG_ENOCONV, "relative residual %.3e > rtol %.3e after %d steps", rel, c->p.rtol, step);
     return DMG_OK;
@@ -394,7 +559,8 @@ int count_levels(int nx, int ny, int nz) {
 Geom make_geom(int nx, int ny, int nz) {
     Geom g;
     g.nx = nx; g.ny = ny; g.nz = nz;
-    g.sy = ((nx + 31) / 32) * 32;
+    g.hx = (((nx + 1) / 2 + 31) / 32) * 32;
+    g.sy = 2 * g.hx;
     g.sz = (long long)g.sy * ny;
     return g;
 }
@@ -461,19 +627,24 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         }
     }
     Level &L0 = c->L[0];
+    TRY(dalloc(c, &c->stage, (size_t)p->nx * p->ny * p->nz));
     for (double **q : {&c->U0, &c->T1, &c->T2, &c->T3}) {
         TRY(dalloc(c, q, L0.n));
         CUDA_TRY(c, cudaMemsetAsync(*q, 0, L0.n * sizeof(double), s));
     }
     TRY(dalloc(c, &c->partial, kNormBlocks));
     TRY(dalloc(c, &c->red, 4));
+    TRY(dalloc(c, &c->ms, 1));
+    CUDA_TRY(c, cudaMemsetAsync(c->ms, 0, sizeof(dmgk::MixScalars), s));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaMemsetAsync(c->red, 0, 4 * sizeof(double), s));
     {
         cudaError_t e = cudaMallocHost(&c->hred, 4 * sizeof(double));
         if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
     }
     // level-0 coefficients from the caller, then coarsen level by level
-    TRY(stage_in(c, D, L0.D, s));
-    TRY(stage_in(c, mu, L0.mu, s));
+    TRY(stage_in(c, D, L0.D, false, s));
+    TRY(stage_in(c, mu, L0.mu, false, s));
     for (int l = 1; l < c->nlev; l++) {
         Level &F = c->L[l - 1], &C = c->L[l];
         dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
@@ -546,7 +717,7 @@ void dmg_default_params(dmg_params *p) {
     p->precision = DMG_FP64;
     p->face_mean = DMG_FACE_ARITHMETIC;
     p->coarsen = DMG_COARSEN_FULL_WEIGHTING;
-    p->inner_cycles = 1;
+    p->inner_cycles = 3;
 }
 
 dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, void *stream, dmg_ctx **out) {
@@ -571,11 +742,11 @@ dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, voi
         info_reset(info);
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
-        TRY(stage_in(c, q, l.f, s));
+        TRY(stage_in(c, q, l.f, false, s));
         dmg_status st = iterate(c, false, c->p.fixed_cycles, info, s);
         if (st != DMG_OK && st != DMG_ENOCONV) return st;
         TRY(stage_out(c, l.u, u, s));
-        CUDA_TRY(c, cudaStreamSynchronize(s));
+        TRY(end_call(c, s));
         return st;
     });
 }
@@ -589,15 +760,14 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
         if (dq) {
-            TRY(stage_in(c, dq, l.f, s));
+            TRY(stage_in(c, dq, l.f, false, s));
         } else {
             CUDA_TRY(c, cudaMemsetAsync(l.f, 0, l.n * sizeof(double), s));
         }
         if (dD || dmu) {
-            TRY(stage_in(c, u, c->U0, s));
-            TRY(zero_boundary(c, c->U0, s));
-            if (dD) TRY(stage_in(c, dD, c->T1, s));
-            if (dmu) TRY(stage_in(c, dmu, c->T2, s));
+            TRY(stage_in(c, u, c->U0, true, s));
+            if (dD) TRY(stage_in(c, dD, c->T1, false, s));
+            if (dmu) TRY(stage_in(c, dmu, c->T2, false, s));
             double ih2 = 1.0 / (l.h * l.h);
             dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0, dD ? c->T1 : nullptr, dmu ? c->T2 : nullptr,
                                                        l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
@@ -606,7 +776,7 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
         dmg_status st = iterate(c, false, c->p.fixed_cycles, info, s);
         if (st != DMG_OK && st != DMG_ENOCONV) return st;
         TRY(stage_out(c, l.u, du, s));
-        CUDA_TRY(c, cudaStreamSynchronize(s));
+        TRY(end_call(c, s));
         return st;
     });
 }
@@ -620,13 +790,12 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
         info_reset(info);
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
-        TRY(stage_in(c, w, l.f, s));
+        TRY(stage_in(c, w, l.f, false, s));
         dmg_status st = iterate(c, true, cycles, info, s);
         if (st != DMG_OK && st != DMG_ENOCONV) return st;
         if (qbar) TRY(stage_out(c, l.u, qbar, s));
         if (Dbar || mubar) {
-            TRY(stage_in(c, u, c->U0, s));
-            TRY(zero_boundary(c, c->U0, s));
+            TRY(stage_in(c, u, c->U0, true, s));
             double ih2 = 1.0 / (l.h * l.h);
             {
                 ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
@@ -638,7 +807,7 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
             if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
             if (mubar) TRY(stage_out(c, c->T2, mubar, s));
         }
-        CUDA_TRY(c, cudaStreamSynchronize(s));
+        TRY(end_call(c, s));
         return st;
     });
 }
@@ -648,10 +817,9 @@ dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *ou
         if (!q || !u || !out) return fail(c, DMG_EINVAL, "q, u and out must not be NULL");
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
-        TRY(stage_in(c, q, c->T3, s));
-        TRY(stage_in(c, u, c->U0, s));
-        TRY(zero_boundary(c, c->U0, s));
-        TRY(resid_norm_async(c, c->U0, c->T3, nullptr, 0.0, 0, s));
+        TRY(stage_in(c, q, c->T3, false, s));
+        TRY(stage_in(c, u, c->U0, true, s));
+        TRY(resid_norm_async(c, c->U0, c->T3, nullptr, 0, s));
         TRY(norm2_async(c, c->T3, 1, s));
         double r[2];
         TRY(finish_reduce(c, 2, s, r));
@@ -664,6 +832,9 @@ dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *ou
 
 dmg_status dmg_destroy(dmg_ctx *c) {
     if (!c) return DMG_OK;
+    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
+    graphs_reset(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (void *q : c->dev_allocs) cudaFree(q);
     if (c->hred) cudaFreeHost(c->hred);
@@ -703,30 +874,35 @@ unsigned long long dmg_launch_count(const dmg_ctx *c) { return c ? c->launches :
 
 dmg_status dmg_profile_begin(dmg_ctx *c, int kernel, int level, int precision_fp32, int max_launches) {
     if (!c || max_launches < 1 || level < 0 || level >= c->nlev) return DMG_EINVAL;
+    CUDA_TRY(c, cudaDeviceSynchronize());
+    graphs_reset(c);   // graphs are re-captured with event nodes
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.assign(2 * (size_t)max_launches, nullptr);
     for (auto &e : c->prof_ev) CUDA_TRY(c, cudaEventCreate(&e));
+    c->prof_free.clear();
+    for (int i = max_launches - 1; i >= 0; i--) c->prof_free.push_back(i);
+    c->prof_direct.clear();
     c->prof_kernel = kernel;
     c->prof_level = level;
     c->prof_fp32 = precision_fp32 ? 1 : 0;
-    c->prof_max = max_launches;
-    c->prof_n = 0;
+    c->prof_count = 0;
+    c->prof_ms = 0.0;
     return DMG_OK;
 }
 
 dmg_status dmg_profile_end(dmg_ctx *c, long long *launches, double *total_ms) {
     if (!c) return DMG_EINVAL;
-    double tot = 0.0;
-    for (int i = 0; i < c->prof_n; i++) {
-        CUDA_TRY(c, cudaEventSynchronize(c->prof_ev[2 * i + 1]));
-        float ms = 0.f;
-        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
-        tot += ms;
-    }
-    if (launches) *launches = c->prof_n;
-    if (total_ms) *total_ms = tot;
+    CUDA_TRY(c, cudaDeviceSynchronize());
+    prof_harvest(c, c->prof_direct, true);
+    if (launches) *launches = c->prof_count;
+    if (total_ms) *total_ms = c->prof_ms;
     c->prof_kernel = -1;
-    c->prof_n = 0;
+    graphs_reset(c);   // drop the event nodes
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_free.clear();
+    c->prof_count = 0;
+    c->prof_ms = 0.0;
     return DMG_OK;
 }
 

@@ -2,10 +2,15 @@
 // (arXiv 2608.00760, Eq. 1), templated on the arithmetic type (double for the
 // FP64 path, float for the inner V-cycles of mixed-precision refinement).
 //
-// Layout: every field is a padded C-order array [nz][ny][sy] (sy >= nx, a
-// multiple of 32 elements, so every row starts on a 256-byte boundary in FP64);
-// element (i, j, k) is at k*sz + j*sy + i with sz = ny*sy. Values on boundary
-// vertices of u, f and r are zero and no kernel writes them.
+// Layout (red-black split rows): every field is an array [nz][ny][sy] whose rows
+// hold the even-x vertices in their first half (index i/2) and the odd-x
+// vertices in their second half (index hx + i/2), hx a multiple of 32 elements.
+// A Red-Black Gauss-Seidel half-sweep updates one colour, which in each row is
+// one parity of x: it reads contiguous runs of its own colour and of the other
+// colour, so every sector it touches is fully used. Neighbours along y and z
+// keep the parity of x (same half, same index); neighbours along x sit in the
+// other half (offsets xm/xp below). Boundary values of u, f and r are zero and
+// no kernel writes them.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -14,32 +19,60 @@ namespace dmgk {
 
 struct Geom {
     int nx, ny, nz;   // vertices per axis, boundary included
-    int sy;           // row pitch in elements
-    long long sz;     // plane pitch in elements
-    __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
-        return (long long)k * sz + (long long)j * sy + i;
+    int hx;           // half-row length (elements)
+    int sy;           // row pitch = 2 hx
+    long long sz;     // plane pitch = ny sy
+    __host__ __device__ __forceinline__ long long pos(int i, int j, int k) const {
+        return (long long)k * sz + (long long)j * sy + (i & 1) * hx + (i >> 1);
     }
+    // offsets of the x-neighbours of vertex i relative to pos(i)
+    __host__ __device__ __forceinline__ int xm(int i) const { return (i & 1) ? -hx : hx - 1; }
+    __host__ __device__ __forceinline__ int xp(int i) const { return (i & 1) ? 1 - hx : hx; }
+    // number of x positions of one parity: even i = 0..nx-1 -> (nx+1)/2
+    __host__ __device__ __forceinline__ int nhalf() const { return (nx + 1) / 2; }
 };
+
+// Thread mapping shared by the per-vertex kernels: blockIdx.x = 2*b + parity,
+// threadIdx.x (32 wide) walks the half-row index m, so i = 2m + parity and a
+// warp touches 32 consecutive elements of one half.
+__device__ __forceinline__ int vertex_i() {
+    int par = blockIdx.x & 1;
+    int m = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
+    return 2 * m + par;
+}
 
 // ---------------------------------------------------------------------------
 // Coefficient access. The 7-point operator (Eq. 1, second-order differences)
 //   (A u)_p = sum_{j in nbr(p)} a_pj (u_p - u_j) + mu_p u_p,  a_pj = face(D_p, D_j) / h^2
-// is read either from precomputed faces (FP64: the couplings a and 1/diag are
-// stored, which keeps the FP64 ALU work per point at 6 FMA + 1 MUL) or from
-// vertex values (FP32: the faces are formed on the fly, which halves the bytes
-// of this memory-bound path).
+// is read either from precomputed faces (FP64: couplings and 1/diag are
+// stored, which keeps the FP64 pipe work per point at 6 FMA + 1 MUL) or from
+// vertex values (FP32: faces formed on the fly, fewer bytes on the HBM-bound
+// path). Neighbour order: -x, +x, -y, +y, -z, +z.
+
+struct Nbr {
+    long long o[6];   // position offsets of the six neighbours
+};
+
+__device__ __forceinline__ Nbr neighbours(const Geom &g, int i) {
+    Nbr n;
+    n.o[0] = g.xm(i); n.o[1] = g.xp(i);
+    n.o[2] = -(long long)g.sy; n.o[3] = g.sy;
+    n.o[4] = -g.sz; n.o[5] = g.sz;
+    return n;
+}
 
 template <class T>
 struct FaceCoef {
-    const T *cx, *cy, *cz;   // a between p and p+x, p+y, p+z
+    const T *cx, *cy, *cz;   // a between p and p+x, p+y, p+z, stored at p
     const T *diag, *invd;    // diagonal and its reciprocal (0 on the boundary)
-    __device__ __forceinline__ void couplings(long long p, int sy, long long sz, T a[6]) const {
-        a[0] = __ldg(cx + p - 1);  a[1] = __ldg(cx + p);
-        a[2] = __ldg(cy + p - sy); a[3] = __ldg(cy + p);
-        a[4] = __ldg(cz + p - sz); a[5] = __ldg(cz + p);
+    __device__ __forceinline__ void couplings(long long p, const Nbr &n, T a[6]) const {
+        a[0] = __ldg(cx + p + n.o[0]); a[1] = __ldg(cx + p);
+        a[2] = __ldg(cy + p + n.o[2]); a[3] = __ldg(cy + p);
+        a[4] = __ldg(cz + p + n.o[4]); a[5] = __ldg(cz + p);
     }
     __device__ __forceinline__ T get_diag(long long p, const T *) const { return __ldg(diag + p); }
-    __device__ __forceinline__ T inv_diag(long long p, const T *) const { return __ldg(invd + p); }
+    // (f + sum a u) / diag
+    __device__ __forceinline__ T finish(T s, long long p, const T *) const { return s * __ldg(invd + p); }
 };
 
 // Dh = D / (2 h^2) for the arithmetic face mean (face = Dh_p + Dh_j),
@@ -51,72 +84,175 @@ struct VertCoef {
         if (HARM) return T(2) * a * b / (a + b);
         return a + b;
     }
-    __device__ __forceinline__ void couplings(long long p, int sy, long long sz, T a[6]) const {
+    __device__ __forceinline__ void couplings(long long p, const Nbr &n, T a[6]) const {
         T d = __ldg(Dh + p);
-        a[0] = face(d, __ldg(Dh + p - 1));  a[1] = face(d, __ldg(Dh + p + 1));
-        a[2] = face(d, __ldg(Dh + p - sy)); a[3] = face(d, __ldg(Dh + p + sy));
-        a[4] = face(d, __ldg(Dh + p - sz)); a[5] = face(d, __ldg(Dh + p + sz));
+#pragma unroll
+        for (int q = 0; q < 6; q++) a[q] = face(d, __ldg(Dh + p + n.o[q]));
     }
     __device__ __forceinline__ T get_diag(long long p, const T *a) const {
         return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
     }
-    __device__ __forceinline__ T inv_diag(long long p, const T *a) const {
-        return T(1) / get_diag(p, a);
+    __device__ __forceinline__ T finish(T s, long long p, const T *a) const {
+        return __fdividef(s, get_diag(p, a));
     }
 };
+
+// s + sum_q a_q u(p + o_q). FP64: one FMA chain (6 FP64-pipe ops, the B300's
+// scarce resource); FP32: three independent pairs (shorter dependency chain).
+template <class T>
+__device__ __forceinline__ T coupled_sum(T s, const T *__restrict__ u, long long p, const Nbr &n, const T *a) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int q = 0; q < 6; q++) s = fma(a[q], u[p + n.o[q]], s);
+        return s;
+    } else {
+        T s0 = fma(a[0], u[p + n.o[0]], s);
+        T s1 = a[2] * u[p + n.o[2]];
+        T s2 = a[4] * u[p + n.o[4]];
+        s0 = fma(a[1], u[p + n.o[1]], s0);
+        s1 = fma(a[3], u[p + n.o[3]], s1);
+        s2 = fma(a[5], u[p + n.o[5]], s2);
+        return (s0 + s1) + s2;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Red-Black Gauss-Seidel half-sweep (Eq. 9): every interior vertex of colour
 // (i+j+k) mod 2 == color takes u_p = (f_p + sum_j a_pj u_j) / diag_p. Vertices
-// of one colour are not coupled, so the update is in place and race-free.
-// Thread layout: x covers the vertices of the colour in a row (every other i).
+// of one colour are not coupled, so the update is in place and race-free. In a
+// row (j, k) the colour is one parity of i, i.e. one contiguous half-row.
+// Each thread updates RPT vertices (rows j, j + blockDim.y, ...), issuing all
+// their loads before any store so that they are in flight together.
+constexpr int kRowsPerThread = 1;
+
 template <class T, class C>
-__global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u,
-                                                     const T *__restrict__ f, C c, int color) {
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (j > g.ny - 2) return;
-    int i = 1 + ((1 + j + k + color) & 1) + 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (i > g.nx - 2) return;
-    long long p = g.at(i, j, k);
-    T a[6];
-    c.couplings(p, g.sy, g.sz, a);
-    T s = __ldg(f + p);
-    s = fma(a[0], u[p - 1], s);
-    s = fma(a[1], u[p + 1], s);
-    s = fma(a[2], u[p - g.sy], s);
-    s = fma(a[3], u[p + g.sy], s);
-    s = fma(a[4], u[p - g.sz], s);
-    s = fma(a[5], u[p + g.sz], s);
-    u[p] = s * c.inv_diag(p, a);
+__global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, const T *__restrict__ f,
+                                                     C c, int color) {
+    constexpr int RPT = kRowsPerThread;
+    const int k = blockIdx.z + 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = blockIdx.y * (blockDim.y * RPT) + threadIdx.y + 1;
+    long long p[RPT];
+    bool on[RPT];
+    T s[RPT], a[RPT][6];
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+        const int j = j0 + r * blockDim.y;
+        const int par = (color + j + k) & 1;               // parity of i of this colour in this row
+        const int i = 2 * t + 2 - par;                     // 1, 3, ... or 2, 4, ...
+        on[r] = j <= g.ny - 2 && i <= g.nx - 2;
+        if (on[r]) {
+            p[r] = g.pos(i, j, k);
+            const Nbr n = neighbours(g, i);
+            c.couplings(p[r], n, a[r]);
+            s[r] = coupled_sum(__ldg(f + p[r]), u, p[r], n, a[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; r++)
+        if (on[r]) u[p[r]] = c.finish(s[r], p[r], a[r]);
+}
+
+// FP32 half-sweep with vertex coefficients, four vertices per thread. In row
+// (j, k) the colour's vertices are half-row indices m = M_lo..M_hi of one half;
+// a thread takes m = 4t..4t+3, so its own f, mu, D and its y/z neighbours
+// (same half, same m) are single float4 loads, and its x neighbours are the
+// other half's indices 4t..4t+3 plus one value beyond either end, taken from
+// the adjacent lane by a shuffle (or loaded by lanes 0 and 31). Requires hx to
+// be a multiple of 4 (it is a multiple of 32).
+template <bool HARM>
+__global__ void __launch_bounds__(256) k_smooth_half_v4(Geom g, float *__restrict__ u, const float *__restrict__ f,
+                                                        VertCoef<float, HARM> c, int color) {
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool jin = j <= g.ny - 2;
+    const int jj = jin ? j : g.ny - 2;                   // keep whole warps in the shuffles
+    const int par = (color + jj + k) & 1;
+    const long long row = (long long)k * g.sz + (long long)jj * g.sy;
+    const long long ob = row + par * g.hx + 4 * t;       // own half, m = 4t
+    const long long tb = row + (1 - par) * g.hx + 4 * t; // other half, index 4t
+    const bool tin = 4 * t < g.hx;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [&](const float *a, long long q) { return tin ? __ldg(reinterpret_cast<const float4 *>(a + q)) : z4; };
+    // every load is issued before the first use (shuffles, early exits), so a
+    // thread has all 13 vector loads in flight at once
+    const float4 uo = ld(u, tb), dox = ld(c.Dh, tb);
+    const float4 dc = ld(c.Dh, ob), f4 = ld(f, ob), m4 = ld(c.mu, ob);
+    const float4 dym = ld(c.Dh, ob - g.sy), dyp = ld(c.Dh, ob + g.sy);
+    const float4 dzm = ld(c.Dh, ob - g.sz), dzp = ld(c.Dh, ob + g.sz);
+    const float4 uym = ld(u, ob - g.sy), uyp = ld(u, ob + g.sy);
+    const float4 uzm = ld(u, ob - g.sz), uzp = ld(u, ob + g.sz);
+    const bool ok0 = lane == 0 && tin && 4 * t >= 1, ok31 = lane == 31 && tin && 4 * t + 4 < g.hx;
+    const float u_prev0 = ok0 ? __ldg(u + tb - 1) : 0.f, d_prev0 = ok0 ? __ldg(c.Dh + tb - 1) : 0.f;
+    const float u_next31 = ok31 ? __ldg(u + tb + 4) : 0.f, d_next31 = ok31 ? __ldg(c.Dh + tb + 4) : 0.f;
+    // values at other-half indices 4t-1 (for even parity) and 4t+4 (odd parity)
+    float u_prev = __shfl_up_sync(0xffffffffu, uo.w, 1), d_prev = __shfl_up_sync(0xffffffffu, dox.w, 1);
+    float u_next = __shfl_down_sync(0xffffffffu, uo.x, 1), d_next = __shfl_down_sync(0xffffffffu, dox.x, 1);
+    if (lane == 0) { u_prev = u_prev0; d_prev = d_prev0; }
+    if (lane == 31) { u_next = u_next31; d_next = d_next31; }
+    const int M_lo = 1 - par, M_hi = par ? (g.nx - 3) / 2 : (g.nx - 2) / 2;
+    if (!jin || !tin || 4 * t > M_hi) return;
+    const float U[6] = {u_prev, uo.x, uo.y, uo.z, uo.w, u_next};   // other half, indices 4t-1 .. 4t+4
+    const float DX[6] = {d_prev, dox.x, dox.y, dox.z, dox.w, d_next};
+    const float DC[4] = {dc.x, dc.y, dc.z, dc.w}, F[4] = {f4.x, f4.y, f4.z, f4.w}, MU[4] = {m4.x, m4.y, m4.z, m4.w};
+    const float DYM[4] = {dym.x, dym.y, dym.z, dym.w}, DYP[4] = {dyp.x, dyp.y, dyp.z, dyp.w};
+    const float DZM[4] = {dzm.x, dzm.y, dzm.z, dzm.w}, DZP[4] = {dzp.x, dzp.y, dzp.z, dzp.w};
+    const float UYM[4] = {uym.x, uym.y, uym.z, uym.w}, UYP[4] = {uyp.x, uyp.y, uyp.z, uyp.w};
+    const float UZM[4] = {uzm.x, uzm.y, uzm.z, uzm.w}, UZP[4] = {uzp.x, uzp.y, uzp.z, uzp.w};
+    float out[4];
+    bool ok[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int m = 4 * t + q;
+        ok[q] = m >= M_lo && m <= M_hi;
+        // x-1 / x+1 neighbours: other-half indices m-1, m (even parity) or m, m+1 (odd);
+        // U[q + 1] holds index m
+        const float ul = par ? U[q + 1] : U[q], ur = par ? U[q + 2] : U[q + 1];
+        const float dl = par ? DX[q + 1] : DX[q], dr = par ? DX[q + 2] : DX[q + 1];
+        const float d = DC[q];
+        const float a0 = VertCoef<float, HARM>::face(d, dl), a1 = VertCoef<float, HARM>::face(d, dr);
+        const float a2 = VertCoef<float, HARM>::face(d, DYM[q]), a3 = VertCoef<float, HARM>::face(d, DYP[q]);
+        const float a4 = VertCoef<float, HARM>::face(d, DZM[q]), a5 = VertCoef<float, HARM>::face(d, DZP[q]);
+        float s0 = fmaf(a0, ul, F[q]);
+        float s1 = a2 * UYM[q];
+        float s2 = a4 * UZM[q];
+        s0 = fmaf(a1, ur, s0);
+        s1 = fmaf(a3, UYP[q], s1);
+        s2 = fmaf(a5, UZP[q], s2);
+        const float dg = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + MU[q]);
+        out[q] = __fdividef((s0 + s1) + s2, dg);
+    }
+    if (ok[0] && ok[1] && ok[2] && ok[3]) {
+        *reinterpret_cast<float4 *>(u + ob) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (ok[q]) u[ob + q] = out[q];
+    }
 }
 
 // residual value at an interior vertex: f_p - diag_p u_p + sum_j a_pj u_j
 template <class T, class C>
-__device__ __forceinline__ T residual_at(const Geom &g, const T *__restrict__ u,
-                                         const T *__restrict__ f, const C &c, long long p) {
+__device__ __forceinline__ T residual_at(const T *__restrict__ u, const T *__restrict__ f, const C &c,
+                                         long long p, const Nbr &n) {
     T a[6];
-    c.couplings(p, g.sy, g.sz, a);
+    c.couplings(p, n, a);
     T s = fma(-c.get_diag(p, a), __ldg(u + p), __ldg(f + p));
-    s = fma(a[0], __ldg(u + p - 1), s);
-    s = fma(a[1], __ldg(u + p + 1), s);
-    s = fma(a[2], __ldg(u + p - g.sy), s);
-    s = fma(a[3], __ldg(u + p + g.sy), s);
-    s = fma(a[4], __ldg(u + p - g.sz), s);
-    s = fma(a[5], __ldg(u + p + g.sz), s);
-    return s;
+    return coupled_sum(s, u, p, n, a);
 }
 
 // r = f - A u on interior vertices (the defect, Eqs. 13-14)
 template <class T, class C>
-__global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ u,
-                                                  const T *__restrict__ f, C c, T *__restrict__ r) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+__global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ u, const T *__restrict__ f,
+                                                  C c, T *__restrict__ r) {
+    int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.at(i, j, k);
-    r[p] = residual_at(g, u, f, c, p);
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    long long p = g.pos(i, j, k);
+    r[p] = residual_at(u, f, c, p, neighbours(g, i));
 }
 
 // Full-weighting restriction (Eq. 7, 1/4[1 2 1] per axis) of a fine field onto
@@ -124,11 +260,12 @@ __global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ 
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__ r, Geom gc,
                                                   T *__restrict__ fc) {
-    int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int I = vertex_i();
     int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int K = blockIdx.z + 1;
-    if (I > gc.nx - 2 || J > gc.ny - 2) return;
-    long long p = gf.at(2 * I, 2 * J, 2 * K);
+    if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
+    long long p = gf.pos(2 * I, 2 * J, 2 * K);
+    const int om = gf.xm(2 * I), op = gf.xp(2 * I);
     T s = T(0);
 #pragma unroll
     for (int c = -1; c <= 1; c++) {
@@ -136,39 +273,61 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
 #pragma unroll
         for (int b = -1; b <= 1; b++) {
             long long q = p + c * gf.sz + b * gf.sy;
-            T row = __ldg(r + q - 1) + T(2) * __ldg(r + q) + __ldg(r + q + 1);
+            T row = __ldg(r + q + om) + T(2) * __ldg(r + q) + __ldg(r + q + op);
             sp += (b == 0 ? T(2) : T(1)) * row;
         }
         s += (c == 0 ? T(2) : T(1)) * sp;
     }
-    fc[gc.at(I, J, K)] = s * T(1.0 / 64.0);
+    fc[gc.pos(I, J, K)] = s * T(1.0 / 64.0);
 }
 
 // Prolongation I = 2^3 R^T (Eq. 17) and correction: u_fine += trilinear(e)
-// on fine interior vertices. e is zero on the coarse boundary.
+// on fine interior vertices; e is zero on the coarse boundary. One thread per
+// coarse cell (I..I+1, J..J+1, K..K+1): it loads the 8 corner values once and
+// corrects the fine vertices (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, with the
+// trilinear weights (1 at a coincident vertex, 1/2 per axis at a midpoint).
+// In the split layout fine x = 2I and 2I+1 are index I of the even and odd
+// halves, so both stay contiguous across a warp.
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf,
                                                      T *__restrict__ u) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (i > gf.nx - 2 || j > gf.ny - 2) return;
-    int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    int ni = (i & 1) + 1, nj = (j & 1) + 1, nk = (k & 1) + 1;
-    T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
-    T s = T(0);
-    for (int c = 0; c < nk; c++) {
-        T sj = T(0);
-        for (int b = 0; b < nj; b++) {
-            long long q = gc.at(i0, j0 + b, k0 + c);
-            T si = __ldg(e + q);
-            if (ni == 2) si += __ldg(e + q + 1);
-            sj += si;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    T c[2][2][2];
+#pragma unroll
+    for (int z = 0; z < 2; z++)
+#pragma unroll
+        for (int y = 0; y < 2; y++)
+#pragma unroll
+            for (int x = 0; x < 2; x++) c[z][y][x] = __ldg(e + gc.pos(I + x, J + y, K + z));
+    // interpolate along x, then y, then z: v[c][b][a] at fine (2I+a, 2J+b, 2K+c)
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++) {
+        const int k = 2 * K + cz;
+        if (k < 1 || k > gf.nz - 2) continue;
+#pragma unroll
+        for (int by = 0; by < 2; by++) {
+            const int j = 2 * J + by;
+            if (j < 1 || j > gf.ny - 2) continue;
+            T row[2];
+#pragma unroll
+            for (int x = 0; x < 2; x++) {
+                T lo = by ? T(0.5) * (c[0][0][x] + c[0][1][x]) : c[0][0][x];
+                T hi = by ? T(0.5) * (c[1][0][x] + c[1][1][x]) : c[1][0][x];
+                row[x] = cz ? T(0.5) * (lo + hi) : lo;
+            }
+            if (2 * I >= 1) {
+                const long long p = gf.pos(2 * I, j, k);
+                u[p] += row[0];
+            }
+            if (2 * I + 1 <= gf.nx - 2) {
+                const long long p = gf.pos(2 * I + 1, j, k);
+                u[p] += T(0.5) * (row[0] + row[1]);
+            }
         }
-        s += sj;
     }
-    long long p = gf.at(i, j, k);
-    u[p] += (wi * wj * wk) * s;
 }
 
 // Exact coarsest-level solve u = A^{-1} f with the symmetric inverse built at
@@ -181,44 +340,79 @@ __global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const 
     int nxi = g.nx - 2, nyi = g.ny - 2;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         int i = c % nxi + 1, j = (c / nxi) % nyi + 1, k = c / (nxi * nyi) + 1;
-        fs[c] = f[g.at(i, j, k)];
+        fs[c] = f[g.pos(i, j, k)];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         T s = T(0);
         for (int c = 0; c < n; c++) s = fma(Ainv[(long long)r * n + c], fs[c], s);
         int i = r % nxi + 1, j = (r / nxi) % nyi + 1, k = r / (nxi * nyi) + 1;
-        u[g.at(i, j, k)] = s;
+        u[g.pos(i, j, k)] = s;
     }
 }
 
 // ---------------------------------------------------------------------------
-// setup kernels
+// layout conversion between the caller's contiguous [nz][ny][nx] arrays and the
+// split level-0 layout (one thread per vertex, coalesced on the contiguous side)
+
+// dst = src on every vertex, or on interior vertices only with zeros on the
+// boundary (zero_boundary != 0)
+__global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict__ src,
+                                                double *__restrict__ dst, int zero_boundary) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long n = (long long)g.nx * g.ny * g.nz;
+    if (t >= n) return;
+    int i = (int)(t % g.nx);
+    long long r = t / g.nx;
+    int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    double v = src[t];
+    if (zero_boundary && (i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1))
+        v = 0.0;
+    dst[g.pos(i, j, k)] = v;
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Geom g, const double *__restrict__ src,
+                                                 double *__restrict__ dst) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long n = (long long)g.nx * g.ny * g.nz;
+    if (t >= n) return;
+    int i = (int)(t % g.nx);
+    long long r = t / g.nx;
+    int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    dst[t] = src[g.pos(i, j, k)];
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels (one thread per vertex, boundary included)
+
+__device__ __forceinline__ bool vertex_ijk(const Geom &g, int &i, int &j, int &k) {
+    i = vertex_i();
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    k = blockIdx.z;
+    return i < g.nx && j < g.ny;
+}
 
 // Coefficient coarsening for the rediscretised coarse operator: full weighting
 // on coarse interior vertices, injection on the coarse boundary (or injection
-// everywhere). One thread per coarse vertex.
+// everywhere).
 __global__ void k_coarsen(Geom gf, const double *__restrict__ X, Geom gc, double *__restrict__ Xc,
                           int inject) {
-    int I = blockIdx.x * blockDim.x + threadIdx.x;
-    int J = blockIdx.y * blockDim.y + threadIdx.y;
-    int K = blockIdx.z;
-    if (I >= gc.nx || J >= gc.ny) return;
-    long long p = gf.at(2 * I, 2 * J, 2 * K);
+    int I, J, K;
+    if (!vertex_ijk(gc, I, J, K)) return;
     bool interior = I > 0 && J > 0 && K > 0 && I < gc.nx - 1 && J < gc.ny - 1 && K < gc.nz - 1;
     double s;
     if (inject || !interior) {
-        s = X[p];
+        s = X[gf.pos(2 * I, 2 * J, 2 * K)];
     } else {
         s = 0.0;
         for (int c = -1; c <= 1; c++)
             for (int b = -1; b <= 1; b++)
                 for (int a = -1; a <= 1; a++) {
                     double w = (a == 0 ? 0.5 : 0.25) * (b == 0 ? 0.5 : 0.25) * (c == 0 ? 0.5 : 0.25);
-                    s += w * X[p + c * gf.sz + b * gf.sy + a];
+                    s += w * X[gf.pos(2 * I + a, 2 * J + b, 2 * K + c)];
                 }
     }
-    Xc[gc.at(I, J, K)] = s;
+    Xc[gc.pos(I, J, K)] = s;
 }
 
 __device__ __forceinline__ double face_mean(double a, double b, int harm) {
@@ -226,22 +420,19 @@ __device__ __forceinline__ double face_mean(double a, double b, int harm) {
 }
 
 // FP64 face couplings a = face(D_p, D_j)/h^2 (stored at the lower vertex of each
-// face), diagonal and its reciprocal. One thread per vertex.
-__global__ void k_build_faces(Geom g, const double *__restrict__ D, const double *__restrict__ mu,
-                              double ih2, int harm, double *cx, double *cy, double *cz,
-                              double *diag, double *invd) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    long long p = g.at(i, j, k);
+// face), diagonal and its reciprocal.
+__global__ void k_build_faces(Geom g, const double *__restrict__ D, const double *__restrict__ mu, double ih2,
+                              int harm, double *cx, double *cy, double *cz, double *diag, double *invd) {
+    int i, j, k;
+    if (!vertex_ijk(g, i, j, k)) return;
+    long long p = g.pos(i, j, k);
     double d = D[p];
-    cx[p] = i < g.nx - 1 ? face_mean(d, D[p + 1], harm) * ih2 : 0.0;
+    cx[p] = i < g.nx - 1 ? face_mean(d, D[p + g.xp(i)], harm) * ih2 : 0.0;
     cy[p] = j < g.ny - 1 ? face_mean(d, D[p + g.sy], harm) * ih2 : 0.0;
     cz[p] = k < g.nz - 1 ? face_mean(d, D[p + g.sz], harm) * ih2 : 0.0;
     bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
     if (interior) {
-        double s = face_mean(d, D[p - 1], harm) + face_mean(d, D[p + 1], harm) +
+        double s = face_mean(d, D[p + g.xm(i)], harm) + face_mean(d, D[p + g.xp(i)], harm) +
                    face_mean(d, D[p - g.sy], harm) + face_mean(d, D[p + g.sy], harm) +
                    face_mean(d, D[p - g.sz], harm) + face_mean(d, D[p + g.sz], harm);
         double dg = s * ih2 + mu[p];
@@ -254,13 +445,11 @@ __global__ void k_build_faces(Geom g, const double *__restrict__ D, const double
 }
 
 // FP32 vertex coefficients for the inner V-cycles: Dh = D * scale, mu32 = mu.
-__global__ void k_build_vertex32(Geom g, const double *__restrict__ D, const double *__restrict__ mu,
-                                 double scale, float *Dh, float *mu32) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    long long p = g.at(i, j, k);
+__global__ void k_build_vertex32(Geom g, const double *__restrict__ D, const double *__restrict__ mu, double scale,
+                                 float *Dh, float *mu32) {
+    int i, j, k;
+    if (!vertex_ijk(g, i, j, k)) return;
+    long long p = g.pos(i, j, k);
     Dh[p] = (float)(D[p] * scale);
     mu32[p] = (float)mu[p];
 }
@@ -278,10 +467,10 @@ __global__ void k_coarse_assemble(Geom g, FaceCoef<double> c, int n, double *M) 
         } else {
             int ri = r % nxi + 1, rj = (r / nxi) % nyi + 1, rk = r / (nxi * nyi) + 1;
             int ci = col % nxi + 1, cj = (col / nxi) % nyi + 1, ck = col / (nxi * nyi) + 1;
-            long long p = g.at(ri, rj, rk);
+            long long p = g.pos(ri, rj, rk);
             int di = ci - ri, dj = cj - rj, dk = ck - rk;
             if (di == 0 && dj == 0 && dk == 0) v = c.diag[p];
-            else if (dj == 0 && dk == 0 && di == -1) v = -c.cx[p - 1];
+            else if (dj == 0 && dk == 0 && di == -1) v = -c.cx[p + g.xm(ri)];
             else if (dj == 0 && dk == 0 && di == 1) v = -c.cx[p];
             else if (di == 0 && dk == 0 && dj == -1) v = -c.cy[p - g.sy];
             else if (di == 0 && dk == 0 && dj == 1) v = -c.cy[p];
@@ -347,24 +536,101 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return s;  // valid in thread 0
 }
 
+// interior vertex t (x fastest) of a grid-stride loop
+__device__ __forceinline__ void interior_ijk(unsigned t, int nxi, int nyi, int &i, int &j, int &k) {
+    unsigned rest = t / nxi;
+    i = (int)(t - rest * nxi) + 1;
+    unsigned kk = rest / nyi;
+    j = (int)(rest - kk * nyi) + 1;
+    k = (int)kk + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision refinement helpers. On this GPU conversions between float
+// and double run on the same scarce pipe as FP64 arithmetic, so the FP32
+// right-hand side r * 2^-e and the FP64 correction e32 * 2^e are formed on the
+// integer pipe from the IEEE-754 bit patterns (a power-of-two scale is an
+// exponent shift, exact for normal numbers).
+
+// device-resident scalars of one refinement loop: the FP32 right-hand side
+// holds r * 2^-e_cur; e_prev is the binary exponent of the latest residual norm
+struct MixScalars {
+    int e_cur;
+    int e_prev;
+};
+
+// floor(log2(x)) of a positive normal double from its exponent field (0 for 0)
+__device__ __forceinline__ int exponent_of(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff);
+    return e == 0 ? 0 : e - 1023;
+}
+
+// (float)(x * 2^shift) with round-to-nearest-even on the dropped mantissa bits.
+// Results below the float normal range flush to zero (sign kept), results above
+// it saturate to +-FLT_MAX; NaN/Inf inputs saturate too (the FP64 norm, which
+// is computed from the unconverted value, reports them).
+__device__ __forceinline__ float f64_to_f32_shift(double x, int shift) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned sign = (unsigned)(b >> 63) << 31;
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return __uint_as_float(sign);
+    int fe = e - 1023 + 127 + shift;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255 || e == 0x7ff) return __uint_as_float(sign | 0x7f7fffffu);
+    unsigned long long m = b & 0xfffffffffffffULL;          // 52 mantissa bits
+    unsigned keep = (unsigned)(m >> 29);                     // 23 kept bits
+    unsigned rem = (unsigned)(m & 0x1fffffffULL);            // 29 dropped bits
+    unsigned bits = ((unsigned)fe << 23) | keep;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) bits += 1u;  // carry may raise the exponent
+    if (bits >= 0x7f800000u) bits = 0x7f7fffffu;
+    return __uint_as_float(sign | bits);
+}
+
+// (double)x * 2^shift, exact for normal x; zero and subnormal x give zero,
+// Inf/NaN give NaN.
+__device__ __forceinline__ double f32_to_f64_shift(float x, int shift) {
+    unsigned b = __float_as_uint(x);
+    unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    int e = (int)((b >> 23) & 0xff);
+    if (e == 0) return __longlong_as_double((long long)sign);
+    if (e == 0xff) return __longlong_as_double((long long)0x7ff8000000000000ULL);
+    unsigned long long de = (unsigned long long)(e - 127 + 1023 + shift);
+    unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sign | (de << 52) | m));
+}
+
+// ms from the first norm: the FP32 right-hand side will be f * 2^-e(||f||)
+__global__ void k_mix_init(const double *red, int slot, MixScalars *ms) {
+    int e = exponent_of(sqrt(red[slot]));
+    ms->e_cur = e;
+    ms->e_prev = e;
+}
+
+// after a refinement step: the new FP32 right-hand side carries 2^-e_prev
+__global__ void k_mix_next(const double *red, int slot, MixScalars *ms) {
+    ms->e_cur = ms->e_prev;
+    ms->e_prev = exponent_of(sqrt(red[slot]));
+}
+
 // partial[b] = sum over this block's interior vertices of (f - A u)^2; optional
-// outputs: r (same type) and r32 = (float)(r * r32_scale).
+// outputs: r (same type) and the FP32 right-hand side r32 = r * 2^-ms->e_prev.
 template <class T, class C>
-__global__ void __launch_bounds__(256) k_resid_norm(Geom g, const T *__restrict__ u,
-                                                    const T *__restrict__ f, C c,
-                                                    T *__restrict__ rout, float *__restrict__ r32,
-                                                    double r32_scale, double *partial) {
+__global__ void __launch_bounds__(256) k_resid_norm(Geom g, const T *__restrict__ u, const T *__restrict__ f,
+                                                    C c, T *__restrict__ rout, float *__restrict__ r32,
+                                                    const MixScalars *ms, double *partial) {
     __shared__ double sh[8];
     int nxi = g.nx - 2, nyi = g.ny - 2, nzi = g.nz - 2;
     unsigned total = (unsigned)nxi * nyi * nzi;
+    int shift = r32 ? -ms->e_prev : 0;
     double acc = 0.0;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        unsigned i = t % nxi, rest = t / nxi;
-        unsigned j = rest % nyi, k = rest / nyi;
-        long long p = g.at(i + 1, j + 1, k + 1);
-        T r = residual_at(g, u, f, c, p);
+        int i, j, k;
+        interior_ijk(t, nxi, nyi, i, j, k);
+        long long p = g.pos(i, j, k);
+        T r = residual_at(u, f, c, p, neighbours(g, i));
         if (rout) rout[p] = r;
-        if (r32) r32[p] = (float)((double)r * r32_scale);
+        if (r32) r32[p] = f64_to_f32_shift((double)r, shift);
         acc = fma((double)r, (double)r, acc);
     }
     double s = block_sum(acc, sh);
@@ -378,9 +644,9 @@ __global__ void __launch_bounds__(256) k_norm2(Geom g, const double *__restrict_
     unsigned total = (unsigned)nxi * nyi * nzi;
     double acc = 0.0;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        unsigned i = t % nxi, rest = t / nxi;
-        unsigned j = rest % nyi, k = rest / nyi;
-        double v = x[g.at(i + 1, j + 1, k + 1)];
+        int i, j, k;
+        interior_ijk(t, nxi, nyi, i, j, k);
+        double v = x[g.pos(i, j, k)];
         acc = fma(v, v, acc);
     }
     double s = block_sum(acc, sh);
@@ -408,25 +674,23 @@ __device__ __forceinline__ double face_da(double a, double b, int harm) {
 //   mubar_v = -lam_v u_v   (0 on the boundary)
 // u and lam are zero on boundary vertices.
 __global__ void __launch_bounds__(256) k_grad(Geom g, const double *__restrict__ u,
-                                              const double *__restrict__ lam,
-                                              const double *__restrict__ D, double ih2, int harm,
-                                              double *__restrict__ Dbar, double *__restrict__ mubar) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    long long p = g.at(i, j, k);
+                                              const double *__restrict__ lam, const double *__restrict__ D,
+                                              double ih2, int harm, double *__restrict__ Dbar,
+                                              double *__restrict__ mubar) {
+    int i, j, k;
+    if (!vertex_ijk(g, i, j, k)) return;
+    long long p = g.pos(i, j, k);
     double uv = u[p], lv = lam[p];
     double dv = harm ? D[p] : 0.0;
     double s = 0.0;
-    long long off[6] = {-1, 1, -(long long)g.sy, (long long)g.sy, -g.sz, g.sz};
+    Nbr n = neighbours(g, i);
     bool ok[6] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1, k > 0, k < g.nz - 1};
 #pragma unroll
-    for (int n = 0; n < 6; n++) {
-        if (!ok[n]) continue;
-        long long q = p + off[n];
-        double w = harm ? face_da(dv, D[q], 1) : 0.5;
-        s = fma(w * (lv - lam[q]), uv - u[q], s);
+    for (int q = 0; q < 6; q++) {
+        if (!ok[q]) continue;
+        long long r = p + n.o[q];
+        double w = harm ? face_da(dv, D[r], 1) : 0.5;
+        s = fma(w * (lv - lam[r]), uv - u[r], s);
     }
     if (Dbar) Dbar[p] = -s * ih2;
     if (mubar) mubar[p] = -lv * uv;
@@ -434,52 +698,50 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, const double *__restrict__
 
 // f -= (dA) u on interior vertices: the derivative of the operator in the
 // direction (dD, dmu) applied to u (either tangent may be NULL).
-__global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u,
-                                            const double *__restrict__ dD,
-                                            const double *__restrict__ dmu,
-                                            const double *__restrict__ D, double ih2, int harm,
-                                            double *__restrict__ f) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+__global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u, const double *__restrict__ dD,
+                                            const double *__restrict__ dmu, const double *__restrict__ D,
+                                            double ih2, int harm, double *__restrict__ f) {
+    int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.at(i, j, k);
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    long long p = g.pos(i, j, k);
     double up = u[p];
     double s = 0.0;
     if (dD) {
-        long long off[6] = {-1, 1, -(long long)g.sy, (long long)g.sy, -g.sz, g.sz};
+        Nbr n = neighbours(g, i);
         double dp = D[p], ddp = dD[p];
 #pragma unroll
-        for (int n = 0; n < 6; n++) {
-            long long q = p + off[n];
-            double dface = face_da(dp, D[q], harm) * ddp + face_da(D[q], dp, harm) * dD[q];
-            s = fma(dface, up - u[q], s);
+        for (int q = 0; q < 6; q++) {
+            long long r = p + n.o[q];
+            double dface = face_da(dp, D[r], harm) * ddp + face_da(D[r], dp, harm) * dD[r];
+            s = fma(dface, up - u[r], s);
         }
     }
     double v = s * ih2 + (dmu ? dmu[p] * up : 0.0);
     f[p] -= v;
 }
 
-// mixed precision: u64 += s * e32 on interior vertices
-__global__ void __launch_bounds__(256) k_update(Geom g, double *__restrict__ u,
-                                                const float *__restrict__ e, double s) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+// mixed precision: u64 += e32 * 2^ms->e_cur on interior vertices (1 FP64 add)
+__global__ void __launch_bounds__(256) k_update(Geom g, double *__restrict__ u, const float *__restrict__ e,
+                                                const MixScalars *ms) {
+    int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.at(i, j, k);
-    u[p] = fma(s, (double)e[p], u[p]);
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    long long p = g.pos(i, j, k);
+    u[p] += f32_to_f64_shift(e[p], ms->e_cur);
 }
 
-// y = (float)(x * s) on interior vertices
-__global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict__ x, double s,
+// y = x * 2^-ms->e_cur in FP32 on interior vertices
+__global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict__ x, const MixScalars *ms,
                                                 float *__restrict__ y) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.at(i, j, k);
-    y[p] = (float)(x[p] * s);
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    long long p = g.pos(i, j, k);
+    y[p] = f64_to_f32_shift(x[p], -ms->e_cur);
 }
 
 }  // namespace dmgk

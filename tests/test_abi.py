@@ -41,7 +41,7 @@ def test_library_is_built_for_sm_103a(dmg):
 
 def test_default_params_and_strerror(dmg):
     p = dmg.dmg_default_params()
-    assert (p.nu1, p.nu2, p.max_cycles, p.rtol, p.precision, p.inner_cycles) == (2, 2, 100, 1e-10, 0, 1)
+    assert (p.nu1, p.nu2, p.max_cycles, p.rtol, p.precision, p.inner_cycles) == (2, 2, 100, 1e-10, 0, 3)
     assert dmg.dmg_strerror(dmg.DMG_OK) == "ok"
     assert dmg.dmg_strerror(dmg.DMG_ENOCONV) == "did not converge"
 

@@ -257,3 +257,44 @@ def test_tissue_129_converged(dmg):
     qbr, Dbr, mbr, _ = H.vjp(ur, w["w"], rtol=1e-10)
     for a, b in ((u, ur), (qb, qbr), (Db, Dbr), (mb, mbr)):
         assert rel(a, b) <= TOL_CONV
+
+
+FUSED_SHAPES = [(65, 65, 65), (33, 49, 97), (129, 33, 65), (17, 33, 161), (9, 9, 257)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+@pytest.mark.parametrize("face_mean", [0, 1])
+def test_fp32_vcycle_matches_fp64_vcycle(dmg, shape, face_mean):
+    # one mixed refinement step is s * V32(q / s); one FP64 cycle is V64(q). The FP32
+    # V-cycle (fused TMA sweeps on the wide levels, ragged tiles and z-chunks
+    # included) must be the same linear map up to FP32 rounding.
+    w = inputs.tissue(shape=shape, seed=8)
+    kw = dict(max_cycles=1, strict=False, face_mean=face_mean)
+    Sm = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=1, **kw)
+    S6 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_FP64, **kw)
+    for transposed in (False, True):
+        if transposed:
+            um, _, _ = Sm.vjp(None, T(w["w"]), need=(True, False, False))
+            u6, _, _ = S6.vjp(None, T(w["w"]), need=(True, False, False))
+        else:
+            um, u6 = Sm.solve(T(w["q"])), S6.solve(T(w["q"]))
+        assert rel(um, N(u6)) <= 2e-6
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES[:2])
+def test_mixed_iterates_track_fp64_iterates(dmg, shape):
+    # FP32 rounding in a correction is damped by the later cycles, so converged
+    # mixed and FP64 solutions agree far below the solve tolerance, in the same
+    # number of cycles.
+    w = inputs.tissue(shape=shape, seed=9)
+    Sm = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=1)
+    S6 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"])
+    um, u6 = Sm.solve(T(w["q"])), S6.solve(T(w["q"]))
+    assert abs(Sm.last_info.outer - S6.last_info.cycles) <= 1
+    assert rel(um, N(u6)) <= 1e-12
+    # three FP32 cycles per FP64 step (the default): same total cycle count, a third of the steps
+    S3 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=3)
+    u3 = S3.solve(T(w["q"]))
+    assert S3.last_info.cycles <= S6.last_info.cycles + 3
+    assert S3.last_info.outer <= (S6.last_info.cycles + 2) // 3 + 1
+    assert S3.last_info.rel_residual <= 1e-10 and rel(u3, N(u6)) <= 1e-9
