@@ -27,6 +27,9 @@ thread_local char g_setup_err[512];
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarse = 512;
 constexpr int kNormBlocks = 148 * 4;
+// Levels this small run in the single-CTA tail. One SM issues 2 FP64 FMA per
+// clock, so the FP64 tail starts lower than the FP32 one.
+constexpr long long kTailMaxInterior[2] = {512, 4096};
 
 struct Level {
     Geom g;
@@ -55,6 +58,7 @@ struct dmg_ctx {
     int nlev = 0;
     Level L[kMaxLevels];
     int nc = 0;                       // coarsest interior unknowns
+    int tail_first[2] = {0, 0};       // first level of the single-CTA tail: [0] FP64, [1] FP32
     double *Ainv = nullptr;           // coarsest inverse (FP64)
     float *Ainv32 = nullptr;
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
@@ -114,10 +118,7 @@ inline dim3 blk() { return dim3(32, 8, 1); }
 inline dim3 grid_int(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nz - 2); }
 inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nz); }
 // half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
-inline dim3 grid_half(const Geom &g) {
-    const int rows = 8 * dmgk::kRowsPerThread;
-    return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + rows - 1) / rows, g.nz - 2);
-}
+inline dim3 grid_half(const Geom &g) { return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nz - 2); }
 
 dmg_status check_launch(dmg_ctx *c, const char *what) {
     c->launches++;
@@ -263,24 +264,6 @@ dmg_status dispatch(dmg_ctx *c, Level &l, Fn fn) {
 template <class T>
 dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
     Level &l = c->L[lev];
-    if constexpr (sizeof(T) == 4) {
-        // four vertices per thread, float4 loads
-        dim3 grid(((l.g.hx / 4) + 31) / 32, (l.g.ny - 2 + 7) / 8, l.g.nz - 2);
-        for (int it = 0; it < nsweeps; it++) {
-            ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, 1, s);
-            for (int h = 0; h < 2; h++) {
-                int color = h == 0 ? first : 1 - first;
-                if (c->p.face_mean == DMG_FACE_HARMONIC)
-                    dmgk::k_smooth_half_v4<true><<<grid, blk(), 0, s>>>(
-                        l.g, l.u32, l.f32, dmgk::VertCoef<float, true>{l.Dh32, l.mu32}, color);
-                else
-                    dmgk::k_smooth_half_v4<false><<<grid, blk(), 0, s>>>(
-                        l.g, l.u32, l.f32, dmgk::VertCoef<float, false>{l.Dh32, l.mu32}, color);
-                TRY(check_launch(c, "smooth_v4"));
-            }
-        }
-        return DMG_OK;
-    }
     for (int it = 0; it < nsweeps; it++) {
         ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
         for (int h = 0; h < 2; h++) {
@@ -318,12 +301,40 @@ dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
     return check_launch(c, "prolong");
 }
 
+
+// per-level coefficient object of the type a kernel instantiation expects
+inline dmgk::FaceCoef<double> make_coef(const Level &l, dmgk::FaceCoef<double>) { return coef64(l); }
+template <bool H>
+inline dmgk::VertCoef<float, H> make_coef(const Level &l, dmgk::VertCoef<float, H>) {
+    return dmgk::VertCoef<float, H>{l.Dh32, l.mu32};
+}
+
+// The levels tail_first .. nlev-1 of one V-cycle (descent, exact coarsest
+// solve, ascent) in a single one-block launch.
 template <class T>
-dmg_status coarse_solve(dmg_ctx *c, cudaStream_t s) {
-    Level &l = c->L[c->nlev - 1];
-    int threads = c->nc < 32 ? 32 : (c->nc > 512 ? 512 : ((c->nc + 31) / 32) * 32);
-    dmgk::k_coarse_solve<T><<<1, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l));
-    return check_launch(c, "coarse_solve");
+dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_first, cudaStream_t s) {
+    const int l0 = c->tail_first[sizeof(T) == 4];
+    return dispatch<T>(c, c->L[l0], [&](auto cf0) -> dmg_status {
+        using C = decltype(cf0);
+        dmgk::TailArgs<T, C> a;
+        a.nl = c->nlev - l0;
+        for (int l = 0; l < a.nl; l++) {
+            Level &lv = c->L[l0 + l];
+            a.L[l].g = lv.g;
+            a.L[l].u = U<T>(lv);
+            a.L[l].f = F<T>(lv);
+            a.L[l].r = R<T>(lv);
+            a.L[l].c = make_coef(lv, cf0);
+        }
+        a.Ainv = AINV<T>(c);
+        a.nc = c->nc;
+        a.npre = npre;
+        a.npost = npost;
+        a.pre_first = pre_first;
+        a.post_first = post_first;
+        dmgk::k_vcycle_tail<T, C><<<1, 1024, c->nc * sizeof(T), s>>>(a);
+        return check_launch(c, "vcycle_tail");
+    });
 }
 
 // One V-cycle at level lev on (u_lev, f_lev), in place (Sec. 2.2, Fig. 1 left).
@@ -331,11 +342,11 @@ dmg_status coarse_solve(dmg_ctx *c, cudaStream_t s) {
 // one (Sec. 2.4): nu2 pre-sweeps and nu1 post-sweeps, colour orders reversed.
 template <class T>
 dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
-    if (lev == c->nlev - 1) return coarse_solve<T>(c, s);
     int post_first = c->p.symmetric ? 1 : 0;
     int npre = transposed ? c->p.nu2 : c->p.nu1, npost = transposed ? c->p.nu1 : c->p.nu2;
     int pre_first = transposed ? 1 - post_first : 0;
     int postf = transposed ? 1 : post_first;
+    if (lev == c->tail_first[sizeof(T) == 4]) return launch_tail<T>(c, npre, npost, pre_first, postf, s);
     TRY(smooth<T>(c, lev, pre_first, npre, s));
     TRY(restrict_defect<T>(c, lev, s));
     TRY(vcycle<T>(c, lev + 1, transposed, s));
@@ -663,6 +674,14 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
             double scale = harm ? ih2 : 0.5 * ih2;
             dmgk::k_build_vertex32<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, scale, L.Dh32, L.mu32);
             TRY(check_launch(c, "build_vertex32"));
+        }
+    }
+    for (int t = 0; t < 2; t++) {
+        c->tail_first[t] = c->nlev - 1;
+        while (c->tail_first[t] > 0) {
+            const Geom &g = c->L[c->tail_first[t] - 1].g;
+            if ((long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2) > kTailMaxInterior[t]) break;
+            c->tail_first[t]--;
         }
     }
     // exact coarsest solve: dense SPD inverse by in-block Gauss-Jordan

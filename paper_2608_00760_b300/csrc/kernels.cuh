@@ -100,7 +100,7 @@ struct VertCoef {
 // s + sum_q a_q u(p + o_q). FP64: one FMA chain (6 FP64-pipe ops, the B300's
 // scarce resource); FP32: three independent pairs (shorter dependency chain).
 template <class T>
-__device__ __forceinline__ T coupled_sum(T s, const T *__restrict__ u, long long p, const Nbr &n, const T *a) {
+__device__ __forceinline__ T coupled_sum(T s, const T *u, long long p, const Nbr &n, const T *a) {
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
         for (int q = 0; q < 6; q++) s = fma(a[q], u[p + n.o[q]], s);
@@ -117,154 +117,37 @@ __device__ __forceinline__ T coupled_sum(T s, const T *__restrict__ u, long long
 }
 
 // ---------------------------------------------------------------------------
-// Red-Black Gauss-Seidel half-sweep (Eq. 9): every interior vertex of colour
-// (i+j+k) mod 2 == color takes u_p = (f_p + sum_j a_pj u_j) / diag_p. Vertices
-// of one colour are not coupled, so the update is in place and race-free. In a
-// row (j, k) the colour is one parity of i, i.e. one contiguous half-row.
-// Each thread updates RPT vertices (rows j, j + blockDim.y, ...), issuing all
-// their loads before any store so that they are in flight together.
-constexpr int kRowsPerThread = 1;
+// Per-vertex bodies of the V-cycle operations. They read u, f and r with plain
+// loads (these arrays are written by earlier phases of the single-CTA tail
+// kernel below) and the coefficients through the read-only path.
 
+// Red-Black Gauss-Seidel update of one vertex (Eq. 9):
+// u_p = (f_p + sum_j a_pj u_j) / diag_p
 template <class T, class C>
-__global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, const T *__restrict__ f,
-                                                     C c, int color) {
-    constexpr int RPT = kRowsPerThread;
-    const int k = blockIdx.z + 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j0 = blockIdx.y * (blockDim.y * RPT) + threadIdx.y + 1;
-    long long p[RPT];
-    bool on[RPT];
-    T s[RPT], a[RPT][6];
-#pragma unroll
-    for (int r = 0; r < RPT; r++) {
-        const int j = j0 + r * blockDim.y;
-        const int par = (color + j + k) & 1;               // parity of i of this colour in this row
-        const int i = 2 * t + 2 - par;                     // 1, 3, ... or 2, 4, ...
-        on[r] = j <= g.ny - 2 && i <= g.nx - 2;
-        if (on[r]) {
-            p[r] = g.pos(i, j, k);
-            const Nbr n = neighbours(g, i);
-            c.couplings(p[r], n, a[r]);
-            s[r] = coupled_sum(__ldg(f + p[r]), u, p[r], n, a[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < RPT; r++)
-        if (on[r]) u[p[r]] = c.finish(s[r], p[r], a[r]);
-}
-
-// FP32 half-sweep with vertex coefficients, four vertices per thread. In row
-// (j, k) the colour's vertices are half-row indices m = M_lo..M_hi of one half;
-// a thread takes m = 4t..4t+3, so its own f, mu, D and its y/z neighbours
-// (same half, same m) are single float4 loads, and its x neighbours are the
-// other half's indices 4t..4t+3 plus one value beyond either end, taken from
-// the adjacent lane by a shuffle (or loaded by lanes 0 and 31). Requires hx to
-// be a multiple of 4 (it is a multiple of 32).
-template <bool HARM>
-__global__ void __launch_bounds__(256) k_smooth_half_v4(Geom g, float *__restrict__ u, const float *__restrict__ f,
-                                                        VertCoef<float, HARM> c, int color) {
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const bool jin = j <= g.ny - 2;
-    const int jj = jin ? j : g.ny - 2;                   // keep whole warps in the shuffles
-    const int par = (color + jj + k) & 1;
-    const long long row = (long long)k * g.sz + (long long)jj * g.sy;
-    const long long ob = row + par * g.hx + 4 * t;       // own half, m = 4t
-    const long long tb = row + (1 - par) * g.hx + 4 * t; // other half, index 4t
-    const bool tin = 4 * t < g.hx;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto ld = [&](const float *a, long long q) { return tin ? __ldg(reinterpret_cast<const float4 *>(a + q)) : z4; };
-    // every load is issued before the first use (shuffles, early exits), so a
-    // thread has all 13 vector loads in flight at once
-    const float4 uo = ld(u, tb), dox = ld(c.Dh, tb);
-    const float4 dc = ld(c.Dh, ob), f4 = ld(f, ob), m4 = ld(c.mu, ob);
-    const float4 dym = ld(c.Dh, ob - g.sy), dyp = ld(c.Dh, ob + g.sy);
-    const float4 dzm = ld(c.Dh, ob - g.sz), dzp = ld(c.Dh, ob + g.sz);
-    const float4 uym = ld(u, ob - g.sy), uyp = ld(u, ob + g.sy);
-    const float4 uzm = ld(u, ob - g.sz), uzp = ld(u, ob + g.sz);
-    const bool ok0 = lane == 0 && tin && 4 * t >= 1, ok31 = lane == 31 && tin && 4 * t + 4 < g.hx;
-    const float u_prev0 = ok0 ? __ldg(u + tb - 1) : 0.f, d_prev0 = ok0 ? __ldg(c.Dh + tb - 1) : 0.f;
-    const float u_next31 = ok31 ? __ldg(u + tb + 4) : 0.f, d_next31 = ok31 ? __ldg(c.Dh + tb + 4) : 0.f;
-    // values at other-half indices 4t-1 (for even parity) and 4t+4 (odd parity)
-    float u_prev = __shfl_up_sync(0xffffffffu, uo.w, 1), d_prev = __shfl_up_sync(0xffffffffu, dox.w, 1);
-    float u_next = __shfl_down_sync(0xffffffffu, uo.x, 1), d_next = __shfl_down_sync(0xffffffffu, dox.x, 1);
-    if (lane == 0) { u_prev = u_prev0; d_prev = d_prev0; }
-    if (lane == 31) { u_next = u_next31; d_next = d_next31; }
-    const int M_lo = 1 - par, M_hi = par ? (g.nx - 3) / 2 : (g.nx - 2) / 2;
-    if (!jin || !tin || 4 * t > M_hi) return;
-    const float U[6] = {u_prev, uo.x, uo.y, uo.z, uo.w, u_next};   // other half, indices 4t-1 .. 4t+4
-    const float DX[6] = {d_prev, dox.x, dox.y, dox.z, dox.w, d_next};
-    const float DC[4] = {dc.x, dc.y, dc.z, dc.w}, F[4] = {f4.x, f4.y, f4.z, f4.w}, MU[4] = {m4.x, m4.y, m4.z, m4.w};
-    const float DYM[4] = {dym.x, dym.y, dym.z, dym.w}, DYP[4] = {dyp.x, dyp.y, dyp.z, dyp.w};
-    const float DZM[4] = {dzm.x, dzm.y, dzm.z, dzm.w}, DZP[4] = {dzp.x, dzp.y, dzp.z, dzp.w};
-    const float UYM[4] = {uym.x, uym.y, uym.z, uym.w}, UYP[4] = {uyp.x, uyp.y, uyp.z, uyp.w};
-    const float UZM[4] = {uzm.x, uzm.y, uzm.z, uzm.w}, UZP[4] = {uzp.x, uzp.y, uzp.z, uzp.w};
-    float out[4];
-    bool ok[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int m = 4 * t + q;
-        ok[q] = m >= M_lo && m <= M_hi;
-        // x-1 / x+1 neighbours: other-half indices m-1, m (even parity) or m, m+1 (odd);
-        // U[q + 1] holds index m
-        const float ul = par ? U[q + 1] : U[q], ur = par ? U[q + 2] : U[q + 1];
-        const float dl = par ? DX[q + 1] : DX[q], dr = par ? DX[q + 2] : DX[q + 1];
-        const float d = DC[q];
-        const float a0 = VertCoef<float, HARM>::face(d, dl), a1 = VertCoef<float, HARM>::face(d, dr);
-        const float a2 = VertCoef<float, HARM>::face(d, DYM[q]), a3 = VertCoef<float, HARM>::face(d, DYP[q]);
-        const float a4 = VertCoef<float, HARM>::face(d, DZM[q]), a5 = VertCoef<float, HARM>::face(d, DZP[q]);
-        float s0 = fmaf(a0, ul, F[q]);
-        float s1 = a2 * UYM[q];
-        float s2 = a4 * UZM[q];
-        s0 = fmaf(a1, ur, s0);
-        s1 = fmaf(a3, UYP[q], s1);
-        s2 = fmaf(a5, UZP[q], s2);
-        const float dg = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + MU[q]);
-        out[q] = __fdividef((s0 + s1) + s2, dg);
-    }
-    if (ok[0] && ok[1] && ok[2] && ok[3]) {
-        *reinterpret_cast<float4 *>(u + ob) = make_float4(out[0], out[1], out[2], out[3]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (ok[q]) u[ob + q] = out[q];
-    }
+__device__ __forceinline__ void smooth_point(const Geom &g, T *u, const T *f, const C &c, int i, int j, int k) {
+    const long long p = g.pos(i, j, k);
+    const Nbr n = neighbours(g, i);
+    T a[6];
+    c.couplings(p, n, a);
+    const T s = coupled_sum(f[p], u, p, n, a);
+    u[p] = c.finish(s, p, a);
 }
 
 // residual value at an interior vertex: f_p - diag_p u_p + sum_j a_pj u_j
 template <class T, class C>
-__device__ __forceinline__ T residual_at(const T *__restrict__ u, const T *__restrict__ f, const C &c,
-                                         long long p, const Nbr &n) {
+__device__ __forceinline__ T residual_at(const T *u, const T *f, const C &c, long long p, const Nbr &n) {
     T a[6];
     c.couplings(p, n, a);
-    T s = fma(-c.get_diag(p, a), __ldg(u + p), __ldg(f + p));
+    T s = fma(-c.get_diag(p, a), u[p], f[p]);
     return coupled_sum(s, u, p, n, a);
 }
 
-// r = f - A u on interior vertices (the defect, Eqs. 13-14)
-template <class T, class C>
-__global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ u, const T *__restrict__ f,
-                                                  C c, T *__restrict__ r) {
-    int i = vertex_i();
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.pos(i, j, k);
-    r[p] = residual_at(u, f, c, p, neighbours(g, i));
-}
-
-// Full-weighting restriction (Eq. 7, 1/4[1 2 1] per axis) of a fine field onto
-// coarse interior vertices. The 27 fine points around 2I are all fine-interior.
+// full weighting (Eq. 7, 1/4[1 2 1] per axis) of r around fine 2I onto the
+// coarse interior vertex (I, J, K); the 27 fine points are all fine-interior
 template <class T>
-__global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__ r, Geom gc,
-                                                  T *__restrict__ fc) {
-    int I = vertex_i();
-    int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int K = blockIdx.z + 1;
-    if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
-    long long p = gf.pos(2 * I, 2 * J, 2 * K);
+__device__ __forceinline__ void restrict_point(const Geom &gf, const T *r, const Geom &gc, T *fc, int I, int J,
+                                               int K) {
+    const long long p = gf.pos(2 * I, 2 * J, 2 * K);
     const int om = gf.xm(2 * I), op = gf.xp(2 * I);
     T s = T(0);
 #pragma unroll
@@ -272,8 +155,8 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
         T sp = T(0);
 #pragma unroll
         for (int b = -1; b <= 1; b++) {
-            long long q = p + c * gf.sz + b * gf.sy;
-            T row = __ldg(r + q + om) + T(2) * __ldg(r + q) + __ldg(r + q + op);
+            const long long q = p + c * gf.sz + b * gf.sy;
+            const T row = r[q + om] + T(2) * r[q] + r[q + op];
             sp += (b == 0 ? T(2) : T(1)) * row;
         }
         s += (c == 0 ? T(2) : T(1)) * sp;
@@ -281,28 +164,20 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
     fc[gc.pos(I, J, K)] = s * T(1.0 / 64.0);
 }
 
-// Prolongation I = 2^3 R^T (Eq. 17) and correction: u_fine += trilinear(e)
-// on fine interior vertices; e is zero on the coarse boundary. One thread per
-// coarse cell (I..I+1, J..J+1, K..K+1): it loads the 8 corner values once and
-// corrects the fine vertices (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, with the
-// trilinear weights (1 at a coincident vertex, 1/2 per axis at a midpoint).
-// In the split layout fine x = 2I and 2I+1 are index I of the even and odd
-// halves, so both stay contiguous across a warp.
+// Prolongation I = 2^3 R^T (Eq. 17) and correction on the fine vertices of one
+// coarse cell (I..I+1, J..J+1, K..K+1): the 8 corner values are loaded once and
+// the fine vertices (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, get the trilinear
+// interpolant (weight 1 at a coincident vertex, 1/2 per axis at a midpoint).
+// e is zero on the coarse boundary; only fine interior vertices are written.
 template <class T>
-__global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf,
-                                                     T *__restrict__ u) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = blockIdx.z;
-    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+__device__ __forceinline__ void prolong_cell(const Geom &gc, const T *e, const Geom &gf, T *u, int I, int J, int K) {
     T c[2][2][2];
 #pragma unroll
     for (int z = 0; z < 2; z++)
 #pragma unroll
         for (int y = 0; y < 2; y++)
 #pragma unroll
-            for (int x = 0; x < 2; x++) c[z][y][x] = __ldg(e + gc.pos(I + x, J + y, K + z));
-    // interpolate along x, then y, then z: v[c][b][a] at fine (2I+a, 2J+b, 2K+c)
+            for (int x = 0; x < 2; x++) c[z][y][x] = e[gc.pos(I + x, J + y, K + z)];
 #pragma unroll
     for (int cz = 0; cz < 2; cz++) {
         const int k = 2 * K + cz;
@@ -314,40 +189,160 @@ __global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restric
             T row[2];
 #pragma unroll
             for (int x = 0; x < 2; x++) {
-                T lo = by ? T(0.5) * (c[0][0][x] + c[0][1][x]) : c[0][0][x];
-                T hi = by ? T(0.5) * (c[1][0][x] + c[1][1][x]) : c[1][0][x];
+                const T lo = by ? T(0.5) * (c[0][0][x] + c[0][1][x]) : c[0][0][x];
+                const T hi = by ? T(0.5) * (c[1][0][x] + c[1][1][x]) : c[1][0][x];
                 row[x] = cz ? T(0.5) * (lo + hi) : lo;
             }
-            if (2 * I >= 1) {
-                const long long p = gf.pos(2 * I, j, k);
-                u[p] += row[0];
-            }
-            if (2 * I + 1 <= gf.nx - 2) {
-                const long long p = gf.pos(2 * I + 1, j, k);
-                u[p] += T(0.5) * (row[0] + row[1]);
-            }
+            if (2 * I >= 1) u[gf.pos(2 * I, j, k)] += row[0];
+            if (2 * I + 1 <= gf.nx - 2) u[gf.pos(2 * I + 1, j, k)] += T(0.5) * (row[0] + row[1]);
         }
     }
 }
 
-// Exact coarsest-level solve u = A^{-1} f with the symmetric inverse built at
-// setup; one block, one thread per coarsest interior unknown.
+// ---------------------------------------------------------------------------
+// grid kernels (one V-cycle operation on one level per launch)
+
+// Red-Black Gauss-Seidel half-sweep: every interior vertex of colour
+// (i+j+k) mod 2 == color. Vertices of one colour are not coupled, so the update
+// is in place and race-free. In a row (j, k) the colour is one parity of i, i.e.
+// one contiguous half-row.
+template <class T, class C>
+__global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, const T *__restrict__ f, C c,
+                                                     int color) {
+    const int k = blockIdx.z + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int par = (color + j + k) & 1;                                       // parity of i of this colour
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;   // 1, 3, ... or 2, 4, ...
+    if (j > g.ny - 2 || i > g.nx - 2) return;
+    smooth_point(g, u, f, c, i, j, k);
+}
+
+// r = f - A u on interior vertices (the defect, Eqs. 13-14)
+template <class T, class C>
+__global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ u, const T *__restrict__ f, C c,
+                                                  T *__restrict__ r) {
+    int i = vertex_i();
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    long long p = g.pos(i, j, k);
+    r[p] = residual_at(u, f, c, p, neighbours(g, i));
+}
+
+// f_{l+1} = R r_l on coarse interior vertices
 template <class T>
-__global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const T *__restrict__ f,
-                               T *__restrict__ u) {
-    extern __shared__ unsigned char smem_raw[];
-    T *fs = reinterpret_cast<T *>(smem_raw);
-    int nxi = g.nx - 2, nyi = g.ny - 2;
+__global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__ r, Geom gc, T *__restrict__ fc) {
+    int I = vertex_i();
+    int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int K = blockIdx.z + 1;
+    if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
+    restrict_point(gf, r, gc, fc, I, J, K);
+}
+
+// u_l += I u_{l+1}, one thread per coarse cell
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I > gc.nx - 2 || J > gc.ny - 2) return;
+    prolong_cell(gc, e, gf, u, I, J, K);
+}
+
+// exact coarsest solve u = A^{-1} f with the symmetric inverse built at setup,
+// by one block (fs: n values of shared memory)
+template <class T>
+__device__ __forceinline__ void coarse_solve_block(const Geom &g, const T *Ainv, int n, const T *f, T *u, T *fs) {
+    const int nxi = g.nx - 2, nyi = g.ny - 2;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        int i = c % nxi + 1, j = (c / nxi) % nyi + 1, k = c / (nxi * nyi) + 1;
+        const int i = c % nxi + 1, j = (c / nxi) % nyi + 1, k = c / (nxi * nyi) + 1;
         fs[c] = f[g.pos(i, j, k)];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         T s = T(0);
         for (int c = 0; c < n; c++) s = fma(Ainv[(long long)r * n + c], fs[c], s);
-        int i = r % nxi + 1, j = (r / nxi) % nyi + 1, k = r / (nxi * nyi) + 1;
+        const int i = r % nxi + 1, j = (r / nxi) % nyi + 1, k = r / (nxi * nyi) + 1;
         u[g.pos(i, j, k)] = s;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Single-CTA tail of the V-cycle: the levels from `first` down to the coarsest
+// are small (a few thousand vertices at most), where one launch per operation
+// costs more than the work. One block runs the whole descent (smoothing,
+// defect, restriction), the exact coarsest solve and the ascent
+// (prolongation, smoothing), with a block barrier between operations.
+
+constexpr int kTailMaxLevels = 10;
+
+template <class T, class C>
+struct TailLevel {
+    Geom g;
+    T *u, *f, *r;
+    C c;
+};
+
+template <class T, class C>
+struct TailArgs {
+    TailLevel<T, C> L[kTailMaxLevels];
+    int nl;                          // levels in the tail; L[nl-1] is the coarsest
+    const T *Ainv;
+    int nc;
+    int npre, npost, pre_first, post_first;
+};
+
+template <class T, class C>
+__device__ __forceinline__ void tail_half(const TailLevel<T, C> &L, int color) {
+    const int nxi = L.g.nx - 2, nyi = L.g.ny - 2, n = nxi * nyi * (L.g.nz - 2);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
+        if (((i + j + k) & 1) == color) smooth_point(L.g, L.u, L.f, L.c, i, j, k);
+    }
+    __syncthreads();
+}
+
+template <class T, class C>
+__global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
+    extern __shared__ unsigned char smem_raw[];
+    T *fs = reinterpret_cast<T *>(smem_raw);
+    for (int l = 0; l < a.nl - 1; l++) {
+        const TailLevel<T, C> &L = a.L[l], &C1 = a.L[l + 1];
+        for (int sw = 0; sw < a.npre; sw++) {
+            tail_half(L, a.pre_first);
+            tail_half(L, 1 - a.pre_first);
+        }
+        const int nxi = L.g.nx - 2, nyi = L.g.ny - 2, n = nxi * nyi * (L.g.nz - 2);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
+            const long long p = L.g.pos(i, j, k);
+            L.r[p] = residual_at(L.u, L.f, L.c, p, neighbours(L.g, i));
+        }
+        __syncthreads();
+        const int cxi = C1.g.nx - 2, cyi = C1.g.ny - 2, nc = cxi * cyi * (C1.g.nz - 2);
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+            const int I = t % cxi + 1, J = (t / cxi) % cyi + 1, K = t / (cxi * cyi) + 1;
+            restrict_point(L.g, L.r, C1.g, C1.f, I, J, K);
+            C1.u[C1.g.pos(I, J, K)] = T(0);
+        }
+        __syncthreads();
+    }
+    const TailLevel<T, C> &LC = a.L[a.nl - 1];
+    coarse_solve_block(LC.g, a.Ainv, a.nc, LC.f, LC.u, fs);
+    __syncthreads();
+    for (int l = a.nl - 2; l >= 0; l--) {
+        const TailLevel<T, C> &L = a.L[l], &C1 = a.L[l + 1];
+        const int cx = C1.g.nx - 1, cy = C1.g.ny - 1, ncell = cx * cy * (C1.g.nz - 1);
+        for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+            const int I = t % cx, J = (t / cx) % cy, K = t / (cx * cy);
+            prolong_cell(C1.g, C1.u, L.g, L.u, I, J, K);
+        }
+        __syncthreads();
+        for (int sw = 0; sw < a.npost; sw++) {
+            tail_half(L, a.post_first);
+            tail_half(L, 1 - a.post_first);
+        }
     }
 }
 

@@ -263,13 +263,13 @@ FUSED_SHAPES = [(65, 65, 65), (33, 49, 97), (129, 33, 65), (17, 33, 161), (9, 9,
 
 
 @pytest.mark.parametrize("shape", FUSED_SHAPES)
-@pytest.mark.parametrize("face_mean", [0, 1])
-def test_fp32_vcycle_matches_fp64_vcycle(dmg, shape, face_mean):
+@pytest.mark.parametrize("face_mean,nu", [(0, (2, 2)), (1, (2, 2)), (0, (3, 1))])
+def test_fp32_vcycle_matches_fp64_vcycle(dmg, shape, face_mean, nu):
     # one mixed refinement step is s * V32(q / s); one FP64 cycle is V64(q). The FP32
     # V-cycle (fused TMA sweeps on the wide levels, ragged tiles and z-chunks
     # included) must be the same linear map up to FP32 rounding.
     w = inputs.tissue(shape=shape, seed=8)
-    kw = dict(max_cycles=1, strict=False, face_mean=face_mean)
+    kw = dict(max_cycles=1, strict=False, face_mean=face_mean, nu1=nu[0], nu2=nu[1])
     Sm = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=1, **kw)
     S6 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_FP64, **kw)
     for transposed in (False, True):
