@@ -34,10 +34,17 @@ METRIC = "fwd+VJP solves/s & HBM GB/s at 257³ (FP32-refined vs FP64, 1e-10); p5
 UNIT = "fwd+VJP solves/s"
 N_SIDE = 257
 RTOL = 1e-10
-# algorithmic bytes per interior point of one RB-GS sweep: read u, f, D, mu and
-# write u (FP32 vertex layout: 4 B each) / read u, f, 3 faces, 1/diag and write u (FP64)
-SWEEP_BYTES = {"fp32": 20.0, "fp64": 56.0}
-SWEEP_FP64_OPS = 7.0   # FP64 pipe operations per point of a sweep (6 FMA + 1 MUL)
+# Roofline unit: one RB-GS half-sweep launch on the finest level (one colour).
+# FP32 (vertex coefficients, split rows): per interior vertex of the grid it
+# reads f and mu of its own colour (2 + 2 B), D of every vertex (4 B), u of the
+# other colour (2 B) and writes u of its own colour (2 B): 12 B.
+# FP64 (precomputed faces): 6 FMA + 1 MUL per updated vertex = 3.5 FP64-pipe
+# operations per interior vertex of the grid, against the measured FP64 rate.
+HALF_SWEEP_BYTES_FP32 = 12.0
+HALF_SWEEP_FP64_OPS = 3.5
+# DRAM bytes (read + write) of one finest-level half-sweep launch at 257^3,
+# from an ncu capture of the current kernel (profiles/rbgs_half_sweep_257.md)
+HALF_SWEEP_TRAFFIC = {"fp32": None, "fp64": None}
 
 
 def percentile(x, p):
@@ -148,6 +155,11 @@ def max_over_ranks(world, x):
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, steps, max_total_ms):
+    """Whole-job pairs/s: every rank runs `steps` pairs; the slowest rank's time counts."""
+    return world * steps / (max_total_ms / 1e3)
 
 
 def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None, clocks=False, inner=1):
@@ -355,7 +367,7 @@ def main():
     head = results[precisions[0]]
     S = head["solver"]
     ms = head["total_ms"] / args.steps
-    value = world * args.steps / (head["total_ms"] / 1e3)
+    value = job_throughput(world, args.steps, head["total_ms"])
 
     def roofline(res, prec):
         pr = res["prof"]
@@ -363,17 +375,17 @@ def main():
             return None
         dur = pr["total_ms"] / pr["launches"] / 1e3
         if prec == "mixed":
-            byt = SWEEP_BYTES["fp32"] * nint
+            byt = HALF_SWEEP_BYTES_FP32 * nint
             ach = byt / dur / 1e9
             pk = peaks.get("hbm_gbs", 6400.0)
-            return dict(kernel="rbgs_sweep_fp32_level0", bound="hbm", achieved=ach, peak=pk, unit="GB/s",
-                        frac=ach / pk, traffic=None, peak_source=peak_src + " hbm_gbs",
+            return dict(kernel="rbgs_half_sweep_fp32_level0", bound="hbm", achieved=ach, peak=pk, unit="GB/s",
+                        frac=ach / pk, traffic=HALF_SWEEP_TRAFFIC["fp32"], peak_source=peak_src + " hbm_gbs",
                         launches=pr["launches"], avg_us=dur * 1e6, algorithmic_bytes=byt)
-        ops = SWEEP_FP64_OPS * nint
+        ops = HALF_SWEEP_FP64_OPS * nint
         ach = ops / dur / 1e12
-        return dict(kernel="rbgs_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK / 1e12,
-                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=None,
-                    peak_source="measured DFMA rate (probe)", launches=pr["launches"], avg_us=dur * 1e6,
+        return dict(kernel="rbgs_half_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK / 1e12,
+                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=HALF_SWEEP_TRAFFIC["fp64"],
+                    peak_source="measured FP64 FMA rate (probe)", launches=pr["launches"], avg_us=dur * 1e6,
                     algorithmic_fp64_ops=ops)
 
     def gbs(res, prec):
@@ -401,7 +413,7 @@ def main():
                roofline=roofline(head, precisions[0]), clocks=head["clocks"])
     for prec in precisions[1:]:
         r = results[prec]
-        out[prec] = dict(value=world * args.steps / (r["total_ms"] / 1e3), unit=UNIT,
+        out[prec] = dict(value=job_throughput(world, args.steps, r["total_ms"]), unit=UNIT,
                          ms_per_step=r["total_ms"] / args.steps, p50_ms=percentile(r["per_ms"], 50),
                          p99_ms=percentile(r["per_ms"], 99), hbm_gbs_algorithmic=gbs(r, prec),
                          cycles=dict(fwd=r["fwd_cycles"], adj=r["adj_cycles"]), gpu_launches=r["launches"],

@@ -224,7 +224,7 @@ dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int 
  *   recorded launches and their summed duration in milliseconds.
  */
 enum {
-    DMG_KERNEL_SMOOTH = 0,     /* one RB-GS sweep (both colours) */
+    DMG_KERNEL_SMOOTH = 0,     /* one RB-GS half-sweep (one colour) */
     DMG_KERNEL_RESTRICT = 1,   /* defect + full-weighting restriction */
     DMG_KERNEL_PROLONG = 2,    /* prolongation + correction */
     DMG_KERNEL_RESIDUAL = 3,   /* FP64 residual + norm */

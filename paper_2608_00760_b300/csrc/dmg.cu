@@ -265,8 +265,8 @@ template <class T>
 dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
     Level &l = c->L[lev];
     for (int it = 0; it < nsweeps; it++) {
-        ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
         for (int h = 0; h < 2; h++) {
+            ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
             int color = h == 0 ? first : 1 - first;
             TRY(dispatch<T>(c, l, [&](auto cf) {
                 dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color);
@@ -277,17 +277,33 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
     return DMG_OK;
 }
 
-// f_{l+1} = R (f_l - A_l u_l), u_{l+1} = 0
+// f_{l+1} = R (f_l - A_l u_l), u_{l+1} = 0. zero_colour >= 0: the defect
+// vanishes on that colour (the last half-sweep updated it), so it is formed on
+// the other colour only and the restriction reads only that colour.
 template <class T>
-dmg_status restrict_defect(dmg_ctx *c, int lev, cudaStream_t s) {
+dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s) {
     Level &l = c->L[lev], &cl = c->L[lev + 1];
     ProfScope ps(c, DMG_KERNEL_RESTRICT, lev, sizeof(T) == 4, s);
-    TRY(dispatch<T>(c, l, [&](auto cf) {
-        dmgk::k_residual<T><<<grid_int(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l));
-        return check_launch(c, "residual");
-    }));
-    dmgk::k_restrict<T><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
-    TRY(check_launch(c, "restrict"));
+    if (zero_colour >= 0) {
+        const int nz = 1 - zero_colour;   // colour carrying the defect
+        TRY(dispatch<T>(c, l, [&](auto cf) {
+            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz);
+            return check_launch(c, "residual_colour");
+        }));
+        // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
+        if (nz == 0)
+            dmgk::k_restrict_colour<T, 0><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+        else
+            dmgk::k_restrict_colour<T, 1><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+        TRY(check_launch(c, "restrict_colour"));
+    } else {
+        TRY(dispatch<T>(c, l, [&](auto cf) {
+            dmgk::k_residual<T><<<grid_int(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l));
+            return check_launch(c, "residual");
+        }));
+        dmgk::k_restrict<T><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+        TRY(check_launch(c, "restrict"));
+    }
     CUDA_TRY(c, cudaMemsetAsync(U<T>(cl), 0, cl.n * sizeof(T), s));
     return DMG_OK;
 }
@@ -348,7 +364,8 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
     int postf = transposed ? 1 : post_first;
     if (lev == c->tail_first[sizeof(T) == 4]) return launch_tail<T>(c, npre, npost, pre_first, postf, s);
     TRY(smooth<T>(c, lev, pre_first, npre, s));
-    TRY(restrict_defect<T>(c, lev, s));
+    // after pre-smoothing the defect is zero on the colour updated last
+    TRY(restrict_defect<T>(c, lev, npre > 0 ? 1 - pre_first : -1, s));
     TRY(vcycle<T>(c, lev + 1, transposed, s));
     TRY(prolong<T>(c, lev, s));
     TRY(smooth<T>(c, lev, postf, npost, s));

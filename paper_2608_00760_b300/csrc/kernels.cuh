@@ -239,6 +239,51 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
     restrict_point(gf, r, gc, fc, I, J, K);
 }
 
+// Defect on one colour only. Right after a Gauss-Seidel half-sweep of colour X
+// the defect f - A u is exactly zero on every vertex of colour X (each was
+// just solved for), so after pre-smoothing it only has to be formed on the
+// other colour; r is written there and nowhere else.
+template <class T, class C>
+__global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__restrict__ u, const T *__restrict__ f,
+                                                         C c, T *__restrict__ r, int color) {
+    const int k = blockIdx.z + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int par = (color + j + k) & 1;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;
+    if (j > g.ny - 2 || i > g.nx - 2) return;
+    const long long p = g.pos(i, j, k);
+    r[p] = residual_at(u, f, c, p, neighbours(g, i));
+}
+
+// Full weighting of a defect that vanishes on one colour: fine vertex
+// (2I+a, 2J+b, 2K+c) has colour (a+b+c) mod 2, so only the 13 (PAR = 0: centre
+// and edges) or 14 (PAR = 1: faces and corners) offsets of that parity carry a
+// nonzero defect; the other r entries are not read.
+template <class T, int PAR>
+__global__ void __launch_bounds__(256) k_restrict_colour(Geom gf, const T *__restrict__ r, Geom gc,
+                                                         T *__restrict__ fc) {
+    const int I = vertex_i();
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int K = blockIdx.z + 1;
+    if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
+    const long long p = gf.pos(2 * I, 2 * J, 2 * K);
+    const int om = gf.xm(2 * I), op = gf.xp(2 * I);
+    T s = T(0);
+#pragma unroll
+    for (int cc = -1; cc <= 1; cc++)
+#pragma unroll
+        for (int b = -1; b <= 1; b++) {
+            const long long q = p + cc * gf.sz + b * gf.sy;
+            const int wcb = (cc == 0 ? 2 : 1) * (b == 0 ? 2 : 1);
+            if (((cc + b) & 1) == PAR) {          // a = 0 has the right parity
+                s = fma(T(2 * wcb), r[q], s);
+            } else {                               // a = -1, +1 have it
+                s = fma(T(wcb), r[q + om] + r[q + op], s);
+            }
+        }
+    fc[gc.pos(I, J, K)] = s * T(1.0 / 64.0);
+}
+
 // u_l += I u_{l+1}, one thread per coarse cell
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u) {
