@@ -30,6 +30,16 @@ constexpr int kNormBlocks = 148 * 4;
 // Levels this small run in the single-CTA tail. One SM issues 2 FP64 FMA per
 // clock, so the FP64 tail starts lower than the FP32 one.
 constexpr long long kTailMaxInterior[2] = {512, 4096};
+constexpr size_t kTailSmemBudget = 200 * 1024;
+
+// unpadded split-row geometry of a level staged in shared memory
+inline Geom smem_geom(const Geom &g) {
+    Geom s = g;
+    s.hx = g.nhalf();
+    s.sy = 2 * s.hx;
+    s.sz = (long long)s.sy * g.ny;
+    return s;
+}
 
 struct Level {
     Geom g;
@@ -58,7 +68,8 @@ struct dmg_ctx {
     int nlev = 0;
     Level L[kMaxLevels];
     int nc = 0;                       // coarsest interior unknowns
-    int tail_first[2] = {0, 0};       // first level of the single-CTA tail: [0] FP64, [1] FP32
+    int tail_first[2] = {0, 0};       // first level of the single-CTA tail: [0] FP64, [1] FP32 (nlev: none)
+    size_t tail_smem[2] = {0, 0};     // its dynamic shared memory in bytes
     double *Ainv = nullptr;           // coarsest inverse (FP64)
     float *Ainv32 = nullptr;
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
@@ -326,10 +337,11 @@ inline dmgk::VertCoef<float, H> make_coef(const Level &l, dmgk::VertCoef<float, 
 }
 
 // The levels tail_first .. nlev-1 of one V-cycle (descent, exact coarsest
-// solve, ascent) in a single one-block launch.
+// solve, ascent) in a single one-block launch working in shared memory.
 template <class T>
 dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_first, cudaStream_t s) {
-    const int l0 = c->tail_first[sizeof(T) == 4];
+    const int t = sizeof(T) == 4;
+    const int l0 = c->tail_first[t];
     return dispatch<T>(c, c->L[l0], [&](auto cf0) -> dmg_status {
         using C = decltype(cf0);
         dmgk::TailArgs<T, C> a;
@@ -337,9 +349,9 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
         for (int l = 0; l < a.nl; l++) {
             Level &lv = c->L[l0 + l];
             a.L[l].g = lv.g;
+            a.L[l].gs = smem_geom(lv.g);
             a.L[l].u = U<T>(lv);
             a.L[l].f = F<T>(lv);
-            a.L[l].r = R<T>(lv);
             a.L[l].c = make_coef(lv, cf0);
         }
         a.Ainv = AINV<T>(c);
@@ -348,9 +360,19 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
         a.npost = npost;
         a.pre_first = pre_first;
         a.post_first = post_first;
-        dmgk::k_vcycle_tail<T, C><<<1, 1024, c->nc * sizeof(T), s>>>(a);
+        dmgk::k_vcycle_tail<T, C><<<1, 1024, c->tail_smem[t], s>>>(a);
         return check_launch(c, "vcycle_tail");
     });
+}
+
+// exact coarsest solve by one grid launch (used when the tail does not fit in
+// shared memory)
+template <class T>
+dmg_status coarse_solve(dmg_ctx *c, cudaStream_t s) {
+    Level &l = c->L[c->nlev - 1];
+    int threads = c->nc < 32 ? 32 : (c->nc > 512 ? 512 : ((c->nc + 31) / 32) * 32);
+    dmgk::k_coarse_solve<T><<<1, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l));
+    return check_launch(c, "coarse_solve");
 }
 
 // One V-cycle at level lev on (u_lev, f_lev), in place (Sec. 2.2, Fig. 1 left).
@@ -363,6 +385,7 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
     int pre_first = transposed ? 1 - post_first : 0;
     int postf = transposed ? 1 : post_first;
     if (lev == c->tail_first[sizeof(T) == 4]) return launch_tail<T>(c, npre, npost, pre_first, postf, s);
+    if (lev == c->nlev - 1) return coarse_solve<T>(c, s);
     TRY(smooth<T>(c, lev, pre_first, npre, s));
     // after pre-smoothing the defect is zero on the colour updated last
     TRY(restrict_defect<T>(c, lev, npre > 0 ? 1 - pre_first : -1, s));
@@ -693,12 +716,40 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
             TRY(check_launch(c, "build_vertex32"));
         }
     }
+    Level &LC0 = c->L[c->nlev - 1];
+    c->nc = (LC0.g.nx - 2) * (LC0.g.ny - 2) * (LC0.g.nz - 2);   // coarsest unknowns (the tail sizes its buffer by it)
+    // single-CTA tail: the small levels, as many as fit the shared-memory budget
     for (int t = 0; t < 2; t++) {
-        c->tail_first[t] = c->nlev - 1;
-        while (c->tail_first[t] > 0) {
-            const Geom &g = c->L[c->tail_first[t] - 1].g;
+        const size_t esz = t ? sizeof(float) : sizeof(double);
+        const int ncoef = t ? 2 : 5;
+        auto bytes = [&](int first) {
+            size_t e = (size_t)c->nc + 16;
+            for (int l = first; l < c->nlev; l++) {
+                Geom gs = smem_geom(c->L[l].g);
+                e += (size_t)gs.sz * gs.nz * (3 + ncoef);
+            }
+            return e * esz;
+        };
+        int first = c->nlev - 1;
+        while (first > 0) {
+            const Geom &g = c->L[first - 1].g;
             if ((long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2) > kTailMaxInterior[t]) break;
-            c->tail_first[t]--;
+            if (bytes(first - 1) > kTailSmemBudget) break;
+            first--;
+        }
+        if (bytes(first) > kTailSmemBudget) first = c->nlev;   // even the coarsest does not fit: no tail
+        c->tail_first[t] = first;
+        c->tail_smem[t] = first < c->nlev ? bytes(first) : 0;
+    }
+    {
+        static bool attr = false;
+        if (!attr) {
+            for (auto fn : {(const void *)dmgk::k_vcycle_tail<double, dmgk::FaceCoef<double>>,
+                            (const void *)dmgk::k_vcycle_tail<float, dmgk::VertCoef<float, false>>,
+                            (const void *)dmgk::k_vcycle_tail<float, dmgk::VertCoef<float, true>>})
+                CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kTailSmemBudget));
+            attr = true;
         }
     }
     // exact coarsest solve: dense SPD inverse by in-block Gauss-Jordan

@@ -61,23 +61,31 @@ __device__ __forceinline__ Nbr neighbours(const Geom &g, int i) {
     return n;
 }
 
-template <class T>
+// RO: coefficients in global memory, read through the read-only path;
+// !RO: coefficients staged in shared memory, plain loads.
+template <bool RO, class T>
+__device__ __forceinline__ T cld(const T *p) {
+    if constexpr (RO) return __ldg(p);
+    else return *p;
+}
+
+template <class T, bool RO = true>
 struct FaceCoef {
     const T *cx, *cy, *cz;   // a between p and p+x, p+y, p+z, stored at p
     const T *diag, *invd;    // diagonal and its reciprocal (0 on the boundary)
     __device__ __forceinline__ void couplings(long long p, const Nbr &n, T a[6]) const {
-        a[0] = __ldg(cx + p + n.o[0]); a[1] = __ldg(cx + p);
-        a[2] = __ldg(cy + p + n.o[2]); a[3] = __ldg(cy + p);
-        a[4] = __ldg(cz + p + n.o[4]); a[5] = __ldg(cz + p);
+        a[0] = cld<RO>(cx + p + n.o[0]); a[1] = cld<RO>(cx + p);
+        a[2] = cld<RO>(cy + p + n.o[2]); a[3] = cld<RO>(cy + p);
+        a[4] = cld<RO>(cz + p + n.o[4]); a[5] = cld<RO>(cz + p);
     }
-    __device__ __forceinline__ T get_diag(long long p, const T *) const { return __ldg(diag + p); }
+    __device__ __forceinline__ T get_diag(long long p, const T *) const { return cld<RO>(diag + p); }
     // (f + sum a u) / diag
-    __device__ __forceinline__ T finish(T s, long long p, const T *) const { return s * __ldg(invd + p); }
+    __device__ __forceinline__ T finish(T s, long long p, const T *) const { return s * cld<RO>(invd + p); }
 };
 
 // Dh = D / (2 h^2) for the arithmetic face mean (face = Dh_p + Dh_j),
 // Dh = D / h^2 for the harmonic mean (face = 2 Dh_p Dh_j / (Dh_p + Dh_j)).
-template <class T, bool HARM>
+template <class T, bool HARM, bool RO = true>
 struct VertCoef {
     const T *Dh, *mu;
     __device__ __forceinline__ static T face(T a, T b) {
@@ -85,12 +93,12 @@ struct VertCoef {
         return a + b;
     }
     __device__ __forceinline__ void couplings(long long p, const Nbr &n, T a[6]) const {
-        T d = __ldg(Dh + p);
+        T d = cld<RO>(Dh + p);
 #pragma unroll
-        for (int q = 0; q < 6; q++) a[q] = face(d, __ldg(Dh + p + n.o[q]));
+        for (int q = 0; q < 6; q++) a[q] = face(d, cld<RO>(Dh + p + n.o[q]));
     }
     __device__ __forceinline__ T get_diag(long long p, const T *a) const {
-        return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
+        return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + cld<RO>(mu + p));
     }
     __device__ __forceinline__ T finish(T s, long long p, const T *a) const {
         return __fdividef(s, get_diag(p, a));
@@ -313,82 +321,154 @@ __device__ __forceinline__ void coarse_solve_block(const Geom &g, const T *Ainv,
 }
 
 
+template <class T>
+__global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const T *__restrict__ f, T *__restrict__ u) {
+    extern __shared__ unsigned char smem_raw[];
+    coarse_solve_block(g, Ainv, n, f, u, reinterpret_cast<T *>(smem_raw));
+}
+
 // ---------------------------------------------------------------------------
-// Single-CTA tail of the V-cycle: the levels from `first` down to the coarsest
-// are small (a few thousand vertices at most), where one launch per operation
-// costs more than the work. One block runs the whole descent (smoothing,
-// defect, restriction), the exact coarsest solve and the ascent
-// (prolongation, smoothing), with a block barrier between operations.
+// Single-CTA tail of the V-cycle: the levels from the first tail level down to
+// the coarsest are small (a few thousand vertices at most), where one launch
+// per operation costs more than the work. One block copies their coefficients
+// and the first tail level's right-hand side into shared memory (same split
+// layout, unpadded rows), runs the whole descent (smoothing, defect,
+// restriction), the exact coarsest solve and the ascent (prolongation,
+// smoothing) there with a block barrier between operations, and writes the
+// first tail level's solution back.
 
 constexpr int kTailMaxLevels = 10;
 
 template <class T, class C>
 struct TailLevel {
-    Geom g;
-    T *u, *f, *r;
-    C c;
+    Geom g;      // global geometry
+    Geom gs;     // shared-memory geometry (hx = number of x positions of one parity)
+    T *u, *f;    // global u and f (used for the first tail level)
+    C c;         // global coefficients
 };
 
 template <class T, class C>
 struct TailArgs {
     TailLevel<T, C> L[kTailMaxLevels];
-    int nl;                          // levels in the tail; L[nl-1] is the coarsest
+    int nl;      // levels in the tail; L[nl-1] is the coarsest
     const T *Ainv;
     int nc;
     int npre, npost, pre_first, post_first;
 };
 
-template <class T, class C>
-__device__ __forceinline__ void tail_half(const TailLevel<T, C> &L, int color) {
-    const int nxi = L.g.nx - 2, nyi = L.g.ny - 2, n = nxi * nyi * (L.g.nz - 2);
+// shared-memory coefficient copies
+template <class T>
+__device__ __forceinline__ FaceCoef<T, false> stage_coef(const FaceCoef<T, true> &cg, const Geom &g, const Geom &gs,
+                                                         T *&cur) {
+    const int n = (int)(gs.sz * gs.nz);
+    T *cx = cur, *cy = cur + n, *cz = cur + 2 * n, *dg = cur + 3 * n, *iv = cur + 4 * n;
+    cur += 5 * n;
+    for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
+        const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+        const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
+        cx[ps] = cg.cx[pg]; cy[ps] = cg.cy[pg]; cz[ps] = cg.cz[pg]; dg[ps] = cg.diag[pg]; iv[ps] = cg.invd[pg];
+    }
+    return FaceCoef<T, false>{cx, cy, cz, dg, iv};
+}
+
+template <class T, bool H>
+__device__ __forceinline__ VertCoef<T, H, false> stage_coef(const VertCoef<T, H, true> &cg, const Geom &g,
+                                                            const Geom &gs, T *&cur) {
+    const int n = (int)(gs.sz * gs.nz);
+    T *dh = cur, *mu = cur + n;
+    cur += 2 * n;
+    for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
+        const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+        const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
+        dh[ps] = cg.Dh[pg]; mu[ps] = cg.mu[pg];
+    }
+    return VertCoef<T, H, false>{dh, mu};
+}
+
+template <class T, class CS>
+__device__ __forceinline__ void tail_half(const Geom &g, T *u, const T *f, const CS &c, int color) {
+    const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
-        if (((i + j + k) & 1) == color) smooth_point(L.g, L.u, L.f, L.c, i, j, k);
+        if (((i + j + k) & 1) == color) smooth_point(g, u, f, c, i, j, k);
     }
     __syncthreads();
 }
 
 template <class T, class C>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
-    extern __shared__ unsigned char smem_raw[];
-    T *fs = reinterpret_cast<T *>(smem_raw);
-    for (int l = 0; l < a.nl - 1; l++) {
-        const TailLevel<T, C> &L = a.L[l], &C1 = a.L[l + 1];
-        for (int sw = 0; sw < a.npre; sw++) {
-            tail_half(L, a.pre_first);
-            tail_half(L, 1 - a.pre_first);
+    using CS = decltype(stage_coef(a.L[0].c, a.L[0].g, a.L[0].gs, *(T **)nullptr));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *cur = reinterpret_cast<T *>(smem_raw);
+    T *su[kTailMaxLevels], *sf[kTailMaxLevels], *sr[kTailMaxLevels];
+    CS sc[kTailMaxLevels];
+    for (int l = 0; l < a.nl; l++) {
+        const int n = (int)(a.L[l].gs.sz * a.L[l].gs.nz);
+        su[l] = cur; sf[l] = cur + n; sr[l] = cur + 2 * n;
+        cur += 3 * n;
+        for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) su[l][t] = T(0);
+        sc[l] = stage_coef(a.L[l].c, a.L[l].g, a.L[l].gs, cur);
+    }
+    T *fs = cur;   // coarsest right-hand side for the dense solve
+    {
+        const Geom &g = a.L[0].g, &gs = a.L[0].gs;
+        __syncthreads();
+        for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
+            const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+            sf[0][gs.pos(i, j, k)] = a.L[0].f[g.pos(i, j, k)];
         }
-        const int nxi = L.g.nx - 2, nyi = L.g.ny - 2, n = nxi * nyi * (L.g.nz - 2);
+    }
+    __syncthreads();
+    for (int l = 0; l < a.nl - 1; l++) {
+        const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
+        for (int sw = 0; sw < a.npre; sw++) {
+            tail_half(g, su[l], sf[l], sc[l], a.pre_first);
+            tail_half(g, su[l], sf[l], sc[l], 1 - a.pre_first);
+        }
+        const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
-            const long long p = L.g.pos(i, j, k);
-            L.r[p] = residual_at(L.u, L.f, L.c, p, neighbours(L.g, i));
+            const long long p = g.pos(i, j, k);
+            sr[l][p] = residual_at(su[l], sf[l], sc[l], p, neighbours(g, i));
         }
         __syncthreads();
-        const int cxi = C1.g.nx - 2, cyi = C1.g.ny - 2, nc = cxi * cyi * (C1.g.nz - 2);
+        const int cxi = gc.nx - 2, cyi = gc.ny - 2, nc = cxi * cyi * (gc.nz - 2);
         for (int t = threadIdx.x; t < nc; t += blockDim.x) {
             const int I = t % cxi + 1, J = (t / cxi) % cyi + 1, K = t / (cxi * cyi) + 1;
-            restrict_point(L.g, L.r, C1.g, C1.f, I, J, K);
-            C1.u[C1.g.pos(I, J, K)] = T(0);
+            restrict_point(g, sr[l], gc, sf[l + 1], I, J, K);
+            su[l + 1][gc.pos(I, J, K)] = T(0);
         }
         __syncthreads();
     }
-    const TailLevel<T, C> &LC = a.L[a.nl - 1];
-    coarse_solve_block(LC.g, a.Ainv, a.nc, LC.f, LC.u, fs);
+    coarse_solve_block(a.L[a.nl - 1].gs, a.Ainv, a.nc, sf[a.nl - 1], su[a.nl - 1], fs);
     __syncthreads();
     for (int l = a.nl - 2; l >= 0; l--) {
-        const TailLevel<T, C> &L = a.L[l], &C1 = a.L[l + 1];
-        const int cx = C1.g.nx - 1, cy = C1.g.ny - 1, ncell = cx * cy * (C1.g.nz - 1);
+        const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
+        const int cx = gc.nx - 1, cy = gc.ny - 1, ncell = cx * cy * (gc.nz - 1);
         for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
             const int I = t % cx, J = (t / cx) % cy, K = t / (cx * cy);
-            prolong_cell(C1.g, C1.u, L.g, L.u, I, J, K);
+            prolong_cell(gc, su[l + 1], g, su[l], I, J, K);
         }
         __syncthreads();
         for (int sw = 0; sw < a.npost; sw++) {
-            tail_half(L, a.post_first);
-            tail_half(L, 1 - a.post_first);
+            tail_half(g, su[l], sf[l], sc[l], a.post_first);
+            tail_half(g, su[l], sf[l], sc[l], 1 - a.post_first);
         }
     }
+    // the first tail level's solution back to global memory (interior)
+    const Geom &g = a.L[0].g, &gs = a.L[0].gs;
+    const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
+        a.L[0].u[g.pos(i, j, k)] = su[0][gs.pos(i, j, k)];
+    }
+}
+
+// shared memory of the tail kernel: u, f, r and the coefficient arrays of every
+// tail level plus the coarsest right-hand side
+template <class T>
+inline size_t tail_smem_elems(const Geom &gs, int ncoef) {
+    return (size_t)gs.sz * gs.nz * (3 + ncoef);
 }
 
 // ---------------------------------------------------------------------------

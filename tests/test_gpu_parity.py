@@ -298,3 +298,18 @@ def test_mixed_iterates_track_fp64_iterates(dmg, shape):
     assert S3.last_info.cycles <= S6.last_info.cycles + 3
     assert S3.last_info.outer <= (S6.last_info.cycles + 2) // 3 + 1
     assert S3.last_info.rel_residual <= 1e-10 and rel(u3, N(u6)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_long_thin_single_level_grid(dmg, precision):
+    # 3 x 3 x 514: one level with 512 unknowns; its FP64 shared-memory tail would
+    # not fit, so the FP64 path uses the grid coarse solve, the FP32 path the tail
+    rng = np.random.default_rng(4)
+    shape = (514, 3, 3)
+    D = np.exp(0.3 * rng.standard_normal(shape))
+    mu = np.full(shape, 0.05)
+    q = rng.uniform(size=shape)
+    S = dmg.Solver(T(D), T(mu), 0.1, precision=precision, rtol=1e-12)
+    assert S.levels() == [shape]
+    u = S.solve(T(q))
+    assert rel(u, oracle.direct_solve(D, mu, 0.1, q)) <= 1e-10
