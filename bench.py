@@ -11,6 +11,12 @@ both converged to relative residual 1e-10. The coefficient hierarchy
 while sources vary, as in the paper's inference use. Every field is 136 MB in
 FP64, larger than the 126 MB L2, so no L2 flush is needed between steps.
 
+The line also carries ``vi_batch``: the batched variational-inference step,
+64 tissue samples of 129^3 (each with its own coefficients, source and
+cotangent) solved forward and pulled back together in one context (one launch
+per kernel and level for all samples), in samples/s, next to the same samples
+run one at a time.
+
 Multi-GPU: a single solve does not shard, so N ranks run N independent replicas
 (weak scaling); the timed region is bracketed by barriers and the max over
 ranks is reported. --impl reference times the FP64 CPU oracle on this host's
@@ -248,6 +254,50 @@ def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
     return dict(seconds=el, h2d=3 * nbytes, d2h=4 * nbytes)
 
 
+def run_vi(dmg, torch, args, world, local, peaks, peak_src):
+    """The batched VI step: B samples x n^3, fwd + VJP of every sample per step,
+    mixed precision; plus the same workload one sample at a time (sample 0's
+    pair time, as a context of batch 1) for comparison."""
+    from paper_2608_00760_b300 import inputs
+    B, n = args.vi_batch, args.vi_size
+    w = inputs.vi_batch(n, B, seed=0)
+    steps = max(3, args.steps // 4)
+    res = run_arm(dmg, torch, w, dmg.DMG_MIXED, steps, 3, world, local,
+                  profile=(dmg.DMG_KERNEL_SMOOTH, True), inner=args.inner)
+    S = res.pop("solver")
+    cyc, rel = S.batch_info()
+    S.close()
+    res.pop("out", None)
+    one = {k: (w[k][0] if k in ("D", "mu", "q", "w") else w[k]) for k in w}
+    one["shape"] = w["shape"][1:]
+    r1 = run_arm(dmg, torch, one, dmg.DMG_MIXED, 3 * steps, 3, world, local, inner=args.inner)
+    r1.pop("solver").close()
+    r1.pop("out", None)
+    ms = res["total_ms"] / steps
+    nint = B * (n - 2) ** 3
+    out = dict(workload="VI step: %d tissue samples x %d^3, fwd+VJP(q,D,mu) of every sample, rtol 1e-10, "
+                        "mixed precision" % (B, n),
+               value=world * B * steps / (res["total_ms"] / 1e3), unit="samples/s (fwd+VJP each)",
+               ms_per_step=ms, p50_ms=percentile(res["per_ms"], 50), p99_ms=percentile(res["per_ms"], 99),
+               gpu_launches_per_step=res["launches"] / steps,
+               cycles_per_sample=dict(fwd_max=res["fwd_cycles"], adj_max=res["adj_cycles"],
+                                      adj_min=min(cyc), adj_rel_max=max(rel)),
+               one_at_a_time=dict(value=world * 3 * steps / (r1["total_ms"] / 1e3), unit="samples/s",
+                                  ms_per_sample=r1["total_ms"] / (3 * steps),
+                                  gpu_launches_per_sample=r1["launches"] / (3 * steps)))
+    pr = res["prof"]
+    if pr and pr["launches"]:
+        dur = pr["total_ms"] / pr["launches"] / 1e3
+        byt = HALF_SWEEP_BYTES_FP32 * nint
+        ach = byt / dur / 1e9
+        pk = peaks.get("hbm_gbs", 6400.0)
+        out["roofline"] = dict(kernel="rbgs_half_sweep_fp32_level0 (all samples)", bound="hbm", achieved=ach,
+                               peak=pk, unit="GB/s", frac=ach / pk, traffic=None,
+                               peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
+                               algorithmic_bytes=byt)
+    return out
+
+
 def cpu_baseline_sample(w, m_fwd, m_adj):
     """Times the FP64 CPU oracle (single-threaded C) on a bounded sample of the
     workload -- one forward V-cycle, one transposed V-cycle, the residual norm
@@ -340,6 +390,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step (mixed)")
+    ap.add_argument("--vi-batch", type=int, default=64, help="samples of the batched VI step (0: skip it)")
+    ap.add_argument("--vi-size", type=int, default=129)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args, int(os.environ.get("RANK", "0")))
@@ -441,6 +493,7 @@ def main():
         out["cpu_baseline"].pop("seconds_per_pair", None)
     else:
         out["cpu_baseline"] = None
+    out["vi_batch"] = run_vi(dmg, torch, args, world, local, peaks, peak_src) if args.vi_batch > 0 else None
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

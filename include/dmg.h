@@ -24,6 +24,14 @@
  * is defined on every vertex (boundary D enters the faces next to the
  * boundary).
  *
+ * Batches: a context set up with batch = B > 1 holds B independent problems of
+ * the same shape and parameters, each with its own D, mu and right-hand side
+ * (the Monte Carlo samples of a variational-inference step, Sec. 2.5). Every
+ * array above is then B such fields one after another, [B][nz][ny][nx]. Each
+ * call runs all samples together, one launch per kernel and level, and each
+ * sample stops at its own rtol: its result is bit for bit the result of the
+ * same sample solved alone with batch = 1.
+ *
  * Streams: every call takes a cudaStream_t (as void*; NULL = legacy default
  * stream) and orders all of its work on it. Calls return after the result has
  * been copied out (convergence tests need the residual norm on the host).
@@ -84,6 +92,8 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 weighting inside, injection on the boundary) or INJECTION.
  *   inner_cycles  FP32 V-cycles per refinement step in mixed mode (default 3:
  *                 each step then gains ~3 decades, far above the FP32 floor).
+ *   batch         independent problems in the context (default 1); needs
+ *                 batch * nz <= 65535.
  */
 typedef struct {
     int nx, ny, nz;
@@ -97,6 +107,7 @@ typedef struct {
     int face_mean;
     int coarsen;
     int inner_cycles;
+    int batch;
 } dmg_params;
 
 #define DMG_HIST_LEN 64
@@ -106,6 +117,9 @@ typedef struct {
  * outer: refinement steps (mixed; equals cycles in FP64); rel_residual: final
  * ||rhs - A x|| / ||rhs|| of the system solved; hist[c]: the relative residual
  * after cycle/step c (first DMG_HIST_LEN entries; not filled in fixed mode).
+ * In a batch: the most cycles and steps of any sample, the largest final
+ * relative residual, and in hist the largest over the samples that ran that
+ * step (dmg_batch_info gives each sample's figures).
  */
 typedef struct {
     int cycles;
@@ -133,7 +147,8 @@ dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, voi
 /*
  * dmg_solve -- u = S(q) (Eq. 2): V-cycles from u = 0 until the relative
  * residual reaches rtol, or exactly fixed_cycles cycles. info may be NULL.
- * Returns DMG_ENOCONV (u still written) when max_cycles is reached first.
+ * Returns DMG_ENOCONV (u still written) when max_cycles is reached first
+ * (in a batch: by any sample).
  */
 dmg_status dmg_solve(dmg_ctx *ctx, const double *q, double *u, dmg_info *info, void *stream);
 
@@ -166,11 +181,20 @@ dmg_status dmg_vjp(dmg_ctx *ctx, const double *u, const double *w, int cycles, d
                    double *Dbar, double *mubar, dmg_info *info, void *stream);
 
 /*
- * dmg_residual -- out[0] = ||q - A u||_2 and out[1] = ||q||_2 over interior
- * vertices, in FP64 (out is a host array of 2 doubles).
+ * dmg_residual -- out[2b] = ||q_b - A_b u_b||_2 and out[2b+1] = ||q_b||_2 over
+ * interior vertices of every sample b, in FP64 (out is a host array of
+ * 2 * batch doubles).
  */
 dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *out,
                         void *stream);
+
+/*
+ * dmg_batch_info -- per-sample report of the last solve/jvp/vjp on the context:
+ * cycles[b] (V-cycles, or FP32 inner V-cycles in mixed mode) and rel[b] (final
+ * relative residual; 0 for a zero right-hand side), host arrays of batch
+ * entries each; either may be NULL. Before any such call every entry is 0.
+ */
+dmg_status dmg_batch_info(const dmg_ctx *ctx, int *cycles, double *rel);
 
 /*
  * dmg_residual_static -- out[0] = ||q - A u||_2 and out[1] = ||q||_2 over

@@ -44,7 +44,7 @@ inline Geom smem_geom(const Geom &g) {
 struct Level {
     Geom g;
     double h;
-    size_t n;   // padded element count
+    size_t n;   // padded element count of all samples (nb * g.sb)
     // FP64
     double *u = nullptr, *f = nullptr, *r = nullptr;
     double *cx = nullptr, *cy = nullptr, *cz = nullptr, *diag = nullptr, *invd = nullptr;
@@ -65,6 +65,7 @@ struct Graph {
 
 struct dmg_ctx {
     dmg_params p;
+    int nb = 1;                       // samples in the batch
     int nlev = 0;
     Level L[kMaxLevels];
     int nc = 0;                       // coarsest interior unknowns
@@ -76,16 +77,24 @@ struct dmg_ctx {
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
-    double *red = nullptr;            // reduction results (device, 4 doubles; slot 3 = kernel error flag)
+    double *red = nullptr;            // reduction results (device, kRedSlots doubles per sample;
+                                      // slot 3 of sample 0 = kernel error flag)
     double *hred = nullptr;           // pinned host copy of red
+    int *act = nullptr;               // device mask: sample still iterating
+    const int *mask = nullptr;        // mask argument of the launches being issued: act, or NULL
+                                      // while every sample iterates (no per-block mask load)
+    int *hact = nullptr;              // pinned host copy of act
+    std::vector<int> bcyc;            // per sample: cycles of the last call
+    std::vector<double> brel;         // per sample: final relative residual of the last call
     dmgk::MixScalars *ms = nullptr;   // device scalars of the mixed-precision loop
     std::vector<void *> dev_allocs;
     unsigned long long launches = 0;
     char err[512] = {0};
     // CUDA graphs of the repeated steps, captured on first use on cap_stream:
-    // [0] forward, [1] transposed
+    // [0] forward, [1] transposed; second index: [0] every sample active
+    // (no mask), [1] masked by act (once some sample of a batch has converged)
     cudaStream_t cap_stream = nullptr;
-    Graph g_mix[2], g_cyc[2], g_fix[2];
+    Graph g_mix[2][2], g_cyc[2][2], g_fix[2][2];
     // profiling: event pairs bracketing launches of one kernel on one level
     int prof_kernel = -1, prof_level = 0, prof_fp32 = 0;
     std::vector<cudaEvent_t> prof_ev;   // 2 per pair
@@ -123,13 +132,17 @@ dmg_status fail(dmg_ctx *c, dmg_status s, const char *fmt, ...) {
 
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// interior launch: block (32, 8), grid over interior x/y, one z-plane per blockIdx.z
+// interior launch: block (32, 8), grid over interior x/y, blockIdx.z = sample * planes + plane
 inline dim3 blk() { return dim3(32, 8, 1); }
 // per-vertex kernels: blockIdx.x = 2 * (32-wide chunk of the half-row) + parity
-inline dim3 grid_int(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nz - 2); }
-inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nz); }
+inline dim3 grid_int(const Geom &g) {
+    return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
+}
+inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb * g.nz); }
 // half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
-inline dim3 grid_half(const Geom &g) { return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nz - 2); }
+inline dim3 grid_half(const Geom &g) {
+    return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
+}
 
 dmg_status check_launch(dmg_ctx *c, const char *what) {
     c->launches++;
@@ -191,8 +204,8 @@ void prof_harvest(dmg_ctx *c, std::vector<int> &pairs, bool release) {
 }
 
 void graphs_reset(dmg_ctx *c) {
-    for (Graph *set : {c->g_mix, c->g_cyc, c->g_fix})
-        for (int t = 0; t < 2; t++) {
+    for (Graph *set : {&c->g_mix[0][0], &c->g_cyc[0][0], &c->g_fix[0][0]})
+        for (int t = 0; t < 4; t++) {
             if (set[t].exec) cudaGraphExecDestroy(set[t].exec);
             for (int idx : set[t].prof) c->prof_free.push_back(idx);
             set[t] = Graph();
@@ -211,30 +224,31 @@ bool is_device_ptr(const void *ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-inline unsigned n_vertex_blocks(const Geom &g) {
-    return (unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256);
+// gather/scatter grid: x over the vertices of one sample, y over samples
+inline dim3 vertex_grid(const Geom &g) {
+    return dim3((unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256), g.nb);
 }
 
 dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s) {
     const Geom &g = c->L[0].g;
-    size_t bytes = (size_t)g.nx * g.ny * g.nz * sizeof(double);
+    size_t bytes = (size_t)g.nx * g.ny * g.nz * g.nb * sizeof(double);
     const double *from = src;
     if (!is_device_ptr(src)) {
         CUDA_TRY(c, cudaMemcpyAsync(c->stage, src, bytes, cudaMemcpyHostToDevice, s));
         from = c->stage;
     }
-    dmgk::k_gather<<<n_vertex_blocks(g), 256, 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
+    dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
     return check_launch(c, "gather");
 }
 
 dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s) {
     const Geom &g = c->L[0].g;
-    size_t bytes = (size_t)g.nx * g.ny * g.nz * sizeof(double);
+    size_t bytes = (size_t)g.nx * g.ny * g.nz * g.nb * sizeof(double);
     if (is_device_ptr(dst)) {
-        dmgk::k_scatter<<<n_vertex_blocks(g), 256, 0, s>>>(g, src, dst);
+        dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
         return check_launch(c, "scatter");
     }
-    dmgk::k_scatter<<<n_vertex_blocks(g), 256, 0, s>>>(g, src, c->stage);
+    dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, c->stage);
     TRY(check_launch(c, "scatter"));
     CUDA_TRY(c, cudaMemcpyAsync(dst, c->stage, bytes, cudaMemcpyDeviceToHost, s));
     return DMG_OK;
@@ -280,7 +294,7 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
             ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
             int color = h == 0 ? first : 1 - first;
             TRY(dispatch<T>(c, l, [&](auto cf) {
-                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color);
+                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color, c->mask);
                 return check_launch(c, "smooth");
             }));
         }
@@ -288,7 +302,8 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
     return DMG_OK;
 }
 
-// f_{l+1} = R (f_l - A_l u_l), u_{l+1} = 0. zero_colour >= 0: the defect
+// f_{l+1} = R (f_l - A_l u_l), u_{l+1} = 0 (the restriction kernels write
+// both). zero_colour >= 0: the defect
 // vanishes on that colour (the last half-sweep updated it), so it is formed on
 // the other colour only and the restriction reads only that colour.
 template <class T>
@@ -298,24 +313,26 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
     if (zero_colour >= 0) {
         const int nz = 1 - zero_colour;   // colour carrying the defect
         TRY(dispatch<T>(c, l, [&](auto cf) {
-            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz);
+            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz,
+                                                                        c->mask);
             return check_launch(c, "residual_colour");
         }));
         // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
         if (nz == 0)
-            dmgk::k_restrict_colour<T, 0><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+            dmgk::k_restrict_colour<T, 0><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
+                                                                           c->mask);
         else
-            dmgk::k_restrict_colour<T, 1><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+            dmgk::k_restrict_colour<T, 1><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
+                                                                           c->mask);
         TRY(check_launch(c, "restrict_colour"));
     } else {
         TRY(dispatch<T>(c, l, [&](auto cf) {
-            dmgk::k_residual<T><<<grid_int(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l));
+            dmgk::k_residual<T><<<grid_int(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), c->mask);
             return check_launch(c, "residual");
         }));
-        dmgk::k_restrict<T><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl));
+        dmgk::k_restrict<T><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl), c->mask);
         TRY(check_launch(c, "restrict"));
     }
-    CUDA_TRY(c, cudaMemsetAsync(U<T>(cl), 0, cl.n * sizeof(T), s));
     return DMG_OK;
 }
 
@@ -323,8 +340,8 @@ template <class T>
 dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
     Level &l = c->L[lev], &cl = c->L[lev + 1];
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
-    dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, cl.g.nz - 1);   // coarse cells
-    dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l));
+    dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, c->nb * (cl.g.nz - 1));   // coarse cells
+    dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
     return check_launch(c, "prolong");
 }
 
@@ -337,7 +354,7 @@ inline dmgk::VertCoef<float, H> make_coef(const Level &l, dmgk::VertCoef<float, 
 }
 
 // The levels tail_first .. nlev-1 of one V-cycle (descent, exact coarsest
-// solve, ascent) in a single one-block launch working in shared memory.
+// solve, ascent) in a launch of one block per sample working in shared memory.
 template <class T>
 dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_first, cudaStream_t s) {
     const int t = sizeof(T) == 4;
@@ -360,7 +377,8 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
         a.npost = npost;
         a.pre_first = pre_first;
         a.post_first = post_first;
-        dmgk::k_vcycle_tail<T, C><<<1, 1024, c->tail_smem[t], s>>>(a);
+        a.act = c->mask;
+        dmgk::k_vcycle_tail<T, C><<<c->nb, 1024, c->tail_smem[t], s>>>(a);
         return check_launch(c, "vcycle_tail");
     });
 }
@@ -371,7 +389,8 @@ template <class T>
 dmg_status coarse_solve(dmg_ctx *c, cudaStream_t s) {
     Level &l = c->L[c->nlev - 1];
     int threads = c->nc < 32 ? 32 : (c->nc > 512 ? 512 : ((c->nc + 31) / 32) * 32);
-    dmgk::k_coarse_solve<T><<<1, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l));
+    dmgk::k_coarse_solve<T><<<c->nb, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l),
+                                                                       c->mask);
     return check_launch(c, "coarse_solve");
 }
 
@@ -396,20 +415,32 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
 }
 
 // --- reductions ------------------------------------------------------------------
-// copy the reduction slots (and the kernel error flag) to pinned host memory
+constexpr int kSlots = dmgk::kRedSlots;
+
+// copy the reduction slots of every sample (and the kernel error flag) to pinned host memory
 dmg_status enqueue_readback(dmg_ctx *c, cudaStream_t s) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, (size_t)kSlots * c->nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                s));
     return DMG_OK;
 }
 
-// wait for the stream, check the kernel error flag, return nslots results
-dmg_status sync_read(dmg_ctx *c, int nslots, cudaStream_t s, double *out) {
+// wait for the stream, check the kernel error flag; the results are in
+// hred[sample * kSlots + slot]
+dmg_status sync_read(dmg_ctx *c, cudaStream_t s) {
     CUDA_TRY(c, cudaStreamSynchronize(s));
     prof_harvest(c, c->prof_direct, true);
     int kerr = 0;
     memcpy(&kerr, c->hred + 3, sizeof(int));
     if (kerr != 0) return fail(c, DMG_ETIMEOUT, "a bounded device wait ran out (kernel error flag %d)", kerr);
-    for (int i = 0; i < nslots; i++) out[i] = c->hred[i];
+    return DMG_OK;
+}
+
+inline double hred(const dmg_ctx *c, int smp, int slot) { return c->hred[smp * kSlots + slot]; }
+
+// the host mask to the device (the next launches see it; a replayed graph
+// reads it at run time)
+dmg_status push_act(dmg_ctx *c, cudaStream_t s) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->act, c->hact, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
     return DMG_OK;
 }
 
@@ -420,30 +451,31 @@ dmg_status end_call(dmg_ctx *c, cudaStream_t s) {
     return DMG_OK;
 }
 
-dmg_status finish_reduce(dmg_ctx *c, int nslots, cudaStream_t s, double *out) {
+dmg_status finish_reduce(dmg_ctx *c, cudaStream_t s) {
     TRY(enqueue_readback(c, s));
-    return sync_read(c, nslots, s, out);
+    return sync_read(c, s);
 }
 
-// ||x||_2^2 over interior of a level-0 FP64 array -> red[slot]
+// ||x||_2^2 over interior of each sample of a level-0 FP64 array -> red[sample][slot]
 dmg_status norm2_async(dmg_ctx *c, const double *x, int slot, cudaStream_t s) {
-    dmgk::k_norm2<<<kNormBlocks, 256, 0, s>>>(c->L[0].g, x, c->partial);
+    dmgk::k_norm2<<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(c->L[0].g, x, c->partial);
     TRY(check_launch(c, "norm2"));
-    dmgk::k_reduce_final<<<1, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot);
+    dmgk::k_reduce_final<<<c->nb, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot, nullptr);
     return check_launch(c, "reduce");
 }
 
-// ||f - A u||^2 (FP64, level 0) -> red[slot]; with r32: the FP32 right-hand side
-// r * 2^-ms->e_prev
-dmg_status resid_norm_async(dmg_ctx *c, const double *u, const double *f, float *r32, int slot, cudaStream_t s) {
+// ||f - A u||^2 (FP64, level 0) of each active sample -> red[sample][slot];
+// with r32: the FP32 right-hand side r * 2^-e_prev
+dmg_status resid_norm_async(dmg_ctx *c, const double *u, const double *f, float *r32, int slot, const int *act,
+                            cudaStream_t s) {
     Level &l = c->L[0];
     {
         ProfScope ps(c, DMG_KERNEL_RESIDUAL, 0, 0, s);
-        dmgk::k_resid_norm<double><<<kNormBlocks, 256, 0, s>>>(l.g, u, f, coef64(l), (double *)nullptr, r32, c->ms,
-                                                               c->partial);
+        dmgk::k_resid_norm<double><<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(l.g, u, f, coef64(l), (double *)nullptr,
+                                                                            r32, c->ms, c->partial, act);
         TRY(check_launch(c, "resid_norm"));
     }
-    dmgk::k_reduce_final<<<1, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot);
+    dmgk::k_reduce_final<<<c->nb, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot, act);
     return check_launch(c, "reduce");
 }
 
@@ -489,6 +521,99 @@ void info_reset(dmg_info *info) {
     memset(info, 0, sizeof(*info));
 }
 
+// --- per-sample convergence -----------------------------------------------------------
+// Every sample of a batch iterates until its own relative residual meets rtol;
+// a sample that has converged is switched off in the device mask, so its
+// iterate is not touched again and it ends with exactly the cycles it would
+// run alone. Samples with a zero right-hand side start converged (u = 0).
+struct Progress {
+    std::vector<double> nf;   // ||f_s||
+    int active = 0;
+};
+
+// after the norms of the right-hand sides are in hred slot 0: set up the mask
+dmg_status progress_start(dmg_ctx *c, Progress &P, dmg_info *info, cudaStream_t s) {
+    c->bcyc.assign(c->nb, 0);
+    c->brel.assign(c->nb, 0.0);
+    P.nf.assign(c->nb, 0.0);
+    P.active = 0;
+    for (int b = 0; b < c->nb; b++) {
+        const double n2 = hred(c, b, 0);
+        if (!std::isfinite(n2)) {
+            if (c->nb == 1) return fail(c, DMG_ENAN, "right-hand side is not finite");
+            return fail(c, DMG_ENAN, "right-hand side of sample %d is not finite", b);
+        }
+        P.nf[b] = std::sqrt(n2);
+        c->hact[b] = P.nf[b] > 0.0;
+        if (c->hact[b]) {
+            c->brel[b] = 1.0;
+            P.active++;
+        }
+    }
+    if (info) { info->cycles = 0; info->outer = 0; info->rel_residual = 0.0; }
+    return P.active ? push_act(c, s) : DMG_OK;
+}
+
+// after step `step` (cycles = cycles of one step) with the residual norms in
+// hred slot 0: record, retire converged samples; done = every sample has
+// converged (or the tolerance is not used: fixed)
+dmg_status progress_step(dmg_ctx *c, Progress &P, int step, int cycles, bool fixed, dmg_info *info, bool &done,
+                         cudaStream_t s) {
+    double worst = 0.0;
+    bool changed = false;
+    for (int b = 0; b < c->nb; b++) {
+        if (!c->hact[b]) continue;
+        const double rn2 = hred(c, b, 0);
+        if (!std::isfinite(rn2)) {
+            if (c->nb == 1) return fail(c, DMG_ENAN, "residual norm is not finite after step %d", step);
+            return fail(c, DMG_ENAN, "residual norm of sample %d is not finite after step %d", b, step);
+        }
+        const double rel = std::sqrt(rn2) / P.nf[b];
+        c->brel[b] = rel;
+        c->bcyc[b] = step * cycles;
+        worst = std::max(worst, rel);
+        if (!fixed && (rel <= c->p.rtol || rn2 == 0.0)) {
+            c->hact[b] = 0;
+            P.active--;
+            changed = true;
+        }
+    }
+    if (info && step - 1 < DMG_HIST_LEN) info->hist[step - 1] = worst;
+    if (info) info->outer = step;
+    done = fixed || P.active == 0;
+    if (changed && !done) TRY(push_act(c, s));
+    return DMG_OK;
+}
+
+// Selects the launch variant for the next step: 0 while every sample iterates
+// (kernels get no mask), 1 once some sample is done (kernels read act). Sets
+// the mask argument the launches issued from now on carry.
+int use_mask(dmg_ctx *c, const Progress &P) {
+    const int m = P.active < c->nb ? 1 : 0;
+    c->mask = m ? c->act : nullptr;
+    return m;
+}
+
+// summary over the batch: most cycles, largest final relative residual
+dmg_status progress_end(dmg_ctx *c, dmg_info *info) {
+    int cyc = 0;
+    double worst = 0.0;
+    for (int b = 0; b < c->nb; b++) {
+        cyc = std::max(cyc, c->bcyc[b]);
+        worst = std::max(worst, c->brel[b]);
+    }
+    if (info) { info->cycles = cyc; info->rel_residual = worst; }
+    for (int b = 0; b < c->nb; b++)
+        if (c->brel[b] > c->p.rtol) {
+            if (c->nb == 1)
+                return fail(c, DMG_ENOCONV, "relative residual %.3e > rtol %.3e after %d cycles", c->brel[b],
+                            c->p.rtol, c->bcyc[b]);
+            return fail(c, DMG_ENOCONV, "sample %d: relative residual %.3e > rtol %.3e after %d cycles", b,
+                        c->brel[b], c->p.rtol, c->bcyc[b]);
+        }
+    return DMG_OK;
+}
+
 // Plain FP64 iteration on level 0: u_0 = 0, then V-cycles on A u_0 = f_0.
 // fixed > 0: exactly `fixed` cycles; else until rtol or max_cycles. One graph
 // replay per cycle (the cycle, and in tolerance mode the residual norm and its
@@ -497,48 +622,40 @@ dmg_status iterate64(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cud
     Level &l = c->L[0];
     const int t = transposed ? 1 : 0;
     CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
-    double nf2;
     TRY(norm2_async(c, l.f, 0, s));
-    TRY(finish_reduce(c, 1, s, &nf2));
-    if (!std::isfinite(nf2)) return fail(c, DMG_ENAN, "right-hand side is not finite");
-    double nf = std::sqrt(nf2);
-    if (info) { info->cycles = 0; info->outer = 0; info->rel_residual = 0.0; }
-    if (nf == 0.0) return DMG_OK;
-    double rel = 1.0;
-    int cyc = 0;
+    TRY(finish_reduce(c, s));
+    Progress P;
+    TRY(progress_start(c, P, info, s));
+    if (P.active == 0) return DMG_OK;
+    bool done = false;
     if (fixed > 0) {
-        TRY(capture(c, c->g_fix[t], [&](cudaStream_t cs) { return vcycle<double>(c, 0, transposed, cs); }));
-        for (cyc = 1; cyc <= fixed; cyc++) TRY(replay(c, c->g_fix[t], s));
-        cyc = fixed;
-        double rn2;
-        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, s));
-        TRY(finish_reduce(c, 1, s, &rn2));
-        prof_harvest(c, c->g_fix[t].prof, false);
-        rel = std::sqrt(rn2) / nf;
-        if (info) { info->cycles = cyc; info->outer = cyc; info->rel_residual = rel; }
-        if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite");
+        const int m = use_mask(c, P);
+        Graph &G = c->g_fix[t][m];
+        TRY(capture(c, G, [&](cudaStream_t cs) { return vcycle<double>(c, 0, transposed, cs); }));
+        for (int cyc = 1; cyc <= fixed; cyc++) TRY(replay(c, G, s));
+        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, c->mask, s));
+        TRY(finish_reduce(c, s));
+        prof_harvest(c, G.prof, false);
+        TRY(progress_step(c, P, 1, fixed, true, nullptr, done, s));
+        if (info) { info->cycles = fixed; info->outer = fixed; }
+        double worst = 0.0;
+        for (double r : c->brel) worst = std::max(worst, r);
+        if (info) info->rel_residual = worst;
         return DMG_OK;
     }
-    TRY(capture(c, c->g_cyc[t], [&](cudaStream_t cs) -> dmg_status {
-        TRY(vcycle<double>(c, 0, transposed, cs));
-        TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, cs));
-        return enqueue_readback(c, cs);
-    }));
-    for (cyc = 1; cyc <= c->p.max_cycles; cyc++) {
-        double rn2;
-        TRY(replay(c, c->g_cyc[t], s));
-        TRY(sync_read(c, 1, s, &rn2));
-        prof_harvest(c, c->g_cyc[t].prof, false);
-        if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite after cycle %d", cyc);
-        rel = std::sqrt(rn2) / nf;
-        if (info && cyc - 1 < DMG_HIST_LEN) info->hist[cyc - 1] = rel;
-        if (rel <= c->p.rtol) break;
+    for (int cyc = 1; cyc <= c->p.max_cycles && !done; cyc++) {
+        Graph &G = c->g_cyc[t][use_mask(c, P)];
+        TRY(capture(c, G, [&](cudaStream_t cs) -> dmg_status {
+            TRY(vcycle<double>(c, 0, transposed, cs));
+            TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, c->mask, cs));
+            return enqueue_readback(c, cs);
+        }));
+        TRY(replay(c, G, s));
+        TRY(sync_read(c, s));
+        prof_harvest(c, G.prof, false);
+        TRY(progress_step(c, P, cyc, 1, false, info, done, s));
     }
-    if (cyc > c->p.max_cycles) cyc = c->p.max_cycles;
-    if (info) { info->cycles = cyc; info->outer = cyc; info->rel_residual = rel; }
-    if (rel > c->p.rtol)
-        return fail(c, DMG_ENOCONV, "relative residual %.3e > rtol %.3e after %d cycles", rel, c->p.rtol, cyc);
-    return DMG_OK;
+    return progress_end(c, info);
 }
 
 // Mixed precision defect correction on level 0 (FP64 u_0, f_0): each step runs
@@ -550,44 +667,34 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
     Level &l = c->L[0];
     const int t = transposed ? 1 : 0;
     CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
-    double nf2;
     TRY(norm2_async(c, l.f, 0, s));
-    dmgk::k_mix_init<<<1, 1, 0, s>>>(c->red, 0, c->ms);
+    dmgk::k_mix_init<<<(c->nb + 127) / 128, 128, 0, s>>>(c->red, 0, c->ms, c->nb);
     TRY(check_launch(c, "mix_init"));
     dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
     TRY(check_launch(c, "to_f32"));
-    TRY(finish_reduce(c, 1, s, &nf2));
-    if (!std::isfinite(nf2)) return fail(c, DMG_ENAN, "right-hand side is not finite");
-    double nf = std::sqrt(nf2);
-    if (info) { info->cycles = 0; info->outer = 0; info->rel_residual = 0.0; }
-    if (nf == 0.0) return DMG_OK;
-    TRY(capture(c, c->g_mix[t], [&](cudaStream_t cs) -> dmg_status {
-        CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), cs));
-        for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
-        dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms);
-        TRY(check_launch(c, "update"));
-        TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, cs));
-        dmgk::k_mix_next<<<1, 1, 0, cs>>>(c->red, 0, c->ms);
-        TRY(check_launch(c, "mix_next"));
-        return enqueue_readback(c, cs);
-    }));
-    double rel = 1.0;
-    int step = 0;
-    for (step = 1; step <= c->p.max_cycles; step++) {
-        double rn2;
-        TRY(replay(c, c->g_mix[t], s));
-        TRY(sync_read(c, 1, s, &rn2));
-        prof_harvest(c, c->g_mix[t].prof, false);
-        if (!std::isfinite(rn2)) return fail(c, DMG_ENAN, "residual norm is not finite after step %d", step);
-        rel = std::sqrt(rn2) / nf;
-        if (info && step - 1 < DMG_HIST_LEN) info->hist[step - 1] = rel;
-        if (rel <= c->p.rtol || rn2 == 0.0) break;
+    TRY(finish_reduce(c, s));
+    Progress P;
+    TRY(progress_start(c, P, info, s));
+    if (P.active == 0) return DMG_OK;
+    bool done = false;
+    for (int step = 1; step <= c->p.max_cycles && !done; step++) {
+        Graph &G = c->g_mix[t][use_mask(c, P)];
+        TRY(capture(c, G, [&](cudaStream_t cs) -> dmg_status {
+            CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), cs));
+            for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
+            dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+            TRY(check_launch(c, "update"));
+            TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
+            dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);
+            TRY(check_launch(c, "mix_next"));
+            return enqueue_readback(c, cs);
+        }));
+        TRY(replay(c, G, s));
+        TRY(sync_read(c, s));
+        prof_harvest(c, G.prof, false);
+        TRY(progress_step(c, P, step, c->p.inner_cycles, false, info, done, s));
     }
-    if (step > c->p.max_cycles) step = c->p.max_cycles;
-    if (info) { info->cycles = step * c->p.inner_cycles; info->outer = step; info->rel_residual = rel; }
-    if (rel > c->p.rtol)
-        return fail(c, DMG_ENOCONV, "relative residual %.3e > rtol %.3e after %d steps", rel, c->p.rtol, step);
-    return DMG_OK;
+    return progress_end(c, info);
 }
 
 dmg_status iterate(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cudaStream_t s) {
@@ -607,12 +714,18 @@ int count_levels(int nx, int ny, int nz) {
     return n;
 }
 
-Geom make_geom(int nx, int ny, int nz) {
+Geom make_geom(int nx, int ny, int nz, int nb) {
     Geom g;
     g.nx = nx; g.ny = ny; g.nz = nz;
     g.hx = (((nx + 1) / 2 + 31) / 32) * 32;
     g.sy = 2 * g.hx;
     g.sz = (long long)g.sy * ny;
+    g.sb = g.sz * nz;
+    g.nb = nb;
+    for (int w = 0; w < 3; w++) {
+        const unsigned long long d = (unsigned long long)(nz - 2 + w);
+        g.mz[w] = d == 1 ? 0u : (unsigned)(((1ULL << 32) + d - 1) / d);
+    }
     return g;
 }
 
@@ -635,6 +748,9 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
         return fail(c, DMG_EINVAL, "bad coarsen");
     if (p->inner_cycles < 1 || p->inner_cycles > 16) return fail(c, DMG_EINVAL, "inner_cycles must be in [1, 16]");
     if (p->symmetric != 0 && p->symmetric != 1) return fail(c, DMG_EINVAL, "symmetric must be 0 or 1");
+    if (p->batch < 1) return fail(c, DMG_EINVAL, "batch must be >= 1");
+    if ((long long)p->batch * p->nz > 65535)
+        return fail(c, DMG_EINVAL, "batch * nz = %lld exceeds 65535", (long long)p->batch * p->nz);
     int nl = count_levels(p->nx, p->ny, p->nz);
     if (nl == 0) return fail(c, DMG_EINVAL, "grid %dx%dx%d cannot be coarsened", p->nx, p->ny, p->nz);
     int cx = p->nx, cy = p->ny, cz = p->nz;
@@ -651,19 +767,21 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     TRY(validate(c, p));
     if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
     c->p = *p;
+    c->nb = p->batch;
+    const int nb = c->nb;
     c->nlev = count_levels(p->nx, p->ny, p->nz);
     bool mixed = p->precision == DMG_MIXED;
     for (int l = 0; l < c->nlev; l++) {
         Level &L = c->L[l];
         if (l == 0) {
-            L.g = make_geom(p->nx, p->ny, p->nz);
+            L.g = make_geom(p->nx, p->ny, p->nz, nb);
             L.h = p->h;
         } else {
             const Level &F = c->L[l - 1];
-            L.g = make_geom((F.g.nx - 1) / 2 + 1, (F.g.ny - 1) / 2 + 1, (F.g.nz - 1) / 2 + 1);
+            L.g = make_geom((F.g.nx - 1) / 2 + 1, (F.g.ny - 1) / 2 + 1, (F.g.nz - 1) / 2 + 1, nb);
             L.h = 2.0 * F.h;
         }
-        L.n = (size_t)L.g.sz * L.g.nz;
+        L.n = (size_t)L.g.sb * nb;
         double **f64[] = {&L.u, &L.f, &L.r, &L.cx, &L.cy, &L.cz, &L.diag, &L.invd, &L.D, &L.mu};
         for (double **q : f64) {
             TRY(dalloc(c, q, L.n));
@@ -678,21 +796,28 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         }
     }
     Level &L0 = c->L[0];
-    TRY(dalloc(c, &c->stage, (size_t)p->nx * p->ny * p->nz));
+    TRY(dalloc(c, &c->stage, (size_t)p->nx * p->ny * p->nz * nb));
     for (double **q : {&c->U0, &c->T1, &c->T2, &c->T3}) {
         TRY(dalloc(c, q, L0.n));
         CUDA_TRY(c, cudaMemsetAsync(*q, 0, L0.n * sizeof(double), s));
     }
-    TRY(dalloc(c, &c->partial, kNormBlocks));
-    TRY(dalloc(c, &c->red, 4));
-    TRY(dalloc(c, &c->ms, 1));
-    CUDA_TRY(c, cudaMemsetAsync(c->ms, 0, sizeof(dmgk::MixScalars), s));
+    TRY(dalloc(c, &c->partial, (size_t)kNormBlocks * nb));
+    TRY(dalloc(c, &c->red, (size_t)kSlots * nb));
+    TRY(dalloc(c, &c->ms, nb));
+    TRY(dalloc(c, &c->act, nb));
+    CUDA_TRY(c, cudaMemsetAsync(c->ms, 0, nb * sizeof(dmgk::MixScalars), s));
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    CUDA_TRY(c, cudaMemsetAsync(c->red, 0, 4 * sizeof(double), s));
+    CUDA_TRY(c, cudaMemsetAsync(c->red, 0, (size_t)kSlots * nb * sizeof(double), s));
     {
-        cudaError_t e = cudaMallocHost(&c->hred, 4 * sizeof(double));
+        cudaError_t e = cudaMallocHost(&c->hred, (size_t)kSlots * nb * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost(&c->hact, nb * sizeof(int));
         if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+        memset(c->hred, 0, (size_t)kSlots * nb * sizeof(double));
+        for (int b = 0; b < nb; b++) c->hact[b] = 1;
     }
+    TRY(push_act(c, s));
+    c->bcyc.assign(nb, 0);
+    c->brel.assign(nb, 0.0);
     // level-0 coefficients from the caller, then coarsen level by level
     TRY(stage_in(c, D, L0.D, false, s));
     TRY(stage_in(c, mu, L0.mu, false, s));
@@ -752,25 +877,31 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
             attr = true;
         }
     }
-    // exact coarsest solve: dense SPD inverse by in-block Gauss-Jordan
+    // exact coarsest solve: dense SPD inverse of every sample by in-block Gauss-Jordan
     Level &LC = c->L[c->nlev - 1];
     c->nc = (LC.g.nx - 2) * (LC.g.ny - 2) * (LC.g.nz - 2);
+    const size_t nc2 = (size_t)c->nc * c->nc;
     double *M = nullptr;
     int *status = nullptr;
-    TRY(dalloc(c, &M, (size_t)c->nc * 2 * c->nc));
-    TRY(dalloc(c, &c->Ainv, (size_t)c->nc * c->nc));
-    TRY(dalloc(c, &c->Ainv32, (size_t)c->nc * c->nc));
-    TRY(dalloc(c, &status, 1));
-    CUDA_TRY(c, cudaMemsetAsync(status, 0xff, sizeof(int), s));
-    dmgk::k_coarse_assemble<<<64, 256, 0, s>>>(LC.g, coef64(LC), c->nc, M);
+    TRY(dalloc(c, &M, 2 * nc2 * nb));
+    TRY(dalloc(c, &c->Ainv, nc2 * nb));
+    TRY(dalloc(c, &c->Ainv32, nc2 * nb));
+    TRY(dalloc(c, &status, nb));
+    CUDA_TRY(c, cudaMemsetAsync(status, 0xff, nb * sizeof(int), s));
+    dmgk::k_coarse_assemble<<<dim3(64, nb), 256, 0, s>>>(LC.g, coef64(LC), c->nc, M);
     TRY(check_launch(c, "coarse_assemble"));
-    dmgk::k_gauss_jordan<<<1, 1024, 0, s>>>(M, c->nc, c->Ainv, c->Ainv32, status);
+    dmgk::k_gauss_jordan<<<nb, 1024, 0, s>>>(M, c->nc, c->Ainv, c->Ainv32, status);
     TRY(check_launch(c, "gauss_jordan"));
-    int hstatus = -1;
-    CUDA_TRY(c, cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> hstatus(nb, -1);
+    CUDA_TRY(c, cudaMemcpyAsync(hstatus.data(), status, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
-    if (hstatus != 0)
-        return fail(c, DMG_EINVAL, "coarsest-level matrix is not positive definite (need D > 0, mu >= 0)");
+    for (int b = 0; b < nb; b++)
+        if (hstatus[b] != 0) {
+            if (nb == 1)
+                return fail(c, DMG_EINVAL, "coarsest-level matrix is not positive definite (need D > 0, mu >= 0)");
+            return fail(c, DMG_EINVAL,
+                        "coarsest-level matrix of sample %d is not positive definite (need D > 0, mu >= 0)", b);
+        }
     return DMG_OK;
 }
 
@@ -805,6 +936,7 @@ void dmg_default_params(dmg_params *p) {
     p->face_mean = DMG_FACE_ARITHMETIC;
     p->coarsen = DMG_COARSEN_FULL_WEIGHTING;
     p->inner_cycles = 3;
+    p->batch = 1;
 }
 
 dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, void *stream, dmg_ctx **out) {
@@ -906,13 +1038,14 @@ dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *ou
         Level &l = c->L[0];
         TRY(stage_in(c, q, c->T3, false, s));
         TRY(stage_in(c, u, c->U0, true, s));
-        TRY(resid_norm_async(c, c->U0, c->T3, nullptr, 0, s));
+        TRY(resid_norm_async(c, c->U0, c->T3, nullptr, 0, nullptr, s));
         TRY(norm2_async(c, c->T3, 1, s));
-        double r[2];
-        TRY(finish_reduce(c, 2, s, r));
+        TRY(finish_reduce(c, s));
         (void)l;
-        out[0] = std::sqrt(r[0]);
-        out[1] = std::sqrt(r[1]);
+        for (int b = 0; b < c->nb; b++) {
+            out[2 * b] = std::sqrt(hred(c, b, 0));
+            out[2 * b + 1] = std::sqrt(hred(c, b, 1));
+        }
         return DMG_OK;
     });
 }
@@ -925,6 +1058,7 @@ dmg_status dmg_destroy(dmg_ctx *c) {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (void *q : c->dev_allocs) cudaFree(q);
     if (c->hred) cudaFreeHost(c->hred);
+    if (c->hact) cudaFreeHost(c->hact);
     delete c;
     return DMG_OK;
 }
@@ -945,6 +1079,15 @@ const char *dmg_strerror(dmg_status s) {
 const char *dmg_last_error(const dmg_ctx *c) {
     if (!c) return g_setup_err;
     return c->err;
+}
+
+dmg_status dmg_batch_info(const dmg_ctx *c, int *cycles, double *rel) {
+    if (!c) return DMG_EINVAL;
+    for (int b = 0; b < c->nb; b++) {
+        if (cycles) cycles[b] = c->bcyc[b];
+        if (rel) rel[b] = c->brel[b];
+    }
+    return DMG_OK;
 }
 
 int dmg_levels(const dmg_ctx *c) { return c ? c->nlev : 0; }

@@ -11,6 +11,15 @@
 // keep the parity of x (same half, same index); neighbours along x sit in the
 // other half (offsets xm/xp below). Boundary values of u, f and r are zero and
 // no kernel writes them.
+//
+// Batches: a context may hold nb independent problems of the same shape (one
+// coefficient field and right-hand side each). Every array stores them one
+// after another, sb elements apart; grid kernels take the sample from
+// blockIdx.z (sample * planes + plane) and single-block kernels from their
+// block index, and shift their pointers by sample * sb at entry. Per-step
+// kernels take a device mask act[sample] (NULL: all active) so that a
+// converged sample stops while the others continue: each sample then runs
+// exactly the arithmetic it would run alone.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,6 +31,13 @@ struct Geom {
     int hx;           // half-row length (elements)
     int sy;           // row pitch = 2 hx
     long long sz;     // plane pitch = ny sy
+    long long sb;     // sample pitch = nz sz
+    int nb;           // samples
+    // ceil(2^32 / d) for d = nz - 2, nz - 1, nz (interior planes, cell planes,
+    // all planes); 0 when d == 1. Splits blockIdx.z = sample * d + plane with
+    // one multiply-high: for n, d < 2^16, floor(n m / 2^32) = floor(n / d)
+    // because m d - 2^32 = e < d makes the excess n e / (d 2^32) < 1 / d.
+    unsigned mz[3];
     __host__ __device__ __forceinline__ long long pos(int i, int j, int k) const {
         return (long long)k * sz + (long long)j * sy + (i & 1) * hx + (i >> 1);
     }
@@ -31,6 +47,19 @@ struct Geom {
     // number of x positions of one parity: even i = 0..nx-1 -> (nx+1)/2
     __host__ __device__ __forceinline__ int nhalf() const { return (nx + 1) / 2; }
 };
+
+enum { kInterior = 0, kCells = 1, kAll = 2 };
+
+// blockIdx.z = sample * d + plane with d = g.nz - 2 + which: returns the
+// sample and sets the plane
+__device__ __forceinline__ int zsplit(const Geom &g, int which, int &plane) {
+    const unsigned z = blockIdx.z, m = g.mz[which];
+    const int smp = m ? (int)__umulhi(z, m) : (int)z;
+    plane = (int)z - smp * (g.nz - 2 + which);
+    return smp;
+}
+
+__device__ __forceinline__ bool inactive(const int *act, int smp) { return act != nullptr && __ldg(act + smp) == 0; }
 
 // Thread mapping shared by the per-vertex kernels: blockIdx.x = 2*b + parity,
 // threadIdx.x (32 wide) walks the half-row index m, so i = 2m + parity and a
@@ -79,6 +108,9 @@ struct FaceCoef {
         a[4] = cld<RO>(cz + p + n.o[4]); a[5] = cld<RO>(cz + p);
     }
     __device__ __forceinline__ T get_diag(long long p, const T *) const { return cld<RO>(diag + p); }
+    __device__ __forceinline__ FaceCoef shifted(long long o) const {
+        return FaceCoef{cx + o, cy + o, cz + o, diag + o, invd + o};
+    }
     // (f + sum a u) / diag
     __device__ __forceinline__ T finish(T s, long long p, const T *) const { return s * cld<RO>(invd + p); }
 };
@@ -103,6 +135,7 @@ struct VertCoef {
     __device__ __forceinline__ T finish(T s, long long p, const T *a) const {
         return __fdividef(s, get_diag(p, a));
     }
+    __device__ __forceinline__ VertCoef shifted(long long o) const { return VertCoef{Dh + o, mu + o}; }
 };
 
 // s + sum_q a_q u(p + o_q). FP64: one FMA chain (6 FP64-pipe ops, the B300's
@@ -216,8 +249,14 @@ __device__ __forceinline__ void prolong_cell(const Geom &gc, const T *e, const G
 // one contiguous half-row.
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, const T *__restrict__ f, C c,
-                                                     int color) {
-    const int k = blockIdx.z + 1;
+                                                     int color, const int *act) {
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
+    if (inactive(act, smp)) return;
+    u += smp * g.sb;
+    f += smp * g.sb;
+    c = c.shifted(smp * g.sb);
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int par = (color + j + k) & 1;                                       // parity of i of this colour
     const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;   // 1, 3, ... or 2, 4, ...
@@ -228,23 +267,37 @@ __global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, 
 // r = f - A u on interior vertices (the defect, Eqs. 13-14)
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_residual(Geom g, const T *__restrict__ u, const T *__restrict__ f, C c,
-                                                  T *__restrict__ r) {
+                                                  T *__restrict__ r, const int *act) {
     int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
+    if (inactive(act, smp)) return;
+    u += smp * g.sb;
+    f += smp * g.sb;
+    r += smp * g.sb;
+    c = c.shifted(smp * g.sb);
     if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
     long long p = g.pos(i, j, k);
     r[p] = residual_at(u, f, c, p, neighbours(g, i));
 }
 
-// f_{l+1} = R r_l on coarse interior vertices
+// f_{l+1} = R r_l and u_{l+1} = 0 on coarse interior vertices
 template <class T>
-__global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__ r, Geom gc, T *__restrict__ fc) {
+__global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__ r, Geom gc, T *__restrict__ fc,
+                                                  T *__restrict__ uc, const int *act) {
     int I = vertex_i();
     int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int K = blockIdx.z + 1;
+    int K;
+    const int smp = zsplit(gc, kInterior, K);
+    K += 1;
+    if (inactive(act, smp)) return;
+    r += smp * gf.sb;
+    fc += smp * gc.sb;
     if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
     restrict_point(gf, r, gc, fc, I, J, K);
+    uc[smp * gc.sb + gc.pos(I, J, K)] = T(0);
 }
 
 // Defect on one colour only. Right after a Gauss-Seidel half-sweep of colour X
@@ -253,8 +306,15 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
 // other colour; r is written there and nowhere else.
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__restrict__ u, const T *__restrict__ f,
-                                                         C c, T *__restrict__ r, int color) {
-    const int k = blockIdx.z + 1;
+                                                         C c, T *__restrict__ r, int color, const int *act) {
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
+    if (inactive(act, smp)) return;
+    u += smp * g.sb;
+    f += smp * g.sb;
+    r += smp * g.sb;
+    c = c.shifted(smp * g.sb);
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int par = (color + j + k) & 1;
     const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;
@@ -269,10 +329,15 @@ __global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__rest
 // nonzero defect; the other r entries are not read.
 template <class T, int PAR>
 __global__ void __launch_bounds__(256) k_restrict_colour(Geom gf, const T *__restrict__ r, Geom gc,
-                                                         T *__restrict__ fc) {
+                                                         T *__restrict__ fc, T *__restrict__ uc, const int *act) {
     const int I = vertex_i();
     const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int K = blockIdx.z + 1;
+    int K;
+    const int smp = zsplit(gc, kInterior, K);
+    K += 1;
+    if (inactive(act, smp)) return;
+    r += smp * gf.sb;
+    fc += smp * gc.sb;
     if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
     const long long p = gf.pos(2 * I, 2 * J, 2 * K);
     const int om = gf.xm(2 * I), op = gf.xp(2 * I);
@@ -290,14 +355,20 @@ __global__ void __launch_bounds__(256) k_restrict_colour(Geom gf, const T *__res
             }
         }
     fc[gc.pos(I, J, K)] = s * T(1.0 / 64.0);
+    uc[smp * gc.sb + gc.pos(I, J, K)] = T(0);
 }
 
 // u_l += I u_{l+1}, one thread per coarse cell
 template <class T>
-__global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u) {
+__global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u,
+                                                     const int *act) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = blockIdx.z;
+    int K;
+    const int smp = zsplit(gc, kCells, K);
+    if (inactive(act, smp)) return;
+    e += smp * gc.sb;
+    u += smp * gf.sb;
     if (I > gc.nx - 2 || J > gc.ny - 2) return;
     prolong_cell(gc, e, gf, u, I, J, K);
 }
@@ -321,10 +392,15 @@ __device__ __forceinline__ void coarse_solve_block(const Geom &g, const T *Ainv,
 }
 
 
+// one block per sample
 template <class T>
-__global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const T *__restrict__ f, T *__restrict__ u) {
+__global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const T *__restrict__ f, T *__restrict__ u,
+                               const int *act) {
     extern __shared__ unsigned char smem_raw[];
-    coarse_solve_block(g, Ainv, n, f, u, reinterpret_cast<T *>(smem_raw));
+    const int smp = blockIdx.x;
+    if (inactive(act, smp)) return;
+    coarse_solve_block(g, Ainv + (long long)smp * n * n, n, f + smp * g.sb, u + smp * g.sb,
+                       reinterpret_cast<T *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -354,6 +430,7 @@ struct TailArgs {
     const T *Ainv;
     int nc;
     int npre, npost, pre_first, post_first;
+    const int *act;
 };
 
 // shared-memory coefficient copies
@@ -395,10 +472,13 @@ __device__ __forceinline__ void tail_half(const Geom &g, T *u, const T *f, const
     __syncthreads();
 }
 
+// one block per sample
 template <class T, class C>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
     using CS = decltype(stage_coef(a.L[0].c, a.L[0].g, a.L[0].gs, *(T **)nullptr));
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int smp = blockIdx.x;
+    if (inactive(a.act, smp)) return;
     T *cur = reinterpret_cast<T *>(smem_raw);
     T *su[kTailMaxLevels], *sf[kTailMaxLevels], *sr[kTailMaxLevels];
     CS sc[kTailMaxLevels];
@@ -407,7 +487,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
         su[l] = cur; sf[l] = cur + n; sr[l] = cur + 2 * n;
         cur += 3 * n;
         for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) su[l][t] = T(0);
-        sc[l] = stage_coef(a.L[l].c, a.L[l].g, a.L[l].gs, cur);
+        sc[l] = stage_coef(a.L[l].c.shifted(smp * a.L[l].g.sb), a.L[l].g, a.L[l].gs, cur);
     }
     T *fs = cur;   // coarsest right-hand side for the dense solve
     {
@@ -415,7 +495,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
         __syncthreads();
         for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
             const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
-            sf[0][gs.pos(i, j, k)] = a.L[0].f[g.pos(i, j, k)];
+            sf[0][gs.pos(i, j, k)] = a.L[0].f[smp * g.sb + g.pos(i, j, k)];
         }
     }
     __syncthreads();
@@ -440,7 +520,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
         }
         __syncthreads();
     }
-    coarse_solve_block(a.L[a.nl - 1].gs, a.Ainv, a.nc, sf[a.nl - 1], su[a.nl - 1], fs);
+    coarse_solve_block(a.L[a.nl - 1].gs, a.Ainv + (long long)smp * a.nc * a.nc, a.nc, sf[a.nl - 1], su[a.nl - 1],
+                       fs);
     __syncthreads();
     for (int l = a.nl - 2; l >= 0; l--) {
         const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
@@ -460,7 +541,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
     const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
-        a.L[0].u[g.pos(i, j, k)] = su[0][gs.pos(i, j, k)];
+        a.L[0].u[smp * g.sb + g.pos(i, j, k)] = su[0][gs.pos(i, j, k)];
     }
 }
 
@@ -473,18 +554,20 @@ inline size_t tail_smem_elems(const Geom &gs, int ncoef) {
 
 // ---------------------------------------------------------------------------
 // layout conversion between the caller's contiguous [nz][ny][nx] arrays and the
-// split level-0 layout (one thread per vertex, coalesced on the contiguous side)
+// split level-0 layout (one thread per vertex, coalesced on the contiguous side;
+// blockIdx.y = sample)
 
 // dst = src on every vertex, or on interior vertices only with zeros on the
 // boundary (zero_boundary != 0)
 __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict__ src,
                                                 double *__restrict__ dst, int zero_boundary) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)g.nx * g.ny * g.nz;
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned n = (unsigned)g.nx * g.ny * g.nz;
     if (t >= n) return;
-    int i = (int)(t % g.nx);
-    long long r = t / g.nx;
-    int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    src += (long long)blockIdx.y * n;
+    dst += blockIdx.y * g.sb;
+    const unsigned r = t / g.nx;
+    const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
     double v = src[t];
     if (zero_boundary && (i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1))
         v = 0.0;
@@ -493,22 +576,24 @@ __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict
 
 __global__ void __launch_bounds__(256) k_scatter(Geom g, const double *__restrict__ src,
                                                  double *__restrict__ dst) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)g.nx * g.ny * g.nz;
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned n = (unsigned)g.nx * g.ny * g.nz;
     if (t >= n) return;
-    int i = (int)(t % g.nx);
-    long long r = t / g.nx;
-    int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    src += blockIdx.y * g.sb;
+    dst += (long long)blockIdx.y * n;
+    const unsigned r = t / g.nx;
+    const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
     dst[t] = src[g.pos(i, j, k)];
 }
 
 // ---------------------------------------------------------------------------
 // setup kernels (one thread per vertex, boundary included)
 
-__device__ __forceinline__ bool vertex_ijk(const Geom &g, int &i, int &j, int &k) {
+// all vertices of every sample: grid z = nb * nz; returns the sample in smp
+__device__ __forceinline__ bool vertex_ijk(const Geom &g, int &i, int &j, int &k, int &smp) {
     i = vertex_i();
     j = blockIdx.y * blockDim.y + threadIdx.y;
-    k = blockIdx.z;
+    smp = zsplit(g, kAll, k);
     return i < g.nx && j < g.ny;
 }
 
@@ -517,8 +602,10 @@ __device__ __forceinline__ bool vertex_ijk(const Geom &g, int &i, int &j, int &k
 // everywhere).
 __global__ void k_coarsen(Geom gf, const double *__restrict__ X, Geom gc, double *__restrict__ Xc,
                           int inject) {
-    int I, J, K;
-    if (!vertex_ijk(gc, I, J, K)) return;
+    int I, J, K, smp;
+    if (!vertex_ijk(gc, I, J, K, smp)) return;
+    X += smp * gf.sb;
+    Xc += smp * gc.sb;
     bool interior = I > 0 && J > 0 && K > 0 && I < gc.nx - 1 && J < gc.ny - 1 && K < gc.nz - 1;
     double s;
     if (inject || !interior) {
@@ -543,9 +630,12 @@ __device__ __forceinline__ double face_mean(double a, double b, int harm) {
 // face), diagonal and its reciprocal.
 __global__ void k_build_faces(Geom g, const double *__restrict__ D, const double *__restrict__ mu, double ih2,
                               int harm, double *cx, double *cy, double *cz, double *diag, double *invd) {
-    int i, j, k;
-    if (!vertex_ijk(g, i, j, k)) return;
-    long long p = g.pos(i, j, k);
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long p = g.pos(i, j, k), o = smp * g.sb;
+    D += o;
+    mu += o;
+    cx += o; cy += o; cz += o; diag += o; invd += o;
     double d = D[p];
     cx[p] = i < g.nx - 1 ? face_mean(d, D[p + g.xp(i)], harm) * ih2 : 0.0;
     cy[p] = j < g.ny - 1 ? face_mean(d, D[p + g.sy], harm) * ih2 : 0.0;
@@ -567,17 +657,20 @@ __global__ void k_build_faces(Geom g, const double *__restrict__ D, const double
 // FP32 vertex coefficients for the inner V-cycles: Dh = D * scale, mu32 = mu.
 __global__ void k_build_vertex32(Geom g, const double *__restrict__ D, const double *__restrict__ mu, double scale,
                                  float *Dh, float *mu32) {
-    int i, j, k;
-    if (!vertex_ijk(g, i, j, k)) return;
-    long long p = g.pos(i, j, k);
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long p = g.pos(i, j, k) + smp * g.sb;
     Dh[p] = (float)(D[p] * scale);
     mu32[p] = (float)mu[p];
 }
 
 // Dense coarsest matrix (n x n, interior unknowns in x-fastest order) from the
 // FP64 faces; row-major into M with row stride 2n (the right half is set to I).
+// blockIdx.y = sample; sample s writes M + s * 2 n^2.
 __global__ void k_coarse_assemble(Geom g, FaceCoef<double> c, int n, double *M) {
     int nxi = g.nx - 2, nyi = g.ny - 2;
+    c = c.shifted(blockIdx.y * g.sb);
+    M += (long long)blockIdx.y * 2 * n * n;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * 2 * n;
          t += (long long)gridDim.x * blockDim.x) {
         int r = (int)(t / (2 * n)), col = (int)(t % (2 * n));
@@ -603,12 +696,17 @@ __global__ void k_coarse_assemble(Geom g, FaceCoef<double> c, int n, double *M) 
 
 // In-block Gauss-Jordan inversion of the SPD matrix in [M | I] (no pivoting is
 // needed for SPD). Writes the symmetrised inverse in FP64 and FP32 and sets
-// *status = 1 if a pivot is not positive. One block; n <= 512.
+// *status = 1 if a pivot is not positive. One block per sample (blockIdx.x);
+// n <= 512.
 __global__ void k_gauss_jordan(double *M, int n, double *Ainv, float *Ainv32, int *status) {
     __shared__ double colk[512];
     __shared__ double piv;
     __shared__ int bad;
     int n2 = 2 * n;
+    M += (long long)blockIdx.x * n * n2;
+    Ainv += (long long)blockIdx.x * n * n;
+    Ainv32 += (long long)blockIdx.x * n * n;
+    status += blockIdx.x;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     for (int k = 0; k < n; k++) {
@@ -720,29 +818,51 @@ __device__ __forceinline__ double f32_to_f64_shift(float x, int shift) {
     return __longlong_as_double((long long)(sign | (de << 52) | m));
 }
 
-// ms from the first norm: the FP32 right-hand side will be f * 2^-e(||f||)
-__global__ void k_mix_init(const double *red, int slot, MixScalars *ms) {
-    int e = exponent_of(sqrt(red[slot]));
-    ms->e_cur = e;
-    ms->e_prev = e;
+// reduction results: kRedSlots doubles per sample
+constexpr int kRedSlots = 4;
+
+// ms from the first norm: the FP32 right-hand side will be f * 2^-e(||f||).
+// One thread per sample.
+__global__ void k_mix_init(const double *red, int slot, MixScalars *ms, int nb) {
+    const int smp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (smp >= nb) return;
+    int e = exponent_of(sqrt(red[smp * kRedSlots + slot]));
+    ms[smp].e_cur = e;
+    ms[smp].e_prev = e;
 }
 
 // after a refinement step: the new FP32 right-hand side carries 2^-e_prev
-__global__ void k_mix_next(const double *red, int slot, MixScalars *ms) {
-    ms->e_cur = ms->e_prev;
-    ms->e_prev = exponent_of(sqrt(red[slot]));
+__global__ void k_mix_next(const double *red, int slot, MixScalars *ms, int nb, const int *act) {
+    const int smp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (smp >= nb || inactive(act, smp)) return;
+    ms[smp].e_cur = ms[smp].e_prev;
+    ms[smp].e_prev = exponent_of(sqrt(red[smp * kRedSlots + slot]));
 }
 
-// partial[b] = sum over this block's interior vertices of (f - A u)^2; optional
-// outputs: r (same type) and the FP32 right-hand side r32 = r * 2^-ms->e_prev.
+// Reductions run gridDim.x blocks per sample (blockIdx.y = sample) whatever the
+// batch, so a sample's sums are the same in a batch and alone.
+//
+// partial[s][b] = sum over block b's interior vertices of sample s of (f - A u)^2;
+// optional outputs: r (same type) and the FP32 right-hand side r32 = r * 2^-e_prev.
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_resid_norm(Geom g, const T *__restrict__ u, const T *__restrict__ f,
                                                     C c, T *__restrict__ rout, float *__restrict__ r32,
-                                                    const MixScalars *ms, double *partial) {
+                                                    const MixScalars *ms, double *partial, const int *act) {
     __shared__ double sh[8];
+    const int smp = blockIdx.y;
+    if (inactive(act, smp)) return;
+    {
+        const long long o = smp * g.sb;
+        u += o;
+        f += o;
+        c = c.shifted(o);
+        if (rout) rout += o;
+        if (r32) r32 += o;
+        partial += smp * gridDim.x;
+    }
     int nxi = g.nx - 2, nyi = g.ny - 2, nzi = g.nz - 2;
     unsigned total = (unsigned)nxi * nyi * nzi;
-    int shift = r32 ? -ms->e_prev : 0;
+    int shift = r32 ? -ms[smp].e_prev : 0;
     double acc = 0.0;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         int i, j, k;
@@ -757,9 +877,11 @@ __global__ void __launch_bounds__(256) k_resid_norm(Geom g, const T *__restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// partial[b] = sum over this block's interior vertices of x^2
+// partial[s][b] = sum over block b's interior vertices of sample s of x^2
 __global__ void __launch_bounds__(256) k_norm2(Geom g, const double *__restrict__ x, double *partial) {
     __shared__ double sh[8];
+    x += blockIdx.y * g.sb;
+    partial += blockIdx.y * gridDim.x;
     int nxi = g.nx - 2, nyi = g.ny - 2, nzi = g.nz - 2;
     unsigned total = (unsigned)nxi * nyi * nzi;
     double acc = 0.0;
@@ -773,9 +895,14 @@ __global__ void __launch_bounds__(256) k_norm2(Geom g, const double *__restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// out[slot] = sum of partial[0..n) in a fixed order (one block of 256 threads)
-__global__ void k_reduce_final(const double *__restrict__ partial, int n, double *out, int slot) {
+// out[s][slot] = sum of partial[s][0..n) in a fixed order (one block of 256
+// threads per sample)
+__global__ void k_reduce_final(const double *__restrict__ partial, int n, double *out, int slot, const int *act) {
     __shared__ double sh[8];
+    const int smp = blockIdx.x;
+    if (inactive(act, smp)) return;
+    partial += (long long)smp * n;
+    out += smp * kRedSlots;
     double acc = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) acc += partial[t];
     double s = block_sum(acc, sh);
@@ -797,8 +924,14 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, const double *__restrict__
                                               const double *__restrict__ lam, const double *__restrict__ D,
                                               double ih2, int harm, double *__restrict__ Dbar,
                                               double *__restrict__ mubar) {
-    int i, j, k;
-    if (!vertex_ijk(g, i, j, k)) return;
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long o = smp * g.sb;
+    u += o;
+    lam += o;
+    D += o;
+    if (Dbar) Dbar += o;
+    if (mubar) mubar += o;
     long long p = g.pos(i, j, k);
     double uv = u[p], lv = lam[p];
     double dv = harm ? D[p] : 0.0;
@@ -823,8 +956,16 @@ __global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u
                                             double ih2, int harm, double *__restrict__ f) {
     int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
     if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
+    const long long o = smp * g.sb;
+    u += o;
+    D += o;
+    f += o;
+    if (dD) dD += o;
+    if (dmu) dmu += o;
     long long p = g.pos(i, j, k);
     double up = u[p];
     double s = 0.0;
@@ -844,13 +985,15 @@ __global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u
 
 // mixed precision: u64 += e32 * 2^ms->e_cur on interior vertices (1 FP64 add)
 __global__ void __launch_bounds__(256) k_update(Geom g, double *__restrict__ u, const float *__restrict__ e,
-                                                const MixScalars *ms) {
+                                                const MixScalars *ms, const int *act) {
     int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.pos(i, j, k);
-    u[p] += f32_to_f64_shift(e[p], ms->e_cur);
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2 || inactive(act, smp)) return;
+    long long p = g.pos(i, j, k) + smp * g.sb;
+    u[p] += f32_to_f64_shift(e[p], ms[smp].e_cur);
 }
 
 // y = x * 2^-ms->e_cur in FP32 on interior vertices
@@ -858,10 +1001,12 @@ __global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict
                                                 float *__restrict__ y) {
     int i = vertex_i();
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
     if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.pos(i, j, k);
-    y[p] = f64_to_f32_shift(x[p], -ms->e_cur);
+    long long p = g.pos(i, j, k) + smp * g.sb;
+    y[p] = f64_to_f32_shift(x[p], -ms[smp].e_cur);
 }
 
 }  // namespace dmgk

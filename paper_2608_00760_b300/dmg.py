@@ -5,6 +5,8 @@ CPU), a numpy array, or None where the C API allows NULL; each must be a
 C-contiguous float64 array of nx*ny*nz elements in [nz][ny][nx] order. The
 stream defaults to torch's current CUDA stream. Every computation runs in the
 library's CUDA kernels; when the library is missing the first call raises.
+A context set up with ``batch = B`` takes B such fields back to back,
+[B][nz][ny][nx].
 
 ``Solver`` is a small convenience owner of one context (setup/destroy) whose
 methods allocate torch outputs and raise ``DMGError`` on a failing status.
@@ -31,7 +33,7 @@ class dmg_params(ctypes.Structure):
                 ("h", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("fixed_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("face_mean", ctypes.c_int),
-                ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class dmg_info(ctypes.Structure):
@@ -45,7 +47,8 @@ class dmg_info(ctypes.Structure):
 
 EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp", "dmg_residual",
            "dmg_destroy", "dmg_strerror", "dmg_last_error", "dmg_levels", "dmg_level_shape",
-           "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static")
+           "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
+           "dmg_batch_info")
 
 _lib = None
 
@@ -82,6 +85,7 @@ def lib():
             "dmg_profile_begin": (i, [vp, i, i, i, i]),
             "dmg_profile_end": (i, [vp, P(ctypes.c_longlong), P(d)]),
             "dmg_residual_static": (i, [P(dmg_params), vp, vp, vp, vp, P(d), vp]),
+            "dmg_batch_info": (i, [vp, P(i), P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -144,7 +148,7 @@ def dmg_default_params(**kw) -> dmg_params:
 
 def dmg_setup(params: dmg_params, D, mu, stream=None):
     """Returns (status, ctx). ctx is an opaque c_void_p (None on failure)."""
-    n = params.nx * params.ny * params.nz
+    n = params.nx * params.ny * params.nz * max(params.batch, 1)
     out = ctypes.c_void_p()
     st = lib().dmg_setup(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _stream(stream), ctypes.byref(out))
     return st, (out if st == DMG_OK else None)
@@ -165,10 +169,19 @@ def dmg_vjp(ctx, u, w, cycles, qbar, Dbar, mubar, info=None, stream=None, n=None
                          _ptr(mubar, n), ctypes.byref(info) if info is not None else None, _stream(stream))
 
 
-def dmg_residual(ctx, q, u, stream=None, n=None):
-    out = (ctypes.c_double * 2)()
+def dmg_residual(ctx, q, u, stream=None, n=None, batch=1):
+    """(status, (||q_0 - A u_0||, ||q_0||, ||q_1 - A u_1||, ...)): 2 * batch norms."""
+    out = (ctypes.c_double * (2 * batch))()
     st = lib().dmg_residual(ctx, _ptr(q, n), _ptr(u, n), out, _stream(stream))
-    return st, (out[0], out[1])
+    return st, tuple(out)
+
+
+def dmg_batch_info(ctx, batch):
+    """(status, cycles, rel): per-sample report of the last solve/jvp/vjp."""
+    cyc = (ctypes.c_int * batch)()
+    rel = (ctypes.c_double * batch)()
+    st = lib().dmg_batch_info(ctx, cyc, rel)
+    return st, list(cyc), list(rel)
 
 
 def dmg_residual_static(params: dmg_params, D, mu, q, u, stream=None):
@@ -218,7 +231,8 @@ def dmg_profile_end(ctx):
 
 
 class Solver:
-    """Owns one dmg context for fixed (D, mu) on a grid of shape (nz, ny, nx).
+    """Owns one dmg context for fixed (D, mu) on a grid of shape (nz, ny, nx),
+    or a batch of B problems of shape (B, nz, ny, nx).
 
     Array arguments are float64 torch tensors (device or host) or numpy arrays;
     results are new torch tensors on ``device`` (default cuda). ``strict``:
@@ -229,9 +243,14 @@ class Solver:
         import torch
         self.torch = torch
         shape = tuple(shape if shape is not None else D.shape)
-        nz, ny, nx = shape
-        self.shape, self.n = shape, nx * ny * nz
-        self.params = dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), **params)
+        if len(shape) == 4:
+            self.batch, (nz, ny, nx) = shape[0], shape[1:]
+        elif len(shape) == 3:
+            self.batch, (nz, ny, nx) = 1, shape
+        else:
+            raise ValueError("expected a shape (nz, ny, nx) or (B, nz, ny, nx), got %r" % (shape,))
+        self.shape, self.n = shape, nx * ny * nz * self.batch
+        self.params = dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.batch, **params)
         self.strict = strict
         self.last_info = dmg_info()
         st, self.ctx = dmg_setup(self.params, D, mu, stream)
@@ -289,6 +308,15 @@ class Solver:
         return qb, Db, mb
 
     def residual(self, q, u, stream=None):
-        st, r = dmg_residual(self.ctx, q, u, stream, n=self.n)
+        """(||q - A u||, ||q||), or a list of such pairs for a batch."""
+        st, r = dmg_residual(self.ctx, q, u, stream, n=self.n, batch=self.batch)
         self._check(st)
-        return r
+        if len(self.shape) == 3:
+            return r
+        return [(r[2 * b], r[2 * b + 1]) for b in range(self.batch)]
+
+    def batch_info(self):
+        """Per-sample (cycles, rel_residual) lists of the last solve/jvp/vjp."""
+        st, cyc, rel = dmg_batch_info(self.ctx, self.batch)
+        self._check(st)
+        return cyc, rel

@@ -22,9 +22,15 @@ distributions of the workloads that are benchmarked:
   interior vertices and 0 elsewhere; the tangent is dq ~ N(0,1),
   dD = 0.1 D xi1, dmu = 0.1 mu xi2 with xi ~ N(0,1).
 
+* ``vi_batch``: the Monte Carlo samples of one variational-inference step
+  (Sec. 2.5: every sample evaluates the forward model and its gradient): B
+  ``tissue`` problems on one grid, sample b drawn from the seed (seed, b), so
+  each sample has its own GRFs for log mus' and log mua, its own source and
+  cotangent.
+
 Random streams come from ``numpy.random.SeedSequence(seed).spawn`` with one
 child per role, each driving a PCG64 generator, so every role is reproducible
-on its own.
+on its own. A seed may be an int or a tuple of ints.
 """
 from __future__ import annotations
 
@@ -103,6 +109,20 @@ def tissue(n: int = 129, seed: int = 0, shape=None, h: float = 0.5) -> dict:
     dmu = 0.1 * mu * r["dmu"].standard_normal(shape)
     return dict(name="tissue", shape=shape, h=h, D=np.ascontiguousarray(D), mu=np.ascontiguousarray(mu),
                 q=np.ascontiguousarray(q), w=w, dq=dq, dD=dD, dmu=dmu)
+
+
+def vi_batch(n: int = 129, batch: int = 64, seed: int = 0, shape=None, h: float = 0.5,
+             keys=("D", "mu", "q", "w")) -> dict:
+    """B tissue samples stacked along a leading axis: arrays of shape (B, nz, ny, nx)."""
+    out = {k: [] for k in keys}
+    w = None
+    for b in range(batch):
+        w = tissue(n, seed=(seed, b), shape=shape, h=h)
+        for k in keys:
+            out[k].append(w[k])
+    res = {k: np.stack(v) for k, v in out.items()}
+    res.update(name="vi_batch", shape=(batch,) + tuple(w["shape"]), h=h)
+    return res
 
 
 def constant(shape, h: float, D: float = 1.0, mu: float = 0.1) -> dict:
