@@ -11,7 +11,10 @@ both converged to relative residual 1e-10. The coefficient hierarchy
 while sources vary, as in the paper's inference use. Every field is 136 MB in
 FP64, larger than the 126 MB L2, so no L2 flush is needed between steps.
 
-The line also carries ``vi_batch``: the batched variational-inference step,
+The line also carries ``serving``: a stream of 2000 Poisson-arrival forward,
+JVP and VJP requests at 200/s on five grid shapes, served with continuous
+batching under an 80 GB budget (p50/p99 latency, solves/s), next to the same
+requests run one at a time in FP64. And ``vi_batch``: the batched variational-inference step,
 64 tissue samples of 129^3 (each with its own coefficients, source and
 cotangent) solved forward and pulled back together in one context (one launch
 per kernel and level for all samples), in samples/s, next to the same samples
@@ -298,6 +301,46 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
     return out
 
 
+SERVE_SHAPES = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
+
+
+def run_serving(dmg, torch, args, world, rank, local):
+    """The request stream: Poisson arrivals of forward, JVP and VJP requests
+    (1:1:2) on grids drawn uniformly from SERVE_SHAPES, tissue coefficients with
+    per-request seeds, served with continuous batching under the memory budget
+    (mixed precision, rtol 1e-10); then the same requests one at a time in FP64."""
+    from paper_2608_00760_b300 import serve
+    dev = torch.device("cuda", local)
+    reqs = serve.poisson_stream(args.serve_requests, args.serve_rate, SERVE_SHAPES, seed=1000 + rank)
+    server = serve.Server(SERVE_SHAPES, budget_bytes=args.serve_budget_gb * 1e9, device=dev,
+                          params=dict(precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=args.inner))
+    try:
+        warm = serve.poisson_stream(3 * len(SERVE_SHAPES), 1e4, SERVE_SHAPES, seed=99)
+        server.run(warm, realtime=False, keep_outputs=False)      # graph capture, outside the measurement
+        barrier(world)
+        served, st = server.run(reqs, keep_outputs=False)
+        slots = {"x".join(map(str, s[::-1])): p.slots for s, p in server.pools.items()}
+        pool_gb = server.pool_bytes / 1e9
+    finally:
+        server.close()
+    secs = max_over_ranks(world, st["seconds"])
+    t_alone = serve.run_one_at_a_time(reqs, params=dict(precision=dmg.DMG_FP64, rtol=RTOL), device=dev)
+    t_alone = max_over_ranks(world, t_alone)
+    nsolves = sum(r.solves for r in reqs)
+    cyc = [c for r in served for c in r.cycles]
+    return dict(workload="%d Poisson arrivals at %g/s; shapes %s (x*y*z) uniform; fwd:JVP:VJP = 1:1:2; tissue "
+                         "coefficients with per-request seeds; %g GB budget; mixed precision, rtol 1e-10"
+                         % (len(reqs), args.serve_rate, ", ".join("x".join(map(str, s[::-1])) for s in SERVE_SHAPES),
+                            args.serve_budget_gb),
+                value=world * nsolves / secs if st["ok"] == len(reqs) else None, unit="solves/s",
+                requests_per_s=world * st["ok"] / secs, ok=st["ok"], requests=len(reqs),
+                p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], seconds=secs,
+                slots=slots, pools_gb=pool_gb, cycles_mean=float(np.mean(cyc)) if cyc else None,
+                one_at_a_time_fp64=dict(value=world * nsolves / t_alone, unit="solves/s",
+                                        requests_per_s=world * len(reqs) / t_alone, seconds=t_alone,
+                                        api="dmg_setup + dmg_solve/dmg_jvp/dmg_vjp per request, batch 1"))
+
+
 def cpu_baseline_sample(w, m_fwd, m_adj):
     """Times the FP64 CPU oracle (single-threaded C) on a bounded sample of the
     workload -- one forward V-cycle, one transposed V-cycle, the residual norm
@@ -392,6 +435,9 @@ def main():
     ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step (mixed)")
     ap.add_argument("--vi-batch", type=int, default=64, help="samples of the batched VI step (0: skip it)")
     ap.add_argument("--vi-size", type=int, default=129)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream (0: skip it)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args, int(os.environ.get("RANK", "0")))
@@ -494,6 +540,7 @@ def main():
     else:
         out["cpu_baseline"] = None
     out["vi_batch"] = run_vi(dmg, torch, args, world, local, peaks, peak_src) if args.vi_batch > 0 else None
+    out["serving"] = (run_serving(dmg, torch, args, world, rank, local) if args.serve_requests > 0 else None)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -44,6 +44,8 @@
 #ifndef DMG_H
 #define DMG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -195,6 +197,67 @@ dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *
  * entries each; either may be NULL. Before any such call every entry is 0.
  */
 dmg_status dmg_batch_info(const dmg_ctx *ctx, int *cycles, double *rel);
+
+/*
+ * Slot-level interface (serving). A context set up with batch = S is also a
+ * pool of S slots for requests that arrive at different times: each slot holds
+ * one request's coefficient hierarchy (kept resident while the request needs
+ * it) and runs one phase at a time; every dmg_step_launch advances all running
+ * slots together by one refinement step (mixed) or one V-cycle (FP64), one
+ * launch per kernel and level for all of them, so requests admitted while
+ * others run share the device (continuous batching). A slot's arithmetic is
+ * that of its sample alone: its results are bit for bit those of
+ * dmg_solve / dmg_jvp / dmg_vjp on a context of batch 1 with the same
+ * parameters. Needs fixed_cycles == 0. While any slot is running a phase, the
+ * whole-context calls (dmg_solve, dmg_jvp, dmg_vjp) return DMG_EINVAL.
+ *
+ * Phases:
+ *   DMG_PHASE_FORWARD  u = S(q); a = q.
+ *   DMG_PHASE_TANGENT  du = S(dq - (dA) u), u the slot's last forward solution;
+ *                      a = dq, b = dD, c = dmu, each may be NULL (zero); b or c
+ *                      needs a forward solution in the slot.
+ *   DMG_PHASE_ADJOINT  lambda = S^dagger w (the converged adjoint, as dmg_vjp
+ *                      with cycles = 0); a = w.
+ * Arrays are one sample, [nz][ny][nx], device or host memory, read by the
+ * calls' stream work (device arrays must stay valid until the next
+ * dmg_step_finish has returned).
+ */
+enum { DMG_PHASE_FORWARD = 0, DMG_PHASE_TANGENT = 1, DMG_PHASE_ADJOINT = 2 };
+
+/* dmg_slot_load -- rebuild the coefficient hierarchy of one slot from D, mu
+   (asynchronous; a matrix that is not positive definite makes the slot's next
+   phase end with DMG_EINVAL). The slot must not be running a phase. */
+dmg_status dmg_slot_load(dmg_ctx *ctx, int slot, const double *D, const double *mu, void *stream);
+
+/* dmg_slot_begin -- stage a phase into an idle slot (asynchronous); it starts
+   iterating with the step after the next dmg_step_launch. */
+dmg_status dmg_slot_begin(dmg_ctx *ctx, int slot, int phase, const double *a, const double *b,
+                          const double *c, void *stream);
+
+/* dmg_step_launch -- enqueue one step of every running slot and the read-back
+   of their residual norms (asynchronous). Must be followed by dmg_step_finish. */
+dmg_status dmg_step_launch(dmg_ctx *ctx, void *stream);
+
+/* dmg_step_finish -- wait for the step, test every slot's relative residual
+   against rtol (and max_cycles), and list in ended[0 .. *nended) the slots
+   whose phase ended (ended may be NULL; it needs room for batch entries). A
+   phase ends converged (DMG_OK), with DMG_ENOCONV, DMG_ENAN, or DMG_EINVAL for
+   a slot whose load failed; dmg_slot_result gives the status. */
+dmg_status dmg_step_finish(dmg_ctx *ctx, void *stream, int *ended, int *nended);
+
+/* dmg_slot_result -- status (-1 while running), cycles and final relative
+   residual of the slot's last phase; any output may be NULL. */
+dmg_status dmg_slot_result(const dmg_ctx *ctx, int slot, int *status, int *cycles, double *rel);
+
+/* dmg_slot_read -- copy results of an idle slot out (asynchronous on stream):
+   u the slot's forward solution; x the last phase's solution (u, du or
+   lambda = qbar); Dbar and mubar (after an adjoint phase) the coefficient
+   gradients of <w, u> as in dmg_vjp. Any output may be NULL. */
+dmg_status dmg_slot_read(dmg_ctx *ctx, int slot, double *u, double *x, double *Dbar, double *mubar,
+                         void *stream);
+
+/* Device memory held by the context, in bytes (for admission by memory budget). */
+size_t dmg_device_bytes(const dmg_ctx *ctx);
 
 /*
  * dmg_residual_static -- out[0] = ||q - A u||_2 and out[1] = ||q||_2 over

@@ -61,6 +61,22 @@ struct Graph {
     std::vector<int> prof;
 };
 
+// Host-side state of one slot of the slot-level (serving) interface.
+enum SlotRun { kIdle = 0, kStarting = 1, kRunning = 2, kDone = 3 };
+struct Slot {
+    int phase = -1;          // DMG_PHASE_* of the current or last phase
+    int run = kIdle;
+    int status = DMG_OK;     // result of the last phase
+    int steps = 0;           // refinement steps (mixed) or cycles (FP64) of the phase
+    double nf = 0.0, rel = 0.0;
+    bool start_seen = false; // its start was enqueued before the last step launch
+    bool in_step = false;    // it iterated in the last step launch
+    bool load_pending = false;
+    bool load_failed = false;
+    bool loaded = false;
+    bool have_fwd = false;   // U0 holds the slot's forward solution
+};
+
 }  // namespace
 
 struct dmg_ctx {
@@ -71,7 +87,10 @@ struct dmg_ctx {
     int nc = 0;                       // coarsest interior unknowns
     int tail_first[2] = {0, 0};       // first level of the single-CTA tail: [0] FP64, [1] FP32 (nlev: none)
     size_t tail_smem[2] = {0, 0};     // its dynamic shared memory in bytes
-    double *Ainv = nullptr;           // coarsest inverse (FP64)
+    double *Ainv = nullptr;           // coarsest inverse (FP64), nc x nc per sample
+    double *M = nullptr;              // Gauss-Jordan work matrix [A | I], nc x 2nc per sample
+    int *gj_status = nullptr;         // Gauss-Jordan status per sample (device)
+    int *hstatus = nullptr;           // pinned host copy
     float *Ainv32 = nullptr;
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
     double *U0 = nullptr;             // level-0 staging: user's u
@@ -84,10 +103,18 @@ struct dmg_ctx {
     const int *mask = nullptr;        // mask argument of the launches being issued: act, or NULL
                                       // while every sample iterates (no per-block mask load)
     int *hact = nullptr;              // pinned host copy of act
+    // slot-level interface: per-slot state, the adjoint-phase mask, and one
+    // step graph per direction ([0] forward and tangent phases, masked by act;
+    // [1] adjoint phases, masked by act_a)
+    std::vector<Slot> slots;
+    int *act_a = nullptr, *hact_a = nullptr;
+    Graph g_srv[2];
+    bool step_open = false;
     std::vector<int> bcyc;            // per sample: cycles of the last call
     std::vector<double> brel;         // per sample: final relative residual of the last call
     dmgk::MixScalars *ms = nullptr;   // device scalars of the mixed-precision loop
     std::vector<void *> dev_allocs;
+    size_t dev_bytes = 0;             // device memory held by the context
     unsigned long long launches = 0;
     char err[512] = {0};
     // CUDA graphs of the repeated steps, captured on first use on cap_stream:
@@ -161,6 +188,7 @@ dmg_status dalloc(dmg_ctx *c, T **p, size_t n) {
                     cudaGetErrorString(e));
     }
     c->dev_allocs.push_back(q);
+    c->dev_bytes += n * sizeof(T);
     *p = static_cast<T *>(q);
     return DMG_OK;
 }
@@ -210,6 +238,11 @@ void graphs_reset(dmg_ctx *c) {
             for (int idx : set[t].prof) c->prof_free.push_back(idx);
             set[t] = Graph();
         }
+    for (Graph &G : c->g_srv) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        for (int idx : G.prof) c->prof_free.push_back(idx);
+        G = Graph();
+    }
 }
 
 // --- staging between the caller's contiguous arrays and the split layout -------
@@ -229,28 +262,41 @@ inline dim3 vertex_grid(const Geom &g) {
     return dim3((unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256), g.nb);
 }
 
-dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s) {
-    const Geom &g = c->L[0].g;
-    size_t bytes = (size_t)g.nx * g.ny * g.nz * g.nb * sizeof(double);
+// level-0 geometry of one slot (a single sample; slot < 0: every sample)
+inline Geom geom0(const dmg_ctx *c, int slot) {
+    Geom g = c->L[0].g;
+    if (slot >= 0) g.nb = 1;
+    return g;
+}
+
+// src (caller layout, every sample or one slot's sample) -> dst (split layout of
+// the same samples; dst already points at the slot's part)
+dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s, int slot = -1) {
+    const Geom g = geom0(c, slot);
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t bytes = n * g.nb * sizeof(double);
     const double *from = src;
     if (!is_device_ptr(src)) {
-        CUDA_TRY(c, cudaMemcpyAsync(c->stage, src, bytes, cudaMemcpyHostToDevice, s));
-        from = c->stage;
+        double *st = c->stage + (slot < 0 ? 0 : n * slot);
+        CUDA_TRY(c, cudaMemcpyAsync(st, src, bytes, cudaMemcpyHostToDevice, s));
+        from = st;
     }
     dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
     return check_launch(c, "gather");
 }
 
-dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s) {
-    const Geom &g = c->L[0].g;
-    size_t bytes = (size_t)g.nx * g.ny * g.nz * g.nb * sizeof(double);
+dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s, int slot = -1) {
+    const Geom g = geom0(c, slot);
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t bytes = n * g.nb * sizeof(double);
     if (is_device_ptr(dst)) {
         dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
         return check_launch(c, "scatter");
     }
-    dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, c->stage);
+    double *st = c->stage + (slot < 0 ? 0 : n * slot);
+    dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, st);
     TRY(check_launch(c, "scatter"));
-    CUDA_TRY(c, cudaMemcpyAsync(dst, c->stage, bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyDeviceToHost, s));
     return DMG_OK;
 }
 
@@ -763,6 +809,66 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     return DMG_OK;
 }
 
+// Level l of one slot (a single sample, pointers at its part; slot < 0: the
+// level itself with every sample).
+Level level_view(const dmg_ctx *c, int l, int slot) {
+    Level v = c->L[l];
+    if (slot < 0) return v;
+    const long long o = (long long)slot * v.g.sb;
+    v.g.nb = 1;
+    v.n = (size_t)v.g.sb;
+    for (double **q : {&v.u, &v.f, &v.r, &v.cx, &v.cy, &v.cz, &v.diag, &v.invd, &v.D, &v.mu})
+        if (*q) *q += o;
+    for (float **q : {&v.u32, &v.f32, &v.r32, &v.Dh32, &v.mu32})
+        if (*q) *q += o;
+    return v;
+}
+
+// The coefficient hierarchy of every sample (slot < 0) or of one slot
+// (Sec. 2.2: D and mu coarsened level by level, the operator rediscretised on
+// every level, the coarsest one inverted). Asynchronous; the Gauss-Jordan
+// status of each built sample lands in hstatus once the stream reaches it.
+dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const double *mu, cudaStream_t s) {
+    const dmg_params *p = &c->p;
+    const bool mixed = p->precision == DMG_MIXED;
+    Level V[kMaxLevels];
+    for (int l = 0; l < c->nlev; l++) V[l] = level_view(c, l, slot);
+    TRY(stage_in(c, D, V[0].D, false, s, slot));
+    TRY(stage_in(c, mu, V[0].mu, false, s, slot));
+    for (int l = 1; l < c->nlev; l++) {
+        Level &F = V[l - 1], &C = V[l];
+        dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
+        TRY(check_launch(c, "coarsen"));
+        dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.mu, C.g, C.mu, p->coarsen);
+        TRY(check_launch(c, "coarsen"));
+    }
+    const int harm = p->face_mean == DMG_FACE_HARMONIC;
+    for (int l = 0; l < c->nlev; l++) {
+        Level &L = V[l];
+        const double ih2 = 1.0 / (L.h * L.h);
+        dmgk::k_build_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.cz,
+                                                            L.diag, L.invd);
+        TRY(check_launch(c, "build_faces"));
+        if (mixed) {
+            const double scale = harm ? ih2 : 0.5 * ih2;
+            dmgk::k_build_vertex32<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, scale, L.Dh32, L.mu32);
+            TRY(check_launch(c, "build_vertex32"));
+        }
+    }
+    const Level &LC = V[c->nlev - 1];
+    const size_t nc2 = (size_t)c->nc * c->nc;
+    const int first = slot < 0 ? 0 : slot, count = slot < 0 ? c->nb : 1;
+    CUDA_TRY(c, cudaMemsetAsync(c->gj_status + first, 0xff, count * sizeof(int), s));
+    dmgk::k_coarse_assemble<<<dim3(64, count), 256, 0, s>>>(LC.g, coef64(LC), c->nc, c->M + 2 * nc2 * first);
+    TRY(check_launch(c, "coarse_assemble"));
+    dmgk::k_gauss_jordan<<<count, 1024, 0, s>>>(c->M + 2 * nc2 * first, c->nc, c->Ainv + nc2 * first,
+                                                c->Ainv32 + nc2 * first, c->gj_status + first);
+    TRY(check_launch(c, "gauss_jordan"));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hstatus + first, c->gj_status + first, count * sizeof(int),
+                                cudaMemcpyDeviceToHost, s));
+    return DMG_OK;
+}
+
 dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const double *mu, cudaStream_t s) {
     TRY(validate(c, p));
     if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
@@ -816,31 +922,17 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         for (int b = 0; b < nb; b++) c->hact[b] = 1;
     }
     TRY(push_act(c, s));
+    TRY(dalloc(c, &c->act_a, nb));
+    CUDA_TRY(c, cudaMemsetAsync(c->act_a, 0, nb * sizeof(int), s));
+    {
+        cudaError_t e = cudaMallocHost(&c->hact_a, nb * sizeof(int));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+        memset(c->hact_a, 0, nb * sizeof(int));
+    }
+    c->slots.assign(nb, Slot());
+    for (Slot &sl : c->slots) sl.loaded = true;   // setup builds every sample's hierarchy
     c->bcyc.assign(nb, 0);
     c->brel.assign(nb, 0.0);
-    // level-0 coefficients from the caller, then coarsen level by level
-    TRY(stage_in(c, D, L0.D, false, s));
-    TRY(stage_in(c, mu, L0.mu, false, s));
-    for (int l = 1; l < c->nlev; l++) {
-        Level &F = c->L[l - 1], &C = c->L[l];
-        dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
-        TRY(check_launch(c, "coarsen"));
-        dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.mu, C.g, C.mu, p->coarsen);
-        TRY(check_launch(c, "coarsen"));
-    }
-    int harm = p->face_mean == DMG_FACE_HARMONIC;
-    for (int l = 0; l < c->nlev; l++) {
-        Level &L = c->L[l];
-        double ih2 = 1.0 / (L.h * L.h);
-        dmgk::k_build_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.cz,
-                                                            L.diag, L.invd);
-        TRY(check_launch(c, "build_faces"));
-        if (mixed) {
-            double scale = harm ? ih2 : 0.5 * ih2;
-            dmgk::k_build_vertex32<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, scale, L.Dh32, L.mu32);
-            TRY(check_launch(c, "build_vertex32"));
-        }
-    }
     Level &LC0 = c->L[c->nlev - 1];
     c->nc = (LC0.g.nx - 2) * (LC0.g.ny - 2) * (LC0.g.nz - 2);   // coarsest unknowns (the tail sizes its buffer by it)
     // single-CTA tail: the small levels, as many as fit the shared-memory budget
@@ -878,30 +970,254 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         }
     }
     // exact coarsest solve: dense SPD inverse of every sample by in-block Gauss-Jordan
-    Level &LC = c->L[c->nlev - 1];
-    c->nc = (LC.g.nx - 2) * (LC.g.ny - 2) * (LC.g.nz - 2);
     const size_t nc2 = (size_t)c->nc * c->nc;
-    double *M = nullptr;
-    int *status = nullptr;
-    TRY(dalloc(c, &M, 2 * nc2 * nb));
+    TRY(dalloc(c, &c->M, 2 * nc2 * nb));
     TRY(dalloc(c, &c->Ainv, nc2 * nb));
     TRY(dalloc(c, &c->Ainv32, nc2 * nb));
-    TRY(dalloc(c, &status, nb));
-    CUDA_TRY(c, cudaMemsetAsync(status, 0xff, nb * sizeof(int), s));
-    dmgk::k_coarse_assemble<<<dim3(64, nb), 256, 0, s>>>(LC.g, coef64(LC), c->nc, M);
-    TRY(check_launch(c, "coarse_assemble"));
-    dmgk::k_gauss_jordan<<<nb, 1024, 0, s>>>(M, c->nc, c->Ainv, c->Ainv32, status);
-    TRY(check_launch(c, "gauss_jordan"));
-    std::vector<int> hstatus(nb, -1);
-    CUDA_TRY(c, cudaMemcpyAsync(hstatus.data(), status, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(dalloc(c, &c->gj_status, nb));
+    {
+        cudaError_t e = cudaMallocHost(&c->hstatus, nb * sizeof(int));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+    }
+    TRY(build_coefficients(c, -1, D, mu, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     for (int b = 0; b < nb; b++)
-        if (hstatus[b] != 0) {
+        if (c->hstatus[b] != 0) {
             if (nb == 1)
                 return fail(c, DMG_EINVAL, "coarsest-level matrix is not positive definite (need D > 0, mu >= 0)");
             return fail(c, DMG_EINVAL,
                         "coarsest-level matrix of sample %d is not positive definite (need D > 0, mu >= 0)", b);
         }
+    return DMG_OK;
+}
+
+// --- slot-level (serving) interface ---------------------------------------------
+// A batched context doubles as a pool of slots. Each slot holds one request's
+// coefficient hierarchy and runs one phase at a time (forward solve, tangent
+// solve, adjoint solve); every step launch advances all running slots by one
+// refinement step (mixed) or V-cycle (FP64), the forward-type phases in one
+// graph and the adjoint phases in another, each masked to its slots. A slot's
+// arithmetic is that of its sample alone, so a served result is bit for bit
+// the result of dmg_solve/dmg_jvp/dmg_vjp on a context of batch 1.
+
+bool slot_busy(const Slot &sl) { return sl.run == kStarting || sl.run == kRunning; }
+
+bool any_busy(const dmg_ctx *c) {
+    for (const Slot &sl : c->slots)
+        if (slot_busy(sl)) return true;
+    return false;
+}
+
+dmg_status check_slot(dmg_ctx *c, int slot) {
+    if (slot < 0 || slot >= c->nb) return fail(c, DMG_EINVAL, "slot %d out of range [0, %d)", slot, c->nb);
+    if (c->p.fixed_cycles != 0) return fail(c, DMG_EINVAL, "the slot interface needs fixed_cycles == 0");
+    return DMG_OK;
+}
+
+dmg_status slot_load_impl(dmg_ctx *c, int slot, const double *D, const double *mu, cudaStream_t s) {
+    TRY(check_slot(c, slot));
+    if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
+    Slot &sl = c->slots[slot];
+    if (slot_busy(sl)) return fail(c, DMG_EINVAL, "slot %d is running a phase", slot);
+    TRY(build_coefficients(c, slot, D, mu, s));
+    sl = Slot();
+    sl.load_pending = true;
+    return DMG_OK;
+}
+
+dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, const double *b, const double *d,
+                           cudaStream_t s) {
+    TRY(check_slot(c, slot));
+    Slot &sl = c->slots[slot];
+    if (slot_busy(sl)) return fail(c, DMG_EINVAL, "slot %d is running a phase", slot);
+    if (!sl.loaded && !sl.load_pending) return fail(c, DMG_EINVAL, "slot %d has no coefficients", slot);
+    if (phase != DMG_PHASE_FORWARD && phase != DMG_PHASE_TANGENT && phase != DMG_PHASE_ADJOINT)
+        return fail(c, DMG_EINVAL, "bad phase %d", phase);
+    if ((phase == DMG_PHASE_FORWARD || phase == DMG_PHASE_ADJOINT) && !a)
+        return fail(c, DMG_EINVAL, "the right-hand side must not be NULL");
+    if (phase == DMG_PHASE_TANGENT && (b || d) && !sl.have_fwd)
+        return fail(c, DMG_EINVAL, "slot %d has no forward solution for a D or mu tangent", slot);
+    Level l = level_view(c, 0, slot);
+    const long long o = (long long)slot * l.g.sb;
+    CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
+    if (a) {
+        TRY(stage_in(c, a, l.f, false, s, slot));
+    } else {
+        CUDA_TRY(c, cudaMemsetAsync(l.f, 0, l.n * sizeof(double), s));
+    }
+    if (phase == DMG_PHASE_TANGENT && (b || d)) {
+        if (b) TRY(stage_in(c, b, c->T1 + o, false, s, slot));
+        if (d) TRY(stage_in(c, d, c->T2 + o, false, s, slot));
+        const double ih2 = 1.0 / (l.h * l.h);
+        dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0 + o, b ? c->T1 + o : nullptr, d ? c->T2 + o : nullptr,
+                                                   l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
+        TRY(check_launch(c, "dA"));
+    }
+    // ||f||^2 -> red[slot][0]; mixed: the slot's scale and FP32 right-hand side
+    dmgk::k_norm2<<<dim3(kNormBlocks, 1), 256, 0, s>>>(l.g, l.f, c->partial + (size_t)kNormBlocks * slot);
+    TRY(check_launch(c, "norm2"));
+    dmgk::k_reduce_final<<<1, 256, 0, s>>>(c->partial + (size_t)kNormBlocks * slot, kNormBlocks,
+                                           c->red + (size_t)kSlots * slot, 0, nullptr);
+    TRY(check_launch(c, "reduce"));
+    if (c->p.precision == DMG_MIXED) {
+        dmgk::k_mix_init<<<1, 32, 0, s>>>(c->red + (size_t)kSlots * slot, 0, c->ms + slot, 1);
+        TRY(check_launch(c, "mix_init"));
+        dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms + slot, l.f32);
+        TRY(check_launch(c, "to_f32"));
+    }
+    const bool keep_fwd = sl.have_fwd && phase != DMG_PHASE_FORWARD;
+    const bool loaded = sl.loaded, pending = sl.load_pending, failed = sl.load_failed;
+    sl = Slot();
+    sl.loaded = loaded;
+    sl.load_pending = pending;
+    sl.load_failed = failed;
+    sl.have_fwd = keep_fwd;
+    sl.phase = phase;
+    sl.run = kStarting;
+    return DMG_OK;
+}
+
+// the step graph of one direction: t = 0 forward and tangent phases, 1 adjoint
+dmg_status capture_step(dmg_ctx *c, int t) {
+    Level &l = c->L[0];
+    const bool transposed = t == 1;
+    c->mask = t ? c->act_a : c->act;
+    return capture(c, c->g_srv[t], [&](cudaStream_t cs) -> dmg_status {
+        if (c->p.precision == DMG_MIXED) {
+            dmgk::k_zero_interior<float><<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u32, c->mask);
+            TRY(check_launch(c, "zero"));
+            for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
+            dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+            TRY(check_launch(c, "update"));
+            TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
+            dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);
+            return check_launch(c, "mix_next");
+        }
+        TRY(vcycle<double>(c, 0, transposed, cs));
+        return resid_norm_async(c, l.u, l.f, nullptr, 0, c->mask, cs);
+    });
+}
+
+dmg_status step_launch_impl(dmg_ctx *c, cudaStream_t s) {
+    if (c->step_open) return fail(c, DMG_EINVAL, "dmg_step_finish must follow every dmg_step_launch");
+    bool run[2] = {false, false};
+    for (int b = 0; b < c->nb; b++) {
+        Slot &sl = c->slots[b];
+        sl.in_step = sl.run == kRunning;
+        sl.start_seen = sl.run == kStarting;
+        const int t = sl.phase == DMG_PHASE_ADJOINT ? 1 : 0;
+        c->hact[b] = sl.in_step && t == 0;
+        c->hact_a[b] = sl.in_step && t == 1;
+        if (sl.in_step) run[t] = true;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->act, c->hact, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->act_a, c->hact_a, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int t = 0; t < 2; t++) {
+        if (!run[t]) continue;
+        TRY(capture_step(c, t));
+        TRY(replay(c, c->g_srv[t], s));
+    }
+    TRY(enqueue_readback(c, s));
+    c->step_open = true;
+    return DMG_OK;
+}
+
+void end_phase(dmg_ctx *c, int b, int status, std::vector<int> &ended) {
+    Slot &sl = c->slots[b];
+    sl.status = status;
+    sl.run = kDone;
+    ended.push_back(b);
+}
+
+dmg_status step_finish_impl(dmg_ctx *c, cudaStream_t s, int *ended_out, int *nended) {
+    if (!c->step_open) return fail(c, DMG_EINVAL, "dmg_step_finish without dmg_step_launch");
+    c->step_open = false;
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    prof_harvest(c, c->prof_direct, true);
+    for (Graph &G : c->g_srv) prof_harvest(c, G.prof, false);
+    int kerr = 0;
+    memcpy(&kerr, c->hred + 3, sizeof(int));
+    if (kerr != 0) return fail(c, DMG_ETIMEOUT, "a bounded device wait ran out (kernel error flag %d)", kerr);
+    std::vector<int> ended;
+    const int per_step = c->p.precision == DMG_MIXED ? c->p.inner_cycles : 1;
+    for (int b = 0; b < c->nb; b++) {
+        Slot &sl = c->slots[b];
+        if (sl.load_pending) {   // every load enqueued so far has completed
+            sl.load_pending = false;
+            sl.load_failed = c->hstatus[b] != 0;
+            sl.loaded = !sl.load_failed;
+        }
+        if (slot_busy(sl) && sl.load_failed) {
+            end_phase(c, b, DMG_EINVAL, ended);
+            continue;
+        }
+        if (sl.run == kStarting && sl.start_seen) {
+            const double n2 = hred(c, b, 0);
+            sl.start_seen = false;
+            if (!std::isfinite(n2)) {
+                end_phase(c, b, DMG_ENAN, ended);
+            } else if (n2 == 0.0) {
+                sl.rel = 0.0;
+                end_phase(c, b, DMG_OK, ended);
+            } else {
+                sl.nf = std::sqrt(n2);
+                sl.rel = 1.0;
+                sl.run = kRunning;
+            }
+        } else if (sl.run == kRunning && sl.in_step) {
+            const double rn2 = hred(c, b, 0);
+            sl.steps++;
+            if (!std::isfinite(rn2)) {
+                end_phase(c, b, DMG_ENAN, ended);
+                continue;
+            }
+            sl.rel = std::sqrt(rn2) / sl.nf;
+            if (sl.rel <= c->p.rtol || rn2 == 0.0) end_phase(c, b, DMG_OK, ended);
+            else if (sl.steps >= c->p.max_cycles) end_phase(c, b, DMG_ENOCONV, ended);
+        }
+        sl.in_step = false;
+    }
+    // a finished forward phase leaves its solution in U0 for the tangent or adjoint phase
+    for (int b : ended) {
+        Slot &sl = c->slots[b];
+        if (sl.phase == DMG_PHASE_FORWARD && (sl.status == DMG_OK || sl.status == DMG_ENOCONV)) {
+            const Level l = level_view(c, 0, b);
+            CUDA_TRY(c, cudaMemcpyAsync(c->U0 + (long long)b * l.g.sb, l.u, l.n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+            sl.have_fwd = true;
+        }
+        c->bcyc[b] = sl.steps * per_step;
+        c->brel[b] = sl.rel;
+    }
+    if (nended) *nended = (int)ended.size();
+    if (ended_out)
+        for (size_t q = 0; q < ended.size(); q++) ended_out[q] = ended[q];
+    return DMG_OK;
+}
+
+dmg_status slot_read_impl(dmg_ctx *c, int slot, double *u, double *x, double *Dbar, double *mubar,
+                          cudaStream_t s) {
+    TRY(check_slot(c, slot));
+    Slot &sl = c->slots[slot];
+    if (slot_busy(sl)) return fail(c, DMG_EINVAL, "slot %d is running a phase", slot);
+    if (sl.phase < 0) return fail(c, DMG_EINVAL, "slot %d has run no phase", slot);
+    if ((u || Dbar || mubar) && !sl.have_fwd) return fail(c, DMG_EINVAL, "slot %d has no forward solution", slot);
+    if ((Dbar || mubar) && sl.phase != DMG_PHASE_ADJOINT)
+        return fail(c, DMG_EINVAL, "Dbar and mubar need a finished adjoint phase");
+    const Level l = level_view(c, 0, slot);
+    const long long o = (long long)slot * l.g.sb;
+    if (u) TRY(stage_out(c, c->U0 + o, u, s, slot));
+    if (x) TRY(stage_out(c, l.u, x, s, slot));
+    if (Dbar || mubar) {
+        const double ih2 = 1.0 / (l.h * l.h);
+        ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+        dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0 + o, l.u, l.D, ih2,
+                                                     c->p.face_mean == DMG_FACE_HARMONIC,
+                                                     Dbar ? c->T1 + o : nullptr, mubar ? c->T2 + o : nullptr);
+        TRY(check_launch(c, "grad"));
+        if (Dbar) TRY(stage_out(c, c->T1 + o, Dbar, s, slot));
+        if (mubar) TRY(stage_out(c, c->T2 + o, mubar, s, slot));
+    }
     return DMG_OK;
 }
 
@@ -957,6 +1273,7 @@ dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, voi
 
 dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
         if (!q || !u) return fail(c, DMG_EINVAL, "q and u must not be NULL");
         info_reset(info);
         cudaStream_t s = S(stream);
@@ -973,6 +1290,7 @@ dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, voi
 dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
                    double *du, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
         if (!du) return fail(c, DMG_EINVAL, "du must not be NULL");
         if ((dD || dmu) && !u) return fail(c, DMG_EINVAL, "u is needed for a D or mu tangent");
         info_reset(info);
@@ -1003,6 +1321,7 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
 dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, double *qbar, double *Dbar,
                    double *mubar, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
         if (!w) return fail(c, DMG_EINVAL, "w must not be NULL");
         if ((Dbar || mubar) && !u) return fail(c, DMG_EINVAL, "u is needed for Dbar / mubar");
         if (cycles < 0) return fail(c, DMG_EINVAL, "cycles must be >= 0");
@@ -1059,6 +1378,8 @@ dmg_status dmg_destroy(dmg_ctx *c) {
     for (void *q : c->dev_allocs) cudaFree(q);
     if (c->hred) cudaFreeHost(c->hred);
     if (c->hact) cudaFreeHost(c->hact);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
+    if (c->hact_a) cudaFreeHost(c->hact_a);
     delete c;
     return DMG_OK;
 }
@@ -1080,6 +1401,38 @@ const char *dmg_last_error(const dmg_ctx *c) {
     if (!c) return g_setup_err;
     return c->err;
 }
+
+dmg_status dmg_slot_load(dmg_ctx *c, int slot, const double *D, const double *mu, void *stream) {
+    return guarded(c, [&]() { return slot_load_impl(c, slot, D, mu, S(stream)); });
+}
+
+dmg_status dmg_slot_begin(dmg_ctx *c, int slot, int phase, const double *a, const double *b, const double *d,
+                          void *stream) {
+    return guarded(c, [&]() { return slot_begin_impl(c, slot, phase, a, b, d, S(stream)); });
+}
+
+dmg_status dmg_step_launch(dmg_ctx *c, void *stream) {
+    return guarded(c, [&]() { return step_launch_impl(c, S(stream)); });
+}
+
+dmg_status dmg_step_finish(dmg_ctx *c, void *stream, int *ended, int *nended) {
+    return guarded(c, [&]() { return step_finish_impl(c, S(stream), ended, nended); });
+}
+
+dmg_status dmg_slot_result(const dmg_ctx *c, int slot, int *status, int *cycles, double *rel) {
+    if (!c || slot < 0 || slot >= c->nb) return DMG_EINVAL;
+    const Slot &sl = c->slots[slot];
+    if (status) *status = slot_busy(sl) ? -1 : (sl.phase < 0 ? DMG_OK : sl.status);
+    if (cycles) *cycles = sl.steps * (c->p.precision == DMG_MIXED ? c->p.inner_cycles : 1);
+    if (rel) *rel = sl.rel;
+    return DMG_OK;
+}
+
+dmg_status dmg_slot_read(dmg_ctx *c, int slot, double *u, double *x, double *Dbar, double *mubar, void *stream) {
+    return guarded(c, [&]() { return slot_read_impl(c, slot, u, x, Dbar, mubar, S(stream)); });
+}
+
+size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes : 0; }
 
 dmg_status dmg_batch_info(const dmg_ctx *c, int *cycles, double *rel) {
     if (!c) return DMG_EINVAL;

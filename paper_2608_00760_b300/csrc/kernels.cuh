@@ -1009,4 +1009,16 @@ __global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict
     y[p] = f64_to_f32_shift(x[p], -ms[smp].e_cur);
 }
 
+// x = 0 on the interior vertices of the active samples
+template <class T>
+__global__ void __launch_bounds__(256) k_zero_interior(Geom g, T *__restrict__ x, const int *act) {
+    int i = vertex_i();
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k;
+    const int smp = zsplit(g, kInterior, k);
+    k += 1;
+    if (i < 1 || i > g.nx - 2 || j > g.ny - 2 || inactive(act, smp)) return;
+    x[g.pos(i, j, k) + smp * g.sb] = T(0);
+}
+
 }  // namespace dmgk

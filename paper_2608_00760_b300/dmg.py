@@ -26,6 +26,7 @@ DMG_FACE_ARITHMETIC, DMG_FACE_HARMONIC = 0, 1
 DMG_COARSEN_FULL_WEIGHTING, DMG_COARSEN_INJECTION = 0, 1
 DMG_KERNEL_SMOOTH, DMG_KERNEL_RESTRICT, DMG_KERNEL_PROLONG, DMG_KERNEL_RESIDUAL, DMG_KERNEL_GRAD = range(5)
 DMG_HIST_LEN = 64
+DMG_PHASE_FORWARD, DMG_PHASE_TANGENT, DMG_PHASE_ADJOINT = range(3)
 
 
 class dmg_params(ctypes.Structure):
@@ -48,7 +49,8 @@ class dmg_info(ctypes.Structure):
 EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp", "dmg_residual",
            "dmg_destroy", "dmg_strerror", "dmg_last_error", "dmg_levels", "dmg_level_shape",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
-           "dmg_batch_info")
+           "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
+           "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes")
 
 _lib = None
 
@@ -86,6 +88,13 @@ def lib():
             "dmg_profile_end": (i, [vp, P(ctypes.c_longlong), P(d)]),
             "dmg_residual_static": (i, [P(dmg_params), vp, vp, vp, vp, P(d), vp]),
             "dmg_batch_info": (i, [vp, P(i), P(d)]),
+            "dmg_slot_load": (i, [vp, i, vp, vp, vp]),
+            "dmg_slot_begin": (i, [vp, i, i, vp, vp, vp, vp]),
+            "dmg_step_launch": (i, [vp, vp]),
+            "dmg_step_finish": (i, [vp, vp, P(i), P(i)]),
+            "dmg_slot_result": (i, [vp, i, P(i), P(i), P(d)]),
+            "dmg_slot_read": (i, [vp, i, vp, vp, vp, vp, vp]),
+            "dmg_device_bytes": (ctypes.c_size_t, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -192,6 +201,42 @@ def dmg_residual_static(params: dmg_params, D, mu, q, u, stream=None):
     st = lib().dmg_residual_static(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _ptr(q, n), _ptr(u, n), out,
                                    _stream(stream))
     return st, (out[0], out[1])
+
+
+def dmg_slot_load(ctx, slot, D, mu, stream=None, n=None):
+    return lib().dmg_slot_load(ctx, int(slot), _ptr(D, n), _ptr(mu, n), _stream(stream))
+
+
+def dmg_slot_begin(ctx, slot, phase, a=None, b=None, c=None, stream=None, n=None):
+    return lib().dmg_slot_begin(ctx, int(slot), int(phase), _ptr(a, n), _ptr(b, n), _ptr(c, n), _stream(stream))
+
+
+def dmg_step_launch(ctx, stream=None):
+    return lib().dmg_step_launch(ctx, _stream(stream))
+
+
+def dmg_step_finish(ctx, batch, stream=None):
+    """(status, [slots whose phase ended])."""
+    ended = (ctypes.c_int * max(batch, 1))()
+    n = ctypes.c_int(0)
+    st = lib().dmg_step_finish(ctx, _stream(stream), ended, ctypes.byref(n))
+    return st, [ended[k] for k in range(n.value)]
+
+
+def dmg_slot_result(ctx, slot):
+    """(status, phase status (-1 while running), cycles, rel)."""
+    a, b, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().dmg_slot_result(ctx, int(slot), ctypes.byref(a), ctypes.byref(b), ctypes.byref(r))
+    return st, a.value, b.value, r.value
+
+
+def dmg_slot_read(ctx, slot, u=None, x=None, Dbar=None, mubar=None, stream=None, n=None):
+    return lib().dmg_slot_read(ctx, int(slot), _ptr(u, n), _ptr(x, n), _ptr(Dbar, n), _ptr(mubar, n),
+                               _stream(stream))
+
+
+def dmg_device_bytes(ctx):
+    return lib().dmg_device_bytes(ctx)
 
 
 def dmg_destroy(ctx):

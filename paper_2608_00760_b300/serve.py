@@ -1,0 +1,329 @@
+"""Continuous-batching request server over the slot-level C ABI (include/dmg.h).
+
+A variational-inference sampler (arXiv 2608.00760, Sec. 2.5) emits forward,
+JVP and VJP solves of its samples, each sample with its own coefficients. The
+server keeps one pool per grid shape: a batched context whose batch entries are
+slots. A request is admitted into a free slot of its shape's pool once the
+device-memory budget allows it. Its coefficient hierarchy is built into the slot
+(``dmg_slot_load``) and stays resident while it runs its phases:
+- forward solve, for every kind;
+- then a tangent solve (JVP) or an adjoint solve (VJP), both with the forward
+  solution kept in the slot.
+
+Every loop iteration launches one step of every pool with running slots, each on
+the pool's own CUDA stream, so pools overlap on the device. Within a pool, all
+running slots advance together, one launch per kernel and level (CUDA graphs).
+New requests join at any step boundary while older ones are mid-solve (continuous
+batching). A slot's arithmetic is that of its sample alone, so each result is bit
+for bit the result of the same request served alone.
+
+Latency is measured from a request's arrival to the completion of its last
+read-back; the server reports p50/p99 latency beside requests/s and solves/s.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import dmg
+
+PHASES = {"fwd": (dmg.DMG_PHASE_FORWARD,),
+          "jvp": (dmg.DMG_PHASE_FORWARD, dmg.DMG_PHASE_TANGENT),
+          "vjp": (dmg.DMG_PHASE_FORWARD, dmg.DMG_PHASE_ADJOINT)}
+# fields a request of each kind brings, and the fields it gets back
+INPUT_KEYS = {"fwd": ("D", "mu", "q"), "jvp": ("D", "mu", "q", "dq", "dD", "dmu"),
+              "vjp": ("D", "mu", "q", "w")}
+OUTPUT_KEYS = {"fwd": ("u",), "jvp": ("u", "du"), "vjp": ("u", "qbar", "Dbar", "mubar")}
+
+
+@dataclasses.dataclass
+class Request:
+    """One solve request. ``make_inputs(device)`` returns the float64 tensors of
+    INPUT_KEYS[kind] on the device; it is called when the request is admitted,
+    on the stream of its pool."""
+    rid: int
+    kind: str
+    shape: tuple
+    make_inputs: object
+    arrival: float = 0.0
+    # filled in by the server
+    t_admit: float = None
+    t_done: float = None
+    status: int = None
+    cycles: list = dataclasses.field(default_factory=list)
+    rel: list = dataclasses.field(default_factory=list)
+    outputs: dict = None
+    pool_steps: tuple = None   # (step of the pool at admission, at completion)
+
+    @property
+    def solves(self):
+        return len(PHASES[self.kind])
+
+    def io_bytes(self):
+        n = int(np.prod(self.shape))
+        return 8 * n * (len(INPUT_KEYS[self.kind]) + len(OUTPUT_KEYS[self.kind]))
+
+
+class Pool:
+    """The slots of one grid shape: a context with batch = slots."""
+
+    def __init__(self, shape, h, slots, params, device):
+        import torch
+        self.torch = torch
+        self.shape, self.slots = tuple(shape), int(slots)
+        self.n = int(np.prod(self.shape))
+        self.device = device
+        self.stream = torch.cuda.Stream(device)
+        nz, ny, nx = self.shape
+        p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.slots, **params)
+        with torch.cuda.stream(self.stream):
+            ones = torch.ones((self.slots,) + self.shape, dtype=torch.float64, device=device)
+            st, self.ctx = dmg.dmg_setup(p, ones, torch.zeros_like(ones), stream=self.stream)
+        self.stream.synchronize()
+        del ones
+        if st != dmg.DMG_OK:
+            raise dmg.DMGError(st, dmg.dmg_last_error(None))
+        self.bytes = dmg.dmg_device_bytes(self.ctx)
+        self.free = list(range(self.slots - 1, -1, -1))
+        self.busy = {}        # slot -> [request, phase index, inputs]
+        self.steps = 0
+
+    def close(self):
+        if self.ctx is not None:
+            dmg.dmg_destroy(self.ctx)
+            self.ctx = None
+
+    def _check(self, st):
+        if st != dmg.DMG_OK:
+            raise dmg.DMGError(st, dmg.dmg_last_error(self.ctx))
+
+    def admit(self, req, now):
+        torch = self.torch
+        slot = self.free.pop()
+        with torch.cuda.stream(self.stream):
+            x = req.make_inputs(self.device)
+        self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=self.n))
+        self._check(dmg.dmg_slot_begin(self.ctx, slot, dmg.DMG_PHASE_FORWARD, x["q"], None, None, self.stream,
+                                       n=self.n))
+        self.busy[slot] = [req, 0, x]
+        req.t_admit = now
+        req.pool_steps = (self.steps, None)
+
+    def launch(self):
+        self._check(dmg.dmg_step_launch(self.ctx, self.stream))
+
+    def finish(self, clock):
+        """Wait for the step; start next phases; read out and release finished
+        requests. Returns the requests completed by this step."""
+        torch = self.torch
+        st, ended = dmg.dmg_step_finish(self.ctx, self.slots, self.stream)
+        self._check(st)
+        self.steps += 1
+        done = []
+        for slot in ended:
+            entry = self.busy[slot]
+            req, ph, x = entry
+            _, status, cyc, rel = dmg.dmg_slot_result(self.ctx, slot)
+            req.cycles.append(cyc)
+            req.rel.append(rel)
+            phases = PHASES[req.kind]
+            ok = status in (dmg.DMG_OK,)
+            if ok and ph + 1 < len(phases):
+                entry[1] = ph + 1
+                nxt = phases[ph + 1]
+                if nxt == dmg.DMG_PHASE_TANGENT:
+                    args = (x["dq"], x["dD"], x["dmu"])
+                else:
+                    args = (x["w"], None, None)
+                self._check(dmg.dmg_slot_begin(self.ctx, slot, nxt, *args, self.stream, n=self.n))
+                continue
+            req.status = status
+            if ok:
+                with torch.cuda.stream(self.stream):
+                    out = {k: torch.empty(self.shape, dtype=torch.float64, device=self.device)
+                           for k in OUTPUT_KEYS[req.kind]}
+                if req.kind == "fwd":
+                    self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], None, None, None, self.stream,
+                                                  n=self.n))
+                elif req.kind == "jvp":
+                    self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], out["du"], None, None, self.stream,
+                                                  n=self.n))
+                else:
+                    self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], out["qbar"], out["Dbar"],
+                                                  out["mubar"], self.stream, n=self.n))
+                req.outputs = out
+            done.append((slot, req))
+        if done:
+            self.stream.synchronize()
+            now = clock()
+            for slot, req in done:
+                req.t_done = now
+                req.pool_steps = (req.pool_steps[0], self.steps)
+                del self.busy[slot]
+                self.free.append(slot)
+        return [r for _, r in done]
+
+    def active(self):
+        return bool(self.busy)
+
+
+def plan_slots(shapes, per_slot_bytes, pool_budget, max_slots=64):
+    """Slots per shape: an equal share of the pool budget each, at most
+    max_slots, at least one, and batch * nz <= 65535."""
+    share = pool_budget / max(len(shapes), 1)
+    plan = {}
+    for s in shapes:
+        k = int(share // per_slot_bytes[s])
+        plan[s] = max(1, min(max_slots, k, 65535 // s[0]))
+    return plan
+
+
+class Server:
+    """Pools for the given shapes, sized to the device-memory budget.
+
+    budget_bytes: device memory for the pools and the requests' own tensors;
+    pool_fraction of it goes to the pools (slots are fixed at start), the rest
+    bounds the inputs and outputs of admitted requests. slots: an explicit
+    {shape: slots} plan instead of the budget split.
+    """
+
+    def __init__(self, shapes, h=0.5, budget_bytes=80e9, params=None, device="cuda", max_slots=64,
+                 slots=None, pool_fraction=0.75):
+        params = dict(params or {})
+        self.h, self.device = h, device
+        self.budget = float(budget_bytes)
+        shapes = [tuple(s) for s in shapes]
+        if slots is None:
+            probe = {}
+            for s in shapes:
+                p = Pool(s, h, 1, params, device)
+                probe[s] = p.bytes
+                p.close()
+            slots = plan_slots(shapes, probe, pool_fraction * self.budget, max_slots)
+        self.pools = {s: Pool(s, h, slots[s], params, device) for s in shapes}
+        self.pool_bytes = sum(p.bytes for p in self.pools.values())
+        if self.pool_bytes > self.budget:
+            raise ValueError("pools need %.1f GB, above the budget of %.1f GB" % (self.pool_bytes / 1e9,
+                                                                                   self.budget / 1e9))
+        self.io_bytes = 0
+
+    def close(self):
+        for p in self.pools.values():
+            p.close()
+
+    def _admit(self, queue, now):
+        """FIFO per shape: the oldest waiting request of each shape is admitted
+        when its pool has a free slot and its tensors fit the budget; a full
+        pool does not hold back requests of other shapes."""
+        blocked = set()
+        kept = collections.deque()
+        while queue:
+            req = queue.popleft()
+            pool = self.pools[tuple(req.shape)]
+            need = req.io_bytes()
+            if (req.shape in blocked or not pool.free or
+                    self.pool_bytes + self.io_bytes + need > self.budget):
+                blocked.add(req.shape)
+                kept.append(req)
+                continue
+            self.io_bytes += need
+            pool.admit(req, now)
+        queue.extend(kept)
+
+    def run(self, requests, realtime=True, keep_outputs=True):
+        """Serve the requests (arrival times in seconds from the start). With
+        realtime=False every request is available at once; keep_outputs=False
+        drops each result once it has been read back. Returns the served
+        requests and summary statistics."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        queue = collections.deque()
+        t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0
+        served = []
+        while pending or queue or any(p.active() for p in self.pools.values()):
+            now = clock()
+            while pending and (not realtime or pending[0].arrival <= now):
+                queue.append(pending.popleft())
+            self._admit(queue, now)
+            live = [p for p in self.pools.values() if p.active()]
+            for p in live:
+                p.launch()
+            for p in live:
+                for req in p.finish(clock):
+                    self.io_bytes -= req.io_bytes()
+                    if not keep_outputs:
+                        req.outputs = None
+                    served.append(req)
+            if not live and queue:
+                raise ValueError("request %d (%s) does not fit the memory budget even alone"
+                                 % (queue[0].rid, "x".join(map(str, queue[0].shape[::-1]))))
+            if not live and pending:
+                time.sleep(max(0.0, pending[0].arrival - clock()))
+        return served, summarize(served, clock())
+
+
+def summarize(served, wall):
+    lat = [1e3 * (r.t_done - r.arrival) for r in served if r.t_done is not None]
+    ok = [r for r in served if r.status == dmg.DMG_OK]
+    first = min((r.arrival for r in served), default=0.0)
+    last = max((r.t_done for r in served if r.t_done is not None), default=wall)
+    span = max(last - first, 1e-9)
+    return dict(requests=len(served), ok=len(ok), seconds=span,
+                requests_per_s=len(ok) / span, solves_per_s=sum(r.solves for r in ok) / span,
+                p50_ms=float(np.percentile(lat, 50)) if lat else None,
+                p99_ms=float(np.percentile(lat, 99)) if lat else None)
+
+
+def poisson_stream(n, rate, shapes, mix=(("fwd", 1), ("jvp", 1), ("vjp", 2)), seed=0, h=0.5):
+    """n requests with exponential inter-arrival times of mean 1/rate, shapes
+    drawn uniformly, kinds by the weights of mix, inputs from the tissue recipe
+    with a per-request seed (drawn on the device when the request is admitted)."""
+    from . import inputs
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    kinds = [k for k, _ in mix]
+    wts = np.array([w for _, w in mix], dtype=float)
+    reqs = []
+    for i in range(n):
+        shape = tuple(shapes[rng.integers(len(shapes))])
+        kind = kinds[rng.choice(len(kinds), p=wts / wts.sum())]
+        rseed = int(rng.integers(1 << 62))
+
+        def make(device, shape=shape, kind=kind, rseed=rseed):
+            return inputs.tissue_torch(shape, rseed, h=h, device=device, keys=INPUT_KEYS[kind])
+
+        reqs.append(Request(rid=i, kind=kind, shape=shape, make_inputs=make, arrival=float(t[i])))
+    return reqs
+
+
+def run_alone(req, h=0.5, params=None, device="cuda"):
+    """The request on its own: a context of batch 1, the whole-context calls."""
+    import torch
+    x = req.make_inputs(device)
+    S = dmg.Solver(x["D"], x["mu"], h, **(params or {}))
+    try:
+        u = S.solve(x["q"])
+        if req.kind == "fwd":
+            return {"u": u}
+        if req.kind == "jvp":
+            return {"u": u, "du": S.jvp(u, x["dq"], x["dD"], x["dmu"])}
+        qb, Db, mb = S.vjp(u, x["w"])
+        return {"u": u, "qbar": qb, "Dbar": Db, "mubar": mb}
+    finally:
+        S.close()
+
+
+def run_one_at_a_time(requests, h=0.5, params=None, device="cuda"):
+    """Every request alone and in arrival order (setup, solves, read-back);
+    returns the wall time in seconds."""
+    import torch
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        out = run_alone(r, h, params, device)
+        del out
+    torch.cuda.synchronize(device)
+    return time.perf_counter() - t0

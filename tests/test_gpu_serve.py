@@ -1,0 +1,97 @@
+"""Serving: forward, JVP and VJP requests of two grid shapes arrive while others
+run, are admitted into slots of per-shape pools as slots free up, and advance
+together step by step. Every served result must be bit for bit the result of
+the same request run alone on a context of batch 1; a request with invalid
+coefficients or non-finite input fails alone without disturbing the others.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(17, 17, 17), (9, 17, 33)]
+
+
+@pytest.fixture(scope="module")
+def serve():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_00760_b300 import build, serve as m
+    build.build()
+    return m
+
+
+def overlapped(served, shape):
+    """Some request of this pool was admitted while another one of the same
+    pool was between its admission and completion."""
+    iv = sorted(r.pool_steps for r in served if r.shape == shape)
+    return any(a2 > a1 and a2 < b1 for (a1, b1), (a2, _) in zip(iv, iv[1:]))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_served_results_equal_alone(serve, precision):
+    from paper_2608_00760_b300 import dmg
+    reqs = serve.poisson_stream(24, rate=2000.0, shapes=SHAPES, seed=11)
+    server = serve.Server(SHAPES, slots={s: 3 for s in SHAPES}, params=dict(precision=precision),
+                          budget_bytes=16e9)
+    try:
+        served, stats = server.run(reqs)
+    finally:
+        server.close()
+    assert stats["requests"] == 24 and stats["ok"] == 24
+    assert {r.kind for r in served} == {"fwd", "jvp", "vjp"}
+    for s in SHAPES:
+        assert overlapped(served, s), s
+    for r in served:
+        alone = serve.run_alone(r, params=dict(precision=precision))
+        assert set(alone) == set(r.outputs)
+        for k in alone:
+            assert torch.equal(r.outputs[k], alone[k]), (r.rid, r.kind, k)
+        assert r.status == dmg.DMG_OK and all(x <= 1e-10 for x in r.rel)
+
+
+def test_failed_requests_are_isolated(serve):
+    from paper_2608_00760_b300 import dmg, inputs
+    good = serve.poisson_stream(6, rate=1000.0, shapes=SHAPES[:1], seed=12)
+
+    def bad_coeffs(device):
+        x = inputs.tissue_torch(SHAPES[0], 5, device=device, keys=("D", "mu", "q"))
+        x["D"] = -x["D"]
+        return x
+
+    def nan_source(device):
+        x = inputs.tissue_torch(SHAPES[0], 6, device=device, keys=("D", "mu", "q"))
+        x["q"][8, 8, 8] = float("nan")
+        return x
+
+    bad = [serve.Request(rid=100, kind="fwd", shape=SHAPES[0], make_inputs=bad_coeffs, arrival=0.0),
+           serve.Request(rid=101, kind="fwd", shape=SHAPES[0], make_inputs=nan_source, arrival=0.0)]
+    server = serve.Server(SHAPES[:1], slots={SHAPES[0]: 4}, budget_bytes=8e9)
+    try:
+        served, stats = server.run(bad + good)
+    finally:
+        server.close()
+    by = {r.rid: r for r in served}
+    assert by[100].status == dmg.DMG_EINVAL and by[101].status == dmg.DMG_ENAN
+    for r in good:
+        s = by[r.rid]
+        assert s.status == dmg.DMG_OK
+        alone = serve.run_alone(s)
+        assert all(torch.equal(s.outputs[k], alone[k]) for k in alone)
+
+
+def test_budget_limits_admission(serve):
+    # room for the pool and one request's tensors: requests run one after another
+    reqs = serve.poisson_stream(4, rate=1e4, shapes=SHAPES[:1], mix=(("fwd", 1),), seed=13)
+    probe = serve.Server(SHAPES[:1], slots={SHAPES[0]: 4}, budget_bytes=8e9)
+    pool_bytes = probe.pool_bytes
+    probe.close()
+    server = serve.Server(SHAPES[:1], slots={SHAPES[0]: 4}, budget_bytes=pool_bytes + 1.5 * reqs[0].io_bytes())
+    try:
+        served, stats = server.run(reqs)
+    finally:
+        server.close()
+    assert stats["ok"] == 4
+    iv = sorted(r.pool_steps for r in served)
+    assert all(a2 >= b1 for (_, b1), (a2, _) in zip(iv, iv[1:]))
