@@ -122,7 +122,7 @@ def _axis_factor_torch(n, h, corr, device):
     import torch
     key = (n, h, corr, str(device))
     if key not in _FACTORS:
-        _FACTORS[key] = torch.from_numpy(np.ascontiguousarray(_axis_factor(n, h, corr))).to(device)
+        _FACTORS[key] = torch.from_numpy(np.ascontiguousarray(_axis_factor(n, h, corr))).to(device).float()
     return _FACTORS[key]
 
 
@@ -135,11 +135,14 @@ def tissue_torch(shape, seed: int, h: float = 0.5, device="cuda", keys=("D", "mu
     f64 = dict(dtype=torch.float64, device=device)
 
     def field(corr, std):
+        # the Kronecker products in FP32 (the field is an input, not solver
+        # arithmetic), then FP64
         Lz, Ly, Lx = (_axis_factor_torch(n, h, corr, device) for n in shape)
-        xi = torch.randn((Lz.shape[1], Ly.shape[1], Lx.shape[1]), generator=g, **f64)
+        xi = torch.randn((Lz.shape[1], Ly.shape[1], Lx.shape[1]), generator=g, dtype=torch.float32,
+                         device=device)
         t = torch.einsum("abc,xc->abx", xi, Lx)
         t = torch.einsum("abx,yb->ayx", t, Ly)
-        return std * torch.einsum("ayx,za->zyx", t, Lz)
+        return std * torch.einsum("ayx,za->zyx", t, Lz).double()
 
     mus = torch.exp(field(5.0, 0.3))
     mua = 0.01 * torch.exp(field(5.0, 0.3))

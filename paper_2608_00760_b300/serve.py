@@ -90,6 +90,8 @@ class Pool:
         self.free = list(range(self.slots - 1, -1, -1))
         self.busy = {}        # slot -> [request, phase index, inputs]
         self.steps = 0
+        self.step_event = None      # recorded after the launched step's read-back
+        self.completing = []        # (event after the read-outs, requests)
 
     def close(self):
         if self.ctx is not None:
@@ -114,12 +116,22 @@ class Pool:
 
     def launch(self):
         self._check(dmg.dmg_step_launch(self.ctx, self.stream))
+        self.step_event = self.torch.cuda.Event()
+        self.step_event.record(self.stream)
 
-    def finish(self, clock):
-        """Wait for the step; start next phases; read out and release finished
-        requests. Returns the requests completed by this step."""
+    def in_flight(self):
+        return self.step_event is not None
+
+    def step_done(self):
+        return self.step_event is not None and self.step_event.query()
+
+    def finish(self):
+        """Take the finished step: start next phases, enqueue the read-outs of
+        requests whose last phase ended and free their slots (later work on the
+        pool's stream is ordered after the read-outs)."""
         torch = self.torch
         st, ended = dmg.dmg_step_finish(self.ctx, self.slots, self.stream)
+        self.step_event = None
         self._check(st)
         self.steps += 1
         done = []
@@ -157,17 +169,31 @@ class Pool:
                 req.outputs = out
             done.append((slot, req))
         if done:
-            self.stream.synchronize()
-            now = clock()
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
             for slot, req in done:
-                req.t_done = now
                 req.pool_steps = (req.pool_steps[0], self.steps)
+                self.busy[slot][2] = None
                 del self.busy[slot]
                 self.free.append(slot)
-        return [r for _, r in done]
+            self.completing.append((ev, [r for _, r in done]))
+
+    def completed(self, clock):
+        """Requests whose read-outs have finished."""
+        out = []
+        while self.completing and self.completing[0][0].query():
+            _, reqs = self.completing.pop(0)
+            now = clock()
+            for r in reqs:
+                r.t_done = now
+            out += reqs
+        return out
 
     def active(self):
         return bool(self.busy)
+
+    def idle(self):
+        return not self.busy and not self.completing and self.step_event is None
 
 
 def plan_slots(shapes, per_slot_bytes, pool_budget, max_slots=64):
@@ -243,25 +269,39 @@ class Server:
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
         served = []
-        while pending or queue or any(p.active() for p in self.pools.values()):
+        pools = list(self.pools.values())
+        while pending or queue or not all(p.idle() for p in pools):
             now = clock()
             while pending and (not realtime or pending[0].arrival <= now):
                 queue.append(pending.popleft())
             self._admit(queue, now)
-            live = [p for p in self.pools.values() if p.active()]
-            for p in live:
-                p.launch()
-            for p in live:
-                for req in p.finish(clock):
+            # each pool advances on its own: a finished step is taken and the
+            # next one launched at once, so pools with short steps do not wait
+            # for pools with long ones
+            moved = False
+            for p in pools:
+                if p.step_done():
+                    p.finish()
+                    moved = True
+                if not p.in_flight() and p.active():
+                    p.launch()
+                    moved = True
+                for req in p.completed(clock):
                     self.io_bytes -= req.io_bytes()
                     if not keep_outputs:
                         req.outputs = None
                     served.append(req)
-            if not live and queue:
-                raise ValueError("request %d (%s) does not fit the memory budget even alone"
-                                 % (queue[0].rid, "x".join(map(str, queue[0].shape[::-1]))))
-            if not live and pending:
-                time.sleep(max(0.0, pending[0].arrival - clock()))
+                    moved = True
+            if moved:
+                continue
+            if all(p.idle() for p in pools):
+                if queue:
+                    raise ValueError("request %d (%s) does not fit the memory budget even alone"
+                                     % (queue[0].rid, "x".join(map(str, queue[0].shape[::-1]))))
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival - clock()))
+            else:
+                time.sleep(2e-5)
         return served, summarize(served, clock())
 
 

@@ -173,3 +173,23 @@ def test_batch_shape_limits(dmg):
     p = dmg.dmg_default_params(nx=17, ny=17, nz=17, h=1.0, batch=4000)
     st, ctx = dmg.dmg_setup(p, None, None)
     assert st == dmg.DMG_EINVAL and "65535" in dmg.dmg_last_error(None)
+
+
+def test_batch_backward_through_autograd_function(dmg):
+    # the VI step as a sampler runs it: forward of every sample, then
+    # loss.backward() through the torch.autograd.Function; each sample's
+    # gradients are bitwise those of the same sample through autograd alone
+    from paper_2608_00760_b300 import autograd
+    w = inputs.vi_batch(17, 3, seed=36)
+    Tg = lambda a: T(a).requires_grad_(True)
+    D, mu, q = Tg(w["D"]), Tg(w["mu"]), Tg(w["q"])
+    u = autograd.solve(q, D, mu, w["h"], precision=1)
+    (u * T(w["w"])).sum().backward()
+    for b in range(3):
+        Db, mub, qb = Tg(w["D"][b]), Tg(w["mu"][b]), Tg(w["q"][b])
+        ub = autograd.solve(qb, Db, mub, w["h"], precision=1)
+        (ub * T(w["w"][b])).sum().backward()
+        assert torch.equal(u[b].detach(), ub.detach())
+        for got, ref in ((q.grad[b], qb.grad), (D.grad[b], Db.grad), (mu.grad[b], mub.grad)):
+            assert torch.equal(got, ref), b
+    autograd.clear_cache()

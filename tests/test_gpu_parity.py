@@ -172,6 +172,24 @@ def test_mixed_precision_matches_fp64_oracle(dmg):
     assert rel(mb, mbr) <= TOL_CONV
 
 
+@pytest.mark.parametrize("n", [257, 513])
+def test_mixed_matches_fp64_gpu_at_full_size(dmg, n):
+    # the full-size configurations: mixed precision against the FP64 GPU path
+    # (the oracle at these sizes is too slow); both at rtol 1e-10
+    w = inputs.tissue_torch((n, n, n), 9, device="cuda", keys=("D", "mu", "q", "w"))
+    out = {}
+    for prec in (dmg.DMG_FP64, dmg.DMG_MIXED):
+        S = dmg.Solver(w["D"], w["mu"], 0.5, precision=prec)
+        u = S.solve(w["q"])
+        assert S.last_info.rel_residual <= 1e-10
+        qb, Db, mb = S.vjp(u, w["w"])
+        assert S.last_info.rel_residual <= 1e-10
+        out[prec] = (u, qb, Db, mb)
+        S.close()
+    for a, b in zip(out[dmg.DMG_MIXED], out[dmg.DMG_FP64]):
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-8
+
+
 def test_host_pointers_give_device_results(dmg):
     w = make("unit_cube", dict(n=17), seed=6)
     S = dmg.Solver(w["D"], w["mu"], w["h"])            # numpy (host) coefficients
