@@ -183,6 +183,35 @@ dmg_status dmg_vjp(dmg_ctx *ctx, const double *u, const double *w, int cycles, d
                    double *Dbar, double *mubar, dmg_info *info, void *stream);
 
 /*
+ * The forward model of the paper's application (Sec. 2.5.3, Eq. response):
+ *   L_e = R(q) = M(mu S(q)),
+ * the absorbed energy density mu u on the voxels that lie at least `edge`
+ * (a length, in the units of h; the paper masks 0.2 cm) from every face of
+ * the grid. Along an axis of n vertices, voxel i is kept when
+ * m <= i <= n-1-m, where m is the smallest integer with m h >= edge; the
+ * other voxels of every output field are written as 0 (M^T M applied: the
+ * data vector is the kept voxels in C order). edge = 0 keeps every voxel.
+ *
+ * dmg_response      -- Le = R(q); u (may be NULL) receives S(q).
+ * dmg_response_jvp  -- dLe = M(mu du + dmu u), du = S(dq - (dA) u): the tangent
+ *                      of R at (q, D, mu) in direction (dq, dD, dmu), any of
+ *                      which may be NULL (zero); u = S(q) is required.
+ * dmg_response_vjp  -- the pull-back of a cotangent rbar on Le:
+ *                      w = mu M^T rbar, lambda = S^dagger w, qbar = lambda,
+ *                      Dbar as in dmg_vjp with that lambda, and
+ *                      mubar = -lambda u + u M^T rbar (the solve's term plus the
+ *                      explicit factor mu). u = S(q) is needed for Dbar/mubar.
+ * Stopping rule and statuses as in dmg_solve (the adjoint iterates to rtol).
+ * Returns DMG_EINVAL for edge < 0 or not finite.
+ */
+dmg_status dmg_response(dmg_ctx *ctx, const double *q, double edge, double *Le, double *u,
+                        dmg_info *info, void *stream);
+dmg_status dmg_response_jvp(dmg_ctx *ctx, const double *u, const double *dq, const double *dD,
+                            const double *dmu, double edge, double *dLe, dmg_info *info, void *stream);
+dmg_status dmg_response_vjp(dmg_ctx *ctx, const double *u, const double *rbar, double edge,
+                            double *qbar, double *Dbar, double *mubar, dmg_info *info, void *stream);
+
+/*
  * dmg_residual -- out[2b] = ||q_b - A_b u_b||_2 and out[2b+1] = ||q_b||_2 over
  * interior vertices of every sample b, in FP64 (out is a host array of
  * 2 * batch doubles).

@@ -295,3 +295,55 @@ def direct_solve(D, mu, h, q, harmonic=False):
     u = np.zeros(D.shape)
     u.reshape(-1)[idx] = spla.spsolve(A.tocsc(), _arr(q).reshape(-1)[idx])
     return u
+
+
+# ---------------------------------------------------------------------------
+# The application's forward model (Sec. 2.5.3, Eq. response): R(q) = M(mu S(q)),
+# the absorbed energy density L_e = mu rho on the voxels outside the masked edge
+# region (Sec. 2.5.1: data masked to a depth of 0.2 cm on all edges). Reading:
+# a vertex at coordinate x = i h on an axis of length (n-1) h is kept when its
+# distance to both faces, min(x, (n-1) h - x), is at least the edge depth (with a
+# relative slack of 1e-12 for the rounding of i h); fields are returned on the
+# full grid with the other voxels set to 0.
+
+def edge_mask(shape, h, edge):
+    """Boolean mask of the kept voxels (Eq. response's M), from the distances."""
+    keep = np.ones(shape, dtype=bool)
+    for axis, n in enumerate(shape):
+        x = np.arange(n) * h
+        dist = np.minimum(x, (n - 1) * h - x)
+        ok = dist >= edge * (1.0 - 1e-12)
+        sl = [None] * len(shape)
+        sl[axis] = slice(None)
+        keep &= ok[tuple(sl)]
+    return keep
+
+
+def response(H, q, edge, rtol=1e-10):
+    """(L_e, u): u = S(q) by the oracle's V-cycles, L_e = M(mu u)."""
+    u, _, _ = H.solve(q, rtol=rtol)
+    return np.where(edge_mask(H.shape, H.h, edge), H.mu * u, 0.0), u
+
+
+def response_jvp(H, u, dq, dD, dmu, edge, rtol=1e-10):
+    """Tangent of L_e: M(dmu u + mu du), du = S(dq - dA u)."""
+    dq = np.zeros(H.shape) if dq is None else dq
+    du, _ = H.jvp(u, dq, dD, dmu, rtol=rtol)
+    t = H.mu * du
+    if dmu is not None:
+        t = t + _arr(dmu) * u
+    return np.where(edge_mask(H.shape, H.h, edge), t, 0.0)
+
+
+def response_vjp(H, u, rbar, edge, rtol=1e-10):
+    """Pull-back of a cotangent rbar on L_e. The chain rule through L_e = M(mu u):
+    the cotangent of u is w = mu M^T rbar (interior), the solve's VJP gives
+    (qbar, Dbar, mubar_S), and the explicit factor mu adds u M^T rbar to mubar."""
+    m = edge_mask(H.shape, H.h, edge)
+    w = np.where(m, H.mu * _arr(rbar), 0.0)
+    w[0, :, :] = w[-1, :, :] = 0.0
+    w[:, 0, :] = w[:, -1, :] = 0.0
+    w[:, :, 0] = w[:, :, -1] = 0.0
+    qb, Db, mb, _ = H.vjp(u, w, rtol=rtol)
+    mb = mb + np.where(m, u * _arr(rbar), 0.0)
+    return qb, Db, mb

@@ -60,6 +60,33 @@ class DMGSolve(torch.autograd.Function):
         return ctx.solver.jvp(u, dq=_c(dq), dD=_c(dD), dmu=_c(dmu))
 
 
+class DMGResponse(torch.autograd.Function):
+    """L_e = M(mu S(q)), the application's forward model (Sec. 2.5.3, Eq.
+    response), with its pull-back (dmg_response_vjp) and push-forward
+    (dmg_response_jvp)."""
+
+    @staticmethod
+    def forward(ctx, q, D, mu, solver, edge):
+        Le, u = solver.response(q.contiguous(), edge)
+        ctx.solver, ctx.edge = solver, float(edge)
+        ctx.save_for_backward(u)
+        ctx.fwd = u
+        return Le
+
+    @staticmethod
+    def backward(ctx, rbar):
+        (u,) = ctx.saved_tensors
+        qb, Db, mb = ctx.solver.response_vjp(u, rbar.contiguous(), ctx.edge)
+        need = ctx.needs_input_grad
+        return (qb if need[0] else None, Db if need[1] else None, mb if need[2] else None, None, None)
+
+    @staticmethod
+    def jvp(ctx, dq, dD, dmu, _solver=None, _edge=None):
+        u = ctx.fwd
+        ctx.fwd = None
+        return ctx.solver.response_jvp(u, ctx.edge, dq=_c(dq), dD=_c(dD), dmu=_c(dmu))
+
+
 class _Cache:
     """Solver contexts for recently used coefficient fields.
 
@@ -102,6 +129,13 @@ def solve(q, D, mu, h, recompute=False, **params):
     """
     s = _cache.get(D, mu, h, params)
     return DMGSolve.apply(q, D, mu, s, recompute)
+
+
+def response(q, D, mu, h, edge, **params):
+    """L_e = M(mu S(q)) with the edge mask of depth `edge` (Eq. response),
+    differentiable w.r.t. q, D and mu (reverse and forward mode)."""
+    s = _cache.get(D, mu, h, params)
+    return DMGResponse.apply(q, D, mu, s, edge)
 
 
 def clear_cache():

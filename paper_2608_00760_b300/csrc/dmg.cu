@@ -1350,6 +1350,122 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// first kept index per axis: the smallest m with m h >= edge (1 - 1e-12)
+dmg_status margins(dmg_ctx *c, double edge, dmgk::Margins *m) {
+    if (!(edge >= 0.0) || !std::isfinite(edge)) return fail(c, DMG_EINVAL, "edge must be finite and >= 0");
+    const double h = c->p.h, e = edge * (1.0 - 1e-12);
+    auto first = [&](int n) {
+        long long k = (long long)std::ceil(e / h);
+        if (k < 0) k = 0;
+        return (int)std::min<long long>(k, n);
+    };
+    m->x = first(c->p.nx);
+    m->y = first(c->p.ny);
+    m->z = first(c->p.nz);
+    return DMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmg_status dmg_response(dmg_ctx *c, const double *q, double edge, double *Le, double *u, dmg_info *info,
+                        void *stream) {
+    return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        if (!q || !Le) return fail(c, DMG_EINVAL, "q and Le must not be NULL");
+        dmgk::Margins m;
+        TRY(margins(c, edge, &m));
+        info_reset(info);
+        cudaStream_t s = S(stream);
+        Level &l = c->L[0];
+        TRY(stage_in(c, q, l.f, false, s));
+        dmg_status st = iterate(c, false, c->p.fixed_cycles, info, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) return st;
+        if (u) TRY(stage_out(c, l.u, u, s));
+        dmgk::k_response<<<grid_all(l.g), blk(), 0, s>>>(l.g, m, l.mu, l.u, nullptr, nullptr, c->T3);
+        TRY(check_launch(c, "response"));
+        TRY(stage_out(c, c->T3, Le, s));
+        TRY(end_call(c, s));
+        return st;
+    });
+}
+
+dmg_status dmg_response_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
+                            double edge, double *dLe, dmg_info *info, void *stream) {
+    return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        if (!u || !dLe) return fail(c, DMG_EINVAL, "u and dLe must not be NULL");
+        dmgk::Margins m;
+        TRY(margins(c, edge, &m));
+        info_reset(info);
+        cudaStream_t s = S(stream);
+        Level &l = c->L[0];
+        if (dq) {
+            TRY(stage_in(c, dq, l.f, false, s));
+        } else {
+            CUDA_TRY(c, cudaMemsetAsync(l.f, 0, l.n * sizeof(double), s));
+        }
+        TRY(stage_in(c, u, c->U0, true, s));
+        if (dD) TRY(stage_in(c, dD, c->T1, false, s));
+        if (dmu) TRY(stage_in(c, dmu, c->T2, false, s));
+        if (dD || dmu) {
+            const double ih2 = 1.0 / (l.h * l.h);
+            dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0, dD ? c->T1 : nullptr, dmu ? c->T2 : nullptr,
+                                                       l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
+            TRY(check_launch(c, "dA"));
+        }
+        dmg_status st = iterate(c, false, c->p.fixed_cycles, info, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) return st;
+        // dLe = M(mu du + dmu u)
+        dmgk::k_response<<<grid_all(l.g), blk(), 0, s>>>(l.g, m, l.mu, l.u, dmu ? c->T2 : nullptr, c->U0, c->T3);
+        TRY(check_launch(c, "response"));
+        TRY(stage_out(c, c->T3, dLe, s));
+        TRY(end_call(c, s));
+        return st;
+    });
+}
+
+dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, double edge, double *qbar,
+                            double *Dbar, double *mubar, dmg_info *info, void *stream) {
+    return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        if (!rbar) return fail(c, DMG_EINVAL, "rbar must not be NULL");
+        if ((Dbar || mubar) && !u) return fail(c, DMG_EINVAL, "u is needed for Dbar / mubar");
+        dmgk::Margins m;
+        TRY(margins(c, edge, &m));
+        info_reset(info);
+        cudaStream_t s = S(stream);
+        Level &l = c->L[0];
+        TRY(stage_in(c, rbar, c->T3, false, s));
+        dmgk::k_response_cot<<<grid_all(l.g), blk(), 0, s>>>(l.g, m, l.mu, c->T3, l.f);
+        TRY(check_launch(c, "response_cot"));
+        dmg_status st = iterate(c, true, 0, info, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) return st;
+        if (qbar) TRY(stage_out(c, l.u, qbar, s));
+        if (Dbar || mubar) {
+            TRY(stage_in(c, u, c->U0, true, s));
+            const double ih2 = 1.0 / (l.h * l.h);
+            dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                         c->p.face_mean == DMG_FACE_HARMONIC, Dbar ? c->T1 : nullptr,
+                                                         c->T2);
+            TRY(check_launch(c, "grad"));
+            if (mubar) {
+                dmgk::k_response_mubar<<<grid_all(l.g), blk(), 0, s>>>(l.g, m, c->U0, c->T3, c->T2);
+                TRY(check_launch(c, "response_mubar"));
+            }
+            if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
+            if (mubar) TRY(stage_out(c, c->T2, mubar, s));
+        }
+        TRY(end_call(c, s));
+        return st;
+    });
+}
+
 dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *out, void *stream) {
     return guarded(c, [&]() -> dmg_status {
         if (!q || !u || !out) return fail(c, DMG_EINVAL, "q, u and out must not be NULL");

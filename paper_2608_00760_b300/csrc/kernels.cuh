@@ -1009,6 +1009,55 @@ __global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict
     y[p] = f64_to_f32_shift(x[p], -ms[smp].e_cur);
 }
 
+// ---------------------------------------------------------------------------
+// The application's forward model (Sec. 2.5.3, Eq. response): L_e = M(mu u),
+// M keeping the voxels at least `edge` from every face of the grid. Margins
+// (m.x, m.y, m.z) are the first kept index per axis; voxel (i, j, k) is kept
+// when m.x <= i <= nx-1-m.x and likewise in y, z. All vertices, every sample.
+
+struct Margins {
+    int x, y, z;
+    __device__ __forceinline__ bool kept(const Geom &g, int i, int j, int k) const {
+        return i >= x && i <= g.nx - 1 - x && j >= y && j <= g.ny - 1 - y && k >= z && k <= g.nz - 1 - z;
+    }
+};
+
+// out = M(mu a + b c): mode 0: out = M(mu u) (a = u);
+// mode 1 (tangent): out = M(mu du + dmu u) with a = du, b = dmu, c = u
+__global__ void __launch_bounds__(256) k_response(Geom g, Margins m, const double *__restrict__ mu,
+                                                  const double *__restrict__ a, const double *__restrict__ b,
+                                                  const double *__restrict__ c, double *__restrict__ out) {
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long p = g.pos(i, j, k) + smp * g.sb;
+    double v = 0.0;
+    if (m.kept(g, i, j, k)) {
+        v = mu[p] * a[p];
+        if (b) v = fma(b[p], c[p], v);
+    }
+    out[p] = v;
+}
+
+// cotangent of the solution for a cotangent rbar on L_e: w = mu M^T rbar (interior
+// vertices; zero on the boundary), and the explicit part of the mu gradient,
+// mubar += u M^T rbar
+__global__ void __launch_bounds__(256) k_response_cot(Geom g, Margins m, const double *__restrict__ mu,
+                                                      const double *__restrict__ rbar, double *__restrict__ w) {
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long p = g.pos(i, j, k) + smp * g.sb;
+    const bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+    w[p] = interior && m.kept(g, i, j, k) ? mu[p] * rbar[p] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_response_mubar(Geom g, Margins m, const double *__restrict__ u,
+                                                        const double *__restrict__ rbar, double *__restrict__ mubar) {
+    int i, j, k, smp;
+    if (!vertex_ijk(g, i, j, k, smp)) return;
+    const long long p = g.pos(i, j, k) + smp * g.sb;
+    if (m.kept(g, i, j, k)) mubar[p] = fma(u[p], rbar[p], mubar[p]);
+}
+
 // x = 0 on the interior vertices of the active samples
 template <class T>
 __global__ void __launch_bounds__(256) k_zero_interior(Geom g, T *__restrict__ x, const int *act) {

@@ -50,7 +50,8 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_destroy", "dmg_strerror", "dmg_last_error", "dmg_levels", "dmg_level_shape",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
-           "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes")
+           "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
+           "dmg_response_vjp")
 
 _lib = None
 
@@ -95,6 +96,9 @@ def lib():
             "dmg_slot_result": (i, [vp, i, P(i), P(i), P(d)]),
             "dmg_slot_read": (i, [vp, i, vp, vp, vp, vp, vp]),
             "dmg_device_bytes": (ctypes.c_size_t, [vp]),
+            "dmg_response": (i, [vp, vp, d, vp, vp, P(dmg_info), vp]),
+            "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
+            "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -201,6 +205,22 @@ def dmg_residual_static(params: dmg_params, D, mu, q, u, stream=None):
     st = lib().dmg_residual_static(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _ptr(q, n), _ptr(u, n), out,
                                    _stream(stream))
     return st, (out[0], out[1])
+
+
+def dmg_response(ctx, q, edge, Le, u=None, info=None, stream=None, n=None):
+    return lib().dmg_response(ctx, _ptr(q, n), float(edge), _ptr(Le, n), _ptr(u, n),
+                              ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def dmg_response_jvp(ctx, u, dq, dD, dmu, edge, dLe, info=None, stream=None, n=None):
+    return lib().dmg_response_jvp(ctx, _ptr(u, n), _ptr(dq, n), _ptr(dD, n), _ptr(dmu, n), float(edge),
+                                  _ptr(dLe, n), ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def dmg_response_vjp(ctx, u, rbar, edge, qbar, Dbar, mubar, info=None, stream=None, n=None):
+    return lib().dmg_response_vjp(ctx, _ptr(u, n), _ptr(rbar, n), float(edge), _ptr(qbar, n), _ptr(Dbar, n),
+                                  _ptr(mubar, n), ctypes.byref(info) if info is not None else None,
+                                  _stream(stream))
 
 
 def dmg_slot_load(ctx, slot, D, mu, stream=None, n=None):
@@ -349,6 +369,28 @@ class Solver:
         info = dmg_info()
         self._check(dmg_vjp(self.ctx, u if (need[1] or need[2]) else None, w, cycles, qb, Db, mb, info,
                             stream, n=self.n))
+        self.last_info = info
+        return qb, Db, mb
+
+    def response(self, q, edge, stream=None):
+        """(Le, u): Le = M(mu S(q)) with the edge mask of depth `edge` (see dmg_response)."""
+        Le, u = self._empty(q), self._empty(q)
+        info = dmg_info()
+        self._check(dmg_response(self.ctx, q, edge, Le, u, info, stream, n=self.n))
+        self.last_info = info
+        return Le, u
+
+    def response_jvp(self, u, edge, dq=None, dD=None, dmu=None, stream=None):
+        dLe = self._empty(u)
+        info = dmg_info()
+        self._check(dmg_response_jvp(self.ctx, u, dq, dD, dmu, edge, dLe, info, stream, n=self.n))
+        self.last_info = info
+        return dLe
+
+    def response_vjp(self, u, rbar, edge, stream=None):
+        qb, Db, mb = self._empty(rbar), self._empty(rbar), self._empty(rbar)
+        info = dmg_info()
+        self._check(dmg_response_vjp(self.ctx, u, rbar, edge, qb, Db, mb, info, stream, n=self.n))
         self.last_info = info
         return qb, Db, mb
 
