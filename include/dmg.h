@@ -139,7 +139,8 @@ void dmg_default_params(dmg_params *p);
  *   D, mu   vertex fields of the diffusion coefficient (> 0) and absorption
  *           (>= 0), copied into the context; the caller may free them after.
  *   out     receives the new context (NULL on failure).
- * All device memory is allocated here; solve/jvp/vjp allocate nothing.
+ * All device memory is allocated here; solve/jvp/vjp allocate nothing
+ * (dmg_vjp_unrolled allocates its own work buffers on first use).
  * Returns DMG_EINVAL for an unsupported shape or parameter, or when the
  * coarsest matrix is not positive definite; DMG_ENOMEM when memory runs out.
  */
@@ -181,6 +182,27 @@ dmg_status dmg_jvp(dmg_ctx *ctx, const double *u, const double *dq, const double
  */
 dmg_status dmg_vjp(dmg_ctx *ctx, const double *u, const double *w, int cycles, double *qbar,
                    double *Dbar, double *mubar, dmg_info *info, void *stream);
+
+/*
+ * dmg_vjp_unrolled -- the exact gradient of <w, S_m(q; D, mu)> for the
+ * fixed-count solver S_m: m FP64 V-cycles from u = 0 (Sec. 2.2), differentiated
+ * through every iterate and through the coarsened coefficients of every level
+ * (the pull-back of Sec. 2.4 extended to D and mu, which Sec. 4 names as future
+ * work). It differs from dmg_vjp's gradient, which is that of the exact
+ * solution, by the truncation of S_m; the two meet as m grows.
+ *   m        cycles (>= 1); stride: iterates are recomputed from level-0
+ *            checkpoints taken every `stride` cycles (0: ceil(sqrt(m))), so
+ *            the memory grows with m / stride, not with m.
+ *   u        receives S_m(q) (may be NULL); qbar = S_m^T w; Dbar, mubar the
+ *            coefficient gradients (each may be NULL).
+ * The forward cycles here use the grid kernels only (full defect, no
+ * single-CTA tail), so S_m agrees with dmg_solve's fixed-cycle iterate to
+ * rounding. Allocates its work buffers (about 2 (nu1 + nu2) + 9 fields per
+ * level plus the checkpoints) on the first call and when m / stride grows.
+ * Always FP64.
+ */
+dmg_status dmg_vjp_unrolled(dmg_ctx *ctx, const double *q, const double *w, int m, int stride,
+                            double *u, double *qbar, double *Dbar, double *mubar, void *stream);
 
 /*
  * The forward model of the paper's application (Sec. 2.5.3, Eq. response):

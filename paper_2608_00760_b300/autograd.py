@@ -60,6 +60,29 @@ class DMGSolve(torch.autograd.Function):
         return ctx.solver.jvp(u, dq=_c(dq), dD=_c(dD), dmu=_c(dmu))
 
 
+class DMGSolveUnrolled(torch.autograd.Function):
+    """u = S_m(q; D, mu), m fixed FP64 V-cycles from u = 0 (the solver must be
+    set up with fixed_cycles = m), whose backward is the exact derivative of
+    the m-cycle iteration through every iterate and the coarsened coefficients
+    (dmg_vjp_unrolled). Only q is kept for backward: the iterates are recomputed
+    there from checkpoints every `stride` cycles (0: about sqrt(m))."""
+
+    @staticmethod
+    def forward(ctx, q, D, mu, solver, m, stride=0):
+        q = q.contiguous()
+        u = solver.solve(q)
+        ctx.solver, ctx.m, ctx.stride = solver, int(m), int(stride)
+        ctx.save_for_backward(q)
+        return u
+
+    @staticmethod
+    def backward(ctx, w):
+        (q,) = ctx.saved_tensors
+        _, qb, Db, mb = ctx.solver.vjp_unrolled(q, w.contiguous(), ctx.m, ctx.stride)
+        need = ctx.needs_input_grad
+        return (qb if need[0] else None, Db if need[1] else None, mb if need[2] else None, None, None, None)
+
+
 class DMGResponse(torch.autograd.Function):
     """L_e = M(mu S(q)), the application's forward model (Sec. 2.5.3, Eq.
     response), with its pull-back (dmg_response_vjp) and push-forward
@@ -121,12 +144,22 @@ class _Cache:
 _cache = _Cache()
 
 
-def solve(q, D, mu, h, recompute=False, **params):
+def solve(q, D, mu, h, recompute=False, unrolled=False, stride=0, **params):
     """u = A(D, mu)^{-1} q, differentiable w.r.t. q, D and mu (reverse and forward mode).
 
-    q, D, mu: float64 CUDA tensors of shape (nz, ny, nx) over all vertices.
+    q, D, mu: float64 CUDA tensors of shape (nz, ny, nx) over all vertices (or
+    (B, nz, ny, nx) for a batch).
     params: dmg_params fields (rtol, precision, nu1, nu2, face_mean, ...).
+    unrolled=True (with fixed_cycles=m in params): u = S_m(q), the m-cycle
+    iterate, and its backward is the exact derivative of the m-cycle solver
+    (dmg_vjp_unrolled) instead of the converged-solution gradient.
     """
+    if unrolled:
+        m = int(params.get("fixed_cycles", 0))
+        if m < 1:
+            raise ValueError("unrolled=True needs fixed_cycles = m >= 1")
+        s = _cache.get(D, mu, h, params)
+        return DMGSolveUnrolled.apply(q, D, mu, s, m, stride)
     s = _cache.get(D, mu, h, params)
     return DMGSolve.apply(q, D, mu, s, recompute)
 

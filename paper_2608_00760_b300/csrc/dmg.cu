@@ -17,6 +17,7 @@
 
 #include "../../include/dmg.h"
 #include "kernels.cuh"
+#include "unrolled.cuh"
 
 using dmgk::Geom;
 
@@ -59,6 +60,16 @@ struct Graph {
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches = 0;
     std::vector<int> prof;
+};
+
+// Work buffers of the unrolled gradient on one level: cotangents of u and f,
+// face cotangents (x, y, z faces at their lower vertex), mu and D cotangents, a
+// scratch field, and the states after every half-sweep of one V-cycle (plus
+// the entry state when there is no pre-smoothing).
+struct ULevel {
+    double *ub = nullptr, *fb = nullptr, *bx = nullptr, *by = nullptr, *bz = nullptr;
+    double *mub = nullptr, *Db = nullptr, *tmp = nullptr;
+    std::vector<double *> st;
 };
 
 // Host-side state of one slot of the slot-level (serving) interface.
@@ -107,6 +118,10 @@ struct dmg_ctx {
     // step graph per direction ([0] forward and tangent phases, masked by act;
     // [1] adjoint phases, masked by act_a)
     std::vector<Slot> slots;
+    // unrolled gradient: per-level work buffers and level-0 checkpoints (allocated on first use)
+    ULevel un[kMaxLevels];
+    bool un_ready = false;
+    std::vector<double *> ck;
     int *act_a = nullptr, *hact_a = nullptr;
     Graph g_srv[2];
     bool step_open = false;
@@ -1221,6 +1236,203 @@ dmg_status slot_read_impl(dmg_ctx *c, int slot, double *u, double *x, double *Db
     return DMG_OK;
 }
 
+// --- unrolled coefficient gradient -------------------------------------------------
+// The exact derivative of <w, S_m(q; D, mu)> for m FP64 V-cycles from u = 0,
+// through every iterate and through the coarsened coefficients of every level.
+// The forward cycles run with the grid kernels only (full defect, no
+// single-CTA tail), so that every state the reverse pass needs can be saved.
+// Iterates are recomputed from level-0 checkpoints taken every `stride` cycles:
+// cycle c is rebuilt from the checkpoint at or before it and run once more
+// saving its states, then reversed.
+
+int n_states(const dmg_ctx *c) { return 2 * (c->p.nu1 + c->p.nu2) + 1; }
+
+dmg_status unrolled_alloc(dmg_ctx *c, int nck) {
+    if (!c->un_ready) {
+        for (int l = 0; l < c->nlev; l++) {
+            ULevel &W = c->un[l];
+            const size_t n = c->L[l].n;
+            for (double **q : {&W.ub, &W.fb, &W.bx, &W.by, &W.bz, &W.mub, &W.Db, &W.tmp}) {
+                TRY(dalloc(c, q, n));
+                CUDA_TRY(c, cudaMemset(*q, 0, n * sizeof(double)));
+            }
+            const int ns = l == c->nlev - 1 ? 1 : n_states(c);
+            W.st.assign(ns, nullptr);
+            for (double *&q : W.st) {
+                TRY(dalloc(c, &q, n));
+                CUDA_TRY(c, cudaMemset(q, 0, n * sizeof(double)));
+            }
+        }
+        c->un_ready = true;
+    }
+    while ((int)c->ck.size() < nck) {
+        double *q = nullptr;
+        TRY(dalloc(c, &q, c->L[0].n));
+        c->ck.push_back(q);
+    }
+    return DMG_OK;
+}
+
+dmg_status copy_level(dmg_ctx *c, double *dst, const double *src, int l, cudaStream_t s) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, c->L[l].n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return DMG_OK;
+}
+
+dmg_status half64(dmg_ctx *c, int l, int color, cudaStream_t s) {
+    Level &L = c->L[l];
+    dmgk::k_smooth_half<double><<<grid_half(L.g), blk(), 0, s>>>(L.g, L.u, L.f, coef64(L), color, nullptr);
+    return check_launch(c, "smooth");
+}
+
+// one forward V-cycle at level l on (u_l, f_l); save: keep the state after
+// every half-sweep in un[l].st (and the coarsest solution in st[0])
+dmg_status fwd_plain(dmg_ctx *c, int l, bool save, cudaStream_t s) {
+    Level &L = c->L[l];
+    ULevel &W = c->un[l];
+    if (l == c->nlev - 1) {
+        TRY(coarse_solve<double>(c, s));
+        if (save) TRY(copy_level(c, W.st[0], L.u, l, s));
+        return DMG_OK;
+    }
+    const int nu1 = c->p.nu1, nu2 = c->p.nu2, pf = c->p.symmetric ? 1 : 0;
+    int h = 0;
+    if (save && nu1 == 0) TRY(copy_level(c, W.st[n_states(c) - 1], L.u, l, s));
+    for (int sw = 0; sw < nu1; sw++)
+        for (int col = 0; col < 2; col++) {
+            TRY(half64(c, l, col, s));
+            if (save) TRY(copy_level(c, W.st[h], L.u, l, s));
+            h++;
+        }
+    Level &C = c->L[l + 1];
+    dmgk::k_residual<double><<<grid_int(L.g), blk(), 0, s>>>(L.g, L.u, L.f, coef64(L), L.r, nullptr);
+    TRY(check_launch(c, "residual"));
+    dmgk::k_restrict<double><<<grid_int(C.g), blk(), 0, s>>>(L.g, L.r, C.g, C.f, C.u, nullptr);
+    TRY(check_launch(c, "restrict"));
+    TRY(fwd_plain(c, l + 1, save, s));
+    TRY(prolong<double>(c, l, s));
+    for (int sw = 0; sw < nu2; sw++)
+        for (int q = 0; q < 2; q++) {
+            TRY(half64(c, l, q == 0 ? pf : 1 - pf, s));
+            if (save) TRY(copy_level(c, W.st[h], L.u, l, s));
+            h++;
+        }
+    return DMG_OK;
+}
+
+dmg_status rev_half(dmg_ctx *c, int l, int color, const double *U, cudaStream_t s) {
+    Level &L = c->L[l];
+    ULevel &W = c->un[l];
+    dmgk::k_rev_other<<<grid_half(L.g), blk(), 0, s>>>(L.g, coef64(L), color, W.ub);
+    TRY(check_launch(c, "rev_other"));
+    dmgk::k_rev_own<<<grid_half(L.g), blk(), 0, s>>>(L.g, coef64(L), color, U, W.ub, W.fb, W.bx, W.by, W.bz,
+                                                     W.mub);
+    return check_launch(c, "rev_own");
+}
+
+// reverse of the V-cycle saved by fwd_plain(l, true): on entry un[l].ub is the
+// cotangent of u_l after the cycle; on return it is the cotangent of u_l before
+// it, un[l].fb has gained the cotangent of f_l, and the coefficient cotangents
+// of levels l.. have gained the cycle's terms
+dmg_status rev_plain(dmg_ctx *c, int l, cudaStream_t s) {
+    Level &L = c->L[l];
+    ULevel &W = c->un[l];
+    if (l == c->nlev - 1) {
+        // fbar += A^{-1} ubar (the inverse is symmetric); coefficient terms with the solution
+        CUDA_TRY(c, cudaMemsetAsync(W.tmp, 0, L.n * sizeof(double), s));
+        const int threads = c->nc < 32 ? 32 : (c->nc > 512 ? 512 : ((c->nc + 31) / 32) * 32);
+        dmgk::k_coarse_solve<double><<<c->nb, threads, c->nc * sizeof(double), s>>>(L.g, c->Ainv, c->nc, W.ub,
+                                                                                   W.tmp, nullptr);
+        TRY(check_launch(c, "coarse_solve"));
+        dmgk::k_rev_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, W.tmp, W.st[0], W.bx, W.by, W.bz, W.mub);
+        TRY(check_launch(c, "rev_faces"));
+        dmgk::k_add_interior<<<grid_int(L.g), blk(), 0, s>>>(L.g, W.tmp, W.fb);
+        return check_launch(c, "add");
+    }
+    const int nu1 = c->p.nu1, nu2 = c->p.nu2, pf = c->p.symmetric ? 1 : 0;
+    int h = 2 * (nu1 + nu2) - 1;
+    for (int sw = nu2 - 1; sw >= 0; sw--)
+        for (int q = 1; q >= 0; q--) {
+            TRY(rev_half(c, l, q == 0 ? pf : 1 - pf, W.st[h], s));
+            h--;
+        }
+    Level &C = c->L[l + 1];
+    ULevel &WC = c->un[l + 1];
+    dmgk::k_prolong_T<<<grid_all(C.g), blk(), 0, s>>>(L.g, W.ub, C.g, WC.ub);
+    TRY(check_launch(c, "prolong_T"));
+    CUDA_TRY(c, cudaMemsetAsync(WC.fb, 0, C.n * sizeof(double), s));
+    TRY(rev_plain(c, l + 1, s));
+    // defect r = f - A u after pre-smoothing; its cotangent is R^T fbar_{l+1}
+    dmgk::k_restrict_T<<<grid_all(L.g), blk(), 0, s>>>(C.g, WC.fb, L.g, W.tmp);
+    TRY(check_launch(c, "restrict_T"));
+    dmgk::k_rev_defect<<<grid_int(L.g), blk(), 0, s>>>(L.g, coef64(L), W.tmp, W.ub, W.fb);
+    TRY(check_launch(c, "rev_defect"));
+    const double *Upre = nu1 > 0 ? W.st[2 * nu1 - 1] : W.st[n_states(c) - 1];
+    dmgk::k_rev_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, W.tmp, Upre, W.bx, W.by, W.bz, W.mub);
+    TRY(check_launch(c, "rev_faces"));
+    for (int sw = nu1 - 1; sw >= 0; sw--)
+        for (int col = 1; col >= 0; col--) {
+            TRY(rev_half(c, l, col, W.st[h], s));
+            h--;
+        }
+    return DMG_OK;
+}
+
+dmg_status vjp_unrolled_impl(dmg_ctx *c, const double *q, const double *w, int m, int stride, double *u,
+                             double *qbar, double *Dbar, double *mubar, cudaStream_t s) {
+    if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+    if (!q || !w) return fail(c, DMG_EINVAL, "q and w must not be NULL");
+    if (m < 1 || m > 100000) return fail(c, DMG_EINVAL, "m must be in [1, 100000]");
+    if (stride < 0) return fail(c, DMG_EINVAL, "stride must be >= 0");
+    if (stride == 0) stride = std::max(1, (int)std::ceil(std::sqrt((double)m)));
+    const int nck = (m + stride - 1) / stride;
+    TRY(unrolled_alloc(c, nck));
+    c->mask = nullptr;
+    Level &L0 = c->L[0];
+    ULevel &W0 = c->un[0];
+    TRY(stage_in(c, q, L0.f, false, s));
+    CUDA_TRY(c, cudaMemsetAsync(L0.u, 0, L0.n * sizeof(double), s));
+    for (int cyc = 0; cyc < m; cyc++) {
+        if (cyc % stride == 0) TRY(copy_level(c, c->ck[cyc / stride], L0.u, 0, s));
+        TRY(fwd_plain(c, 0, false, s));
+    }
+    if (u) TRY(stage_out(c, L0.u, u, s));
+    for (int l = 0; l < c->nlev; l++) {
+        ULevel &W = c->un[l];
+        for (double *x : {W.fb, W.bx, W.by, W.bz, W.mub})
+            CUDA_TRY(c, cudaMemsetAsync(x, 0, c->L[l].n * sizeof(double), s));
+    }
+    TRY(stage_in(c, w, W0.ub, true, s));
+    for (int cyc = m - 1; cyc >= 0; cyc--) {
+        const int base = (cyc / stride) * stride;
+        TRY(copy_level(c, L0.u, c->ck[cyc / stride], 0, s));
+        for (int r = base; r < cyc; r++) TRY(fwd_plain(c, 0, false, s));
+        TRY(fwd_plain(c, 0, true, s));
+        TRY(rev_plain(c, 0, s));
+    }
+    if (qbar) TRY(stage_out(c, W0.fb, qbar, s));
+    if (Dbar || mubar) {
+        const int harm = c->p.face_mean == DMG_FACE_HARMONIC;
+        for (int l = 0; l < c->nlev; l++) {
+            Level &L = c->L[l];
+            ULevel &W = c->un[l];
+            dmgk::k_faces_to_vertex<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, 1.0 / (L.h * L.h), harm, W.bx, W.by,
+                                                                    W.bz, W.Db);
+            TRY(check_launch(c, "faces_to_vertex"));
+        }
+        const int inj = c->p.coarsen == DMG_COARSEN_INJECTION;
+        for (int l = c->nlev - 2; l >= 0; l--) {
+            Level &L = c->L[l], &C = c->L[l + 1];
+            dmgk::k_coarsen_T<<<grid_all(L.g), blk(), 0, s>>>(C.g, c->un[l + 1].Db, L.g, c->un[l].Db, inj);
+            TRY(check_launch(c, "coarsen_T"));
+            dmgk::k_coarsen_T<<<grid_all(L.g), blk(), 0, s>>>(C.g, c->un[l + 1].mub, L.g, c->un[l].mub, inj);
+            TRY(check_launch(c, "coarsen_T"));
+        }
+        if (Dbar) TRY(stage_out(c, W0.Db, Dbar, s));
+        if (mubar) TRY(stage_out(c, W0.mub, mubar, s));
+    }
+    return end_call(c, s);
+}
+
 template <class F>
 dmg_status guarded(dmg_ctx *c, F fn) {
     if (!c) return DMG_EINVAL;
@@ -1516,6 +1728,11 @@ const char *dmg_strerror(dmg_status s) {
 const char *dmg_last_error(const dmg_ctx *c) {
     if (!c) return g_setup_err;
     return c->err;
+}
+
+dmg_status dmg_vjp_unrolled(dmg_ctx *c, const double *q, const double *w, int m, int stride, double *u,
+                            double *qbar, double *Dbar, double *mubar, void *stream) {
+    return guarded(c, [&]() { return vjp_unrolled_impl(c, q, w, m, stride, u, qbar, Dbar, mubar, S(stream)); });
 }
 
 dmg_status dmg_slot_load(dmg_ctx *c, int slot, const double *D, const double *mu, void *stream) {

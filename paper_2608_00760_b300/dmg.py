@@ -51,7 +51,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
-           "dmg_response_vjp")
+           "dmg_response_vjp", "dmg_vjp_unrolled")
 
 _lib = None
 
@@ -97,6 +97,7 @@ def lib():
             "dmg_slot_read": (i, [vp, i, vp, vp, vp, vp, vp]),
             "dmg_device_bytes": (ctypes.c_size_t, [vp]),
             "dmg_response": (i, [vp, vp, d, vp, vp, P(dmg_info), vp]),
+            "dmg_vjp_unrolled": (i, [vp, vp, vp, i, i, vp, vp, vp, vp, vp]),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
         }
@@ -205,6 +206,11 @@ def dmg_residual_static(params: dmg_params, D, mu, q, u, stream=None):
     st = lib().dmg_residual_static(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _ptr(q, n), _ptr(u, n), out,
                                    _stream(stream))
     return st, (out[0], out[1])
+
+
+def dmg_vjp_unrolled(ctx, q, w, m, stride, u, qbar, Dbar, mubar, stream=None, n=None):
+    return lib().dmg_vjp_unrolled(ctx, _ptr(q, n), _ptr(w, n), int(m), int(stride), _ptr(u, n), _ptr(qbar, n),
+                                  _ptr(Dbar, n), _ptr(mubar, n), _stream(stream))
 
 
 def dmg_response(ctx, q, edge, Le, u=None, info=None, stream=None, n=None):
@@ -371,6 +377,12 @@ class Solver:
                             stream, n=self.n))
         self.last_info = info
         return qb, Db, mb
+
+    def vjp_unrolled(self, q, w, m, stride=0, stream=None):
+        """(u, qbar, Dbar, mubar): u = S_m(q) and the exact gradient of <w, S_m(q; D, mu)>."""
+        u, qb, Db, mb = (self._empty(q) for _ in range(4))
+        self._check(dmg_vjp_unrolled(self.ctx, q, w, m, stride, u, qb, Db, mb, stream, n=self.n))
+        return u, qb, Db, mb
 
     def response(self, q, edge, stream=None):
         """(Le, u): Le = M(mu S(q)) with the edge mask of depth `edge` (see dmg_response)."""
