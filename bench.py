@@ -340,6 +340,43 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
     return out
 
 
+def run_unrolled(dmg, torch, args, world, local):
+    """The paper's fixed-count mode (15 FP64 V-cycles, Sec. 2.2 / 2.4) at n^3: the
+    forward S_15(q), the count-matched pull-back (dmg_vjp with cycles = 15, the
+    exact transpose in q) and the unrolled gradient w.r.t. q, D and mu through
+    every iterate and the coarsened coefficients (dmg_vjp_unrolled, iterates
+    recomputed from checkpoints)."""
+    from paper_2608_00760_b300 import inputs
+    n, m = args.unrolled_size, 15
+    dev = torch.device("cuda", local)
+    w = inputs.tissue_torch((n, n, n), 7, device=dev, keys=("D", "mu", "q", "w"))
+    S = dmg.Solver(w["D"], w["mu"], 0.5, fixed_cycles=m)
+    u = S.solve(w["q"])
+    S.vjp(u, w["w"], cycles=m, need=(True, True, True))
+    S.vjp_unrolled(w["q"], w["w"], m)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=3):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(world, e0.elapsed_time(e1) / reps)
+
+    t_f = timed(lambda: S.solve(w["q"]))
+    t_cm = timed(lambda: S.vjp(u, w["w"], cycles=m, need=(True, True, True)))
+    t_u = timed(lambda: S.vjp_unrolled(w["q"], w["w"], m))
+    S.close()
+    return dict(workload="tissue %d^3, %d fixed FP64 V(2,2) cycles" % (n, m), forward_ms=t_f,
+                count_matched_vjp_ms=t_cm, unrolled_vjp_ms=t_u, unrolled_over_forward=t_u / t_f,
+                note="unrolled: forward iterates recomputed from ceil(sqrt(m)) checkpoints, states of one cycle "
+                     "saved at a time; count-matched: transposed cycles plus the exact-solution coefficient "
+                     "gradient")
+
+
 SERVE_SHAPES = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
 
 
@@ -475,6 +512,8 @@ def main():
     ap.add_argument("--vi-batch", type=int, default=64, help="samples of the batched VI step (0: skip it)")
     ap.add_argument("--vi-size", type=int, default=129)
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream (0: skip it)")
+    ap.add_argument("--unrolled-size", type=int, default=257, help="grid of the unrolled-gradient timing (0: skip)")
+    ap.add_argument("--vi-only", action="store_true", help="run only the batched VI step and print its object")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     args = ap.parse_args()
@@ -488,6 +527,12 @@ def main():
     from paper_2608_00760_b300 import dmg
     dmg.lib()
     torch.cuda.set_device(local)
+    if args.vi_only:
+        peaks, peak_src = load_peaks()
+        vi = run_vi(dmg, torch, args, world, local, peaks, peak_src)
+        if rank == 0:
+            print(json.dumps(vi))
+        return
     w = make_inputs(args.size)
     npts = int(np.prod(w["shape"]))
     nint = int(np.prod([s - 2 for s in w["shape"]]))
@@ -580,6 +625,7 @@ def main():
         out["cpu_baseline"] = None
     out["vi_batch"] = run_vi(dmg, torch, args, world, local, peaks, peak_src) if args.vi_batch > 0 else None
     out["serving"] = (run_serving(dmg, torch, args, world, rank, local) if args.serve_requests > 0 else None)
+    out["unrolled"] = run_unrolled(dmg, torch, args, world, local) if args.unrolled_size > 0 else None
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -354,10 +354,22 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
         for (int h = 0; h < 2; h++) {
             ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
             int color = h == 0 ? first : 1 - first;
-            TRY(dispatch<T>(c, l, [&](auto cf) {
-                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color, c->mask);
-                return check_launch(c, "smooth");
-            }));
+            if constexpr (sizeof(T) == 4) {
+                TRY(with_coef32(c, l, [&](auto cf) {
+                    constexpr bool H = decltype(cf)::harmonic;
+                    if (c->nb == 1)
+                        dmgk::k_smooth_half32<H, false><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                          nullptr);
+                    else
+                        dmgk::k_smooth_half32<H, true><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                         c->mask);
+                    return check_launch(c, "smooth");
+                }));
+            } else {
+                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color,
+                                                                        c->mask);
+                TRY(check_launch(c, "smooth"));
+            }
         }
     }
     return DMG_OK;
@@ -373,11 +385,22 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
     ProfScope ps(c, DMG_KERNEL_RESTRICT, lev, sizeof(T) == 4, s);
     if (zero_colour >= 0) {
         const int nz = 1 - zero_colour;   // colour carrying the defect
-        TRY(dispatch<T>(c, l, [&](auto cf) {
-            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz,
+        if constexpr (sizeof(T) == 4) {
+            TRY(with_coef32(c, l, [&](auto cf) {
+                constexpr bool H = decltype(cf)::harmonic;
+                if (c->nb == 1)
+                    dmgk::k_residual_colour32<H, false><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf,
+                                                                                          l.r32, nz, nullptr);
+                else
+                    dmgk::k_residual_colour32<H, true><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf,
+                                                                                         l.r32, nz, c->mask);
+                return check_launch(c, "residual_colour");
+            }));
+        } else {
+            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), R<T>(l), nz,
                                                                         c->mask);
-            return check_launch(c, "residual_colour");
-        }));
+            TRY(check_launch(c, "residual_colour"));
+        }
         // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
         if (nz == 0)
             dmgk::k_restrict_colour<T, 0><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
@@ -810,6 +833,12 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (p->inner_cycles < 1 || p->inner_cycles > 16) return fail(c, DMG_EINVAL, "inner_cycles must be in [1, 16]");
     if (p->symmetric != 0 && p->symmetric != 1) return fail(c, DMG_EINVAL, "symmetric must be 0 or 1");
     if (p->batch < 1) return fail(c, DMG_EINVAL, "batch must be >= 1");
+    {
+        const Geom g0 = make_geom(p->nx, p->ny, p->nz, 1);
+        if (g0.sb > (long long)INT32_MAX)
+            return fail(c, DMG_EINVAL, "grid %dx%dx%d: a padded sample of %lld elements exceeds 2^31 - 1", p->nx,
+                        p->ny, p->nz, g0.sb);
+    }
     if ((long long)p->batch * p->nz > 65535)
         return fail(c, DMG_EINVAL, "batch * nz = %lld exceeds 65535", (long long)p->batch * p->nz);
     int nl = count_levels(p->nx, p->ny, p->nz);

@@ -119,6 +119,7 @@ struct FaceCoef {
 // Dh = D / h^2 for the harmonic mean (face = 2 Dh_p Dh_j / (Dh_p + Dh_j)).
 template <class T, bool HARM, bool RO = true>
 struct VertCoef {
+    static constexpr bool harmonic = HARM;
     const T *Dh, *mu;
     __device__ __forceinline__ static T face(T a, T b) {
         if (HARM) return T(2) * a * b / (a + b);
@@ -321,6 +322,95 @@ __global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__rest
     if (j > g.ny - 2 || i > g.nx - 2) return;
     const long long p = g.pos(i, j, k);
     r[p] = residual_at(u, f, c, p, neighbours(g, i));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 colour kernels on the grid levels, specialised for the vertex
+// coefficients: the same arithmetic as k_smooth_half / k_residual_colour with
+// VertCoef (bit for bit), but with 32-bit offsets inside a sample (a sample of
+// up to 2^31 padded elements) and, for single problems (BATCH = false), no
+// sample decoding. These are the bandwidth-bound kernels of the mixed-precision
+// cycle, where the instruction issue rate is the co-limit.
+
+// vertex of colour `color` handled by this thread: its in-sample position p and
+// the offset of its -x neighbour (the +x neighbour is at p + xm + 1)
+template <bool BATCH>
+__device__ __forceinline__ bool colour_vertex32(const Geom &g, int color, const int *act, long long &base, int &p,
+                                                int &xm) {
+    int k, smp = 0;
+    if (BATCH) {
+        smp = zsplit(g, kInterior, k);
+        if (inactive(act, smp)) return false;
+    } else {
+        k = blockIdx.z;
+    }
+    k += 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int par = (color + j + k) & 1;            // parity of i for this colour in row (j, k)
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > g.ny - 2 || 2 * t + 2 - par > g.nx - 2) return false;
+    base = BATCH ? (long long)smp * g.sb : 0;
+    p = k * (int)g.sz + j * g.sy + par * g.hx + (t + 1 - par);   // i = 2t + 2 - par
+    xm = par ? -g.hx : g.hx - 1;
+    return true;
+}
+
+template <bool HARM>
+__device__ __forceinline__ void couplings32(const float *Dh, int p, int xm, int sy, int sz, float a[6]) {
+    using C = VertCoef<float, HARM>;
+    const float d = __ldg(Dh + p);
+    a[0] = C::face(d, __ldg(Dh + p + xm));
+    a[1] = C::face(d, __ldg(Dh + p + xm + 1));
+    a[2] = C::face(d, __ldg(Dh + p - sy));
+    a[3] = C::face(d, __ldg(Dh + p + sy));
+    a[4] = C::face(d, __ldg(Dh + p - sz));
+    a[5] = C::face(d, __ldg(Dh + p + sz));
+}
+
+// s + sum_q a_q u_q in the pairing of coupled_sum<float>
+__device__ __forceinline__ float coupled_sum32(float s, const float *u, int p, int xm, int sy, int sz, const float *a) {
+    float s0 = fmaf(a[0], u[p + xm], s);
+    float s1 = a[2] * u[p - sy];
+    float s2 = a[4] * u[p - sz];
+    s0 = fmaf(a[1], u[p + xm + 1], s0);
+    s1 = fmaf(a[3], u[p + sy], s1);
+    s2 = fmaf(a[5], u[p + sz], s2);
+    return (s0 + s1) + s2;
+}
+
+template <bool HARM, bool BATCH>
+__global__ void __launch_bounds__(256) k_smooth_half32(Geom g, float *__restrict__ u, const float *__restrict__ f,
+                                                       VertCoef<float, HARM> c, int color, const int *act) {
+    long long base;
+    int p, xm;
+    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
+    u += base;
+    f += base;
+    const float *Dh = c.Dh + base, *mu = c.mu + base;
+    const int sy = g.sy, sz = (int)g.sz;
+    float a[6];
+    couplings32<HARM>(Dh, p, xm, sy, sz, a);
+    const float s = coupled_sum32(f[p], u, p, xm, sy, sz, a);
+    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
+    u[p] = __fdividef(s, dg);
+}
+
+template <bool HARM, bool BATCH>
+__global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *__restrict__ u,
+                                                           const float *__restrict__ f, VertCoef<float, HARM> c,
+                                                           float *__restrict__ r, int color, const int *act) {
+    long long base;
+    int p, xm;
+    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
+    u += base;
+    f += base;
+    r += base;
+    const float *Dh = c.Dh + base, *mu = c.mu + base;
+    const int sy = g.sy, sz = (int)g.sz;
+    float a[6];
+    couplings32<HARM>(Dh, p, xm, sy, sz, a);
+    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
+    r[p] = coupled_sum32(fmaf(-dg, u[p], f[p]), u, p, xm, sy, sz, a);
 }
 
 // Full weighting of a defect that vanishes on one colour: fine vertex
