@@ -53,7 +53,10 @@ HALF_SWEEP_BYTES_FP32 = 12.0
 HALF_SWEEP_FP64_OPS = 3.5
 # DRAM bytes (read + write) of one finest-level half-sweep launch at 257^3,
 # from an ncu capture of the current kernel (profiles/rbgs_half_sweep_257.md)
-HALF_SWEEP_TRAFFIC = {"fp32": 199764224, "fp64": 665421824}
+HALF_SWEEP_TRAFFIC = {"fp32": 200145920, "fp64": 664092672}
+# DRAM bytes per sample of one batched finest-level FP32 half-sweep at 129^3, from an ncu capture of 8 samples
+# (profiles/rbgs_half_sweep_257.md), scaled by the sample count
+VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = 25872500
 
 
 def percentile(x, p):
@@ -334,7 +337,8 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
         ach = byt / dur / 1e9
         pk = peaks.get("hbm_gbs", 6400.0)
         out["roofline"] = dict(kernel="rbgs_half_sweep_fp32_level0 (all samples)", bound="hbm", achieved=ach,
-                               peak=pk, unit="GB/s", frac=ach / pk, traffic=None,
+                               peak=pk, unit="GB/s", frac=ach / pk,
+                               traffic=VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 * B if n == 129 else None,
                                peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
                                algorithmic_bytes=byt)
     return out
@@ -561,12 +565,12 @@ def main():
             ach = byt / dur / 1e9
             pk = peaks.get("hbm_gbs", 6400.0)
             return dict(kernel="rbgs_half_sweep_fp32_level0", bound="hbm", achieved=ach, peak=pk, unit="GB/s",
-                        frac=ach / pk, traffic=HALF_SWEEP_TRAFFIC["fp32"], peak_source=peak_src + " hbm_gbs",
+                        frac=ach / pk, traffic=HALF_SWEEP_TRAFFIC["fp32"] if args.size == 257 else None, peak_source=peak_src + " hbm_gbs",
                         launches=pr["launches"], avg_us=dur * 1e6, algorithmic_bytes=byt)
         ops = HALF_SWEEP_FP64_OPS * nint
         ach = ops / dur / 1e12
         return dict(kernel="rbgs_half_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK / 1e12,
-                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=HALF_SWEEP_TRAFFIC["fp64"],
+                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=HALF_SWEEP_TRAFFIC["fp64"] if args.size == 257 else None,
                     peak_source="measured FP64 FMA rate (probe)", launches=pr["launches"], avg_us=dur * 1e6,
                     algorithmic_fp64_ops=ops)
 
