@@ -59,6 +59,9 @@ HALF_SWEEP_TRAFFIC = {"fp32": 200145920, "fp64": 664092672}
 VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = 25872500
 
 
+AUTOTUNE = [1]   # set from --autotune
+
+
 def percentile(x, p):
     return float(np.percentile(np.asarray(x), p)) if len(x) else None
 
@@ -179,7 +182,7 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     D, mu, q, wv = T(w["D"]), T(w["mu"]), T(w["q"]), T(w["w"])
-    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL, inner_cycles=inner)
+    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL, inner_cycles=inner, autotune=AUTOTUNE[0])
     u = torch.empty_like(q)
     qb, Db, mb = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
     info_f, info_a = dmg.dmg_info(), dmg.dmg_info()
@@ -518,6 +521,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream (0: skip it)")
     ap.add_argument("--unrolled-size", type=int, default=257, help="grid of the unrolled-gradient timing (0: skip)")
     ap.add_argument("--vi-only", action="store_true", help="run only the batched VI step and print its object")
+    ap.add_argument("--autotune", type=int, default=1, help="tile autotuner at setup (dmg_params.autotune)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     args = ap.parse_args()
@@ -525,6 +529,7 @@ def main():
         reference_arm(args, int(os.environ.get("RANK", "0")))
         return
     args.warmup = max(args.warmup, 3)
+    AUTOTUNE[0] = args.autotune
     world, rank, local = dist_setup()
 
     import torch
@@ -552,6 +557,8 @@ def main():
 
     head = results[precisions[0]]
     S = head["solver"]
+    tiles = {"fp32" if prec == "mixed" else "fp64": ["%dx%d" % t for t in results[prec]["solver"].tiles(prec == "mixed")]
+             for prec in precisions}
     ms = head["total_ms"] / args.steps
     value = job_throughput(world, args.steps, head["total_ms"])
 
@@ -590,7 +597,8 @@ def main():
                            parallelism="replicas" if world > 1 else "single-gpu",
                            inner_cycles=args.inner if precisions[0] == "mixed" else None,
                            l2="inputs larger than L2 (each FP64 field %.0f MB > 126 MB); no flush" % (8 * npts / 1e6),
-                           setup="dmg_setup once per coefficient field, outside the timed region"),
+                           setup="dmg_setup once per coefficient field, outside the timed region",
+                           autotune=args.autotune, tiles_per_level=tiles),
                p50_ms=percentile(head["per_ms"], 50), p99_ms=percentile(head["per_ms"], 99),
                hbm_gbs_algorithmic=gbs(head, precisions[0]),
                cycles=dict(fwd=head["fwd_cycles"], adj=head["adj_cycles"], fwd_outer=head["fwd_outer"],

@@ -96,6 +96,13 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 each step then gains ~3 decades, far above the FP32 floor).
  *   batch         independent problems in the context (default 1); needs
  *                 batch * nz <= 65535.
+ *   autotune      0 (default): colour kernels use 32 x 8 thread blocks; 1: dmg_setup
+ *                 times the candidate block shapes of the half-sweep on every
+ *                 grid level (FP64, and FP32 in mixed mode) and keeps the
+ *                 fastest (one at least 3% faster than 32 x 8). Results are
+ *                 reused within the process for the same device, precision,
+ *                 grid, batch and face mean, and, if the environment variable
+ *                 DMG_TUNE_CACHE names a file, read from and appended to it.
  */
 typedef struct {
     int nx, ny, nz;
@@ -110,6 +117,7 @@ typedef struct {
     int coarsen;
     int inner_cycles;
     int batch;
+    int autotune;
 } dmg_params;
 
 #define DMG_HIST_LEN 64
@@ -351,6 +359,10 @@ const char *dmg_last_error(const dmg_ctx *ctx);
 /* Number of hierarchy levels and the vertex counts of level l (0 = finest). */
 int dmg_levels(const dmg_ctx *ctx);
 dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int *nz);
+
+/* Thread-block shape (threads along the half-row, rows) of the colour kernels
+   on a level, FP32 (fp32 != 0) or FP64: 32 x 8 unless autotuned. */
+dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 
 /*
  * Instrumentation (for benchmarks).

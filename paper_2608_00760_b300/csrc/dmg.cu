@@ -9,6 +9,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -93,6 +97,9 @@ struct Slot {
 struct dmg_ctx {
     dmg_params p;
     int nb = 1;                       // samples in the batch
+    // thread-block shape of the colour kernels (half-sweep, colour defect) per
+    // level: [0] FP64, [1] FP32; 32 x 8 unless the autotuner chose another
+    dim3 tb[2][kMaxLevels];
     int nlev = 0;
     Level L[kMaxLevels];
     int nc = 0;                       // coarsest interior unknowns
@@ -184,6 +191,10 @@ inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (
 // half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
 inline dim3 grid_half(const Geom &g) {
     return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
+}
+// the same with a tuned block shape b (b.x threads along the half-row, b.y rows)
+inline dim3 grid_half(const Geom &g, dim3 b) {
+    return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
 }
 
 dmg_status check_launch(dmg_ctx *c, const char *what) {
@@ -357,17 +368,19 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
             if constexpr (sizeof(T) == 4) {
                 TRY(with_coef32(c, l, [&](auto cf) {
                     constexpr bool H = decltype(cf)::harmonic;
+                    const dim3 b = c->tb[1][lev];
                     if (c->nb == 1)
-                        dmgk::k_smooth_half32<H, false><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                          nullptr);
+                        dmgk::k_smooth_half32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                         nullptr);
                     else
-                        dmgk::k_smooth_half32<H, true><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                         c->mask);
+                        dmgk::k_smooth_half32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                        c->mask);
                     return check_launch(c, "smooth");
                 }));
             } else {
-                dmgk::k_smooth_half<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color,
-                                                                        c->mask);
+                const dim3 b = c->tb[0][lev];
+                dmgk::k_smooth_half<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color,
+                                                                       c->mask);
                 TRY(check_launch(c, "smooth"));
             }
         }
@@ -388,17 +401,19 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
         if constexpr (sizeof(T) == 4) {
             TRY(with_coef32(c, l, [&](auto cf) {
                 constexpr bool H = decltype(cf)::harmonic;
+                const dim3 b = c->tb[1][lev];
                 if (c->nb == 1)
-                    dmgk::k_residual_colour32<H, false><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf,
-                                                                                          l.r32, nz, nullptr);
+                    dmgk::k_residual_colour32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
+                                                                                         l.r32, nz, nullptr);
                 else
-                    dmgk::k_residual_colour32<H, true><<<grid_half(l.g), blk(), 0, s>>>(l.g, l.u32, l.f32, cf,
-                                                                                         l.r32, nz, c->mask);
+                    dmgk::k_residual_colour32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
+                                                                                        l.r32, nz, c->mask);
                 return check_launch(c, "residual_colour");
             }));
         } else {
-            dmgk::k_residual_colour<T><<<grid_half(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), R<T>(l), nz,
-                                                                        c->mask);
+            const dim3 b = c->tb[0][lev];
+            dmgk::k_residual_colour<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), R<T>(l), nz,
+                                                                       c->mask);
             TRY(check_launch(c, "residual_colour"));
         }
         // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
@@ -833,6 +848,7 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (p->inner_cycles < 1 || p->inner_cycles > 16) return fail(c, DMG_EINVAL, "inner_cycles must be in [1, 16]");
     if (p->symmetric != 0 && p->symmetric != 1) return fail(c, DMG_EINVAL, "symmetric must be 0 or 1");
     if (p->batch < 1) return fail(c, DMG_EINVAL, "batch must be >= 1");
+    if (p->autotune != 0 && p->autotune != 1) return fail(c, DMG_EINVAL, "autotune must be 0 or 1");
     {
         const Geom g0 = make_geom(p->nx, p->ny, p->nz, 1);
         if (g0.sb > (long long)INT32_MAX)
@@ -850,6 +866,129 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
         return fail(c, DMG_EINVAL,
                     "grid %dx%dx%d coarsens to %dx%dx%d with %lld unknowns (> %d): use c*2^n+1 vertices with small c",
                     p->nx, p->ny, p->nz, cx, cy, cz, nc, kMaxCoarse);
+    return DMG_OK;
+}
+
+// --- tile autotuner ----------------------------------------------------------------
+// Chooses, per level and precision, the thread-block shape of the colour kernels
+// (the half-sweep, whose shape the colour defect shares) by timing half-sweeps
+// on the level's own arrays during setup. Results are kept for the process
+// (keyed by device, precision, grid, batch and face mean) and, when the
+// environment variable DMG_TUNE_CACHE names a file, read from and appended to
+// it. A candidate replaces the default 32 x 8 only when it is at least 3% faster.
+
+const dim3 kTiles[] = {dim3(32, 8), dim3(32, 4), dim3(32, 2), dim3(64, 4), dim3(64, 2),
+                       dim3(128, 2), dim3(128, 1), dim3(16, 16), dim3(16, 8)};
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(int prec, const Geom &g, int harm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        prop.name[0] = 0;
+    }
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s:%s:%dx%dx%d:b%d:h%d", name.c_str(), prec ? "f32" : "f64", g.nx, g.ny, g.nz, g.nb,
+             harm);
+    return buf;
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("DMG_TUNE_CACHE");
+    if (!path) return;
+    FILE *fh = fopen(path, "r");
+    if (!fh) return;
+    char key[256];
+    int bx, by;
+    while (fscanf(fh, "%255s %d %d", key, &bx, &by) == 3)
+        if (bx > 0 && by > 0 && bx * by <= 256) g_tune[key] = {bx, by};
+    fclose(fh);
+}
+
+void tune_store_locked(const std::string &key, dim3 b) {
+    g_tune[key] = {(int)b.x, (int)b.y};
+    const char *path = getenv("DMG_TUNE_CACHE");
+    if (!path) return;
+    FILE *fh = fopen(path, "a");
+    if (!fh) return;
+    fprintf(fh, "%s %u %u\n", key.c_str(), b.x, b.y);
+    fclose(fh);
+}
+
+// one half-sweep of level l with block shape b (precision 1: FP32 vertex kernel)
+dmg_status tune_launch(dmg_ctx *c, int l, int prec, dim3 b, int color, cudaStream_t s) {
+    Level &L = c->L[l];
+    if (prec == 1) {
+        return with_coef32(c, L, [&](auto cf) {
+            constexpr bool H = decltype(cf)::harmonic;
+            if (c->nb == 1)
+                dmgk::k_smooth_half32<H, false><<<grid_half(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
+            else
+                dmgk::k_smooth_half32<H, true><<<grid_half(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
+            return check_launch(c, "tune");
+        });
+    }
+    dmgk::k_smooth_half<double><<<grid_half(L.g, b), b, 0, s>>>(L.g, L.u, L.f, coef64(L), color, nullptr);
+    return check_launch(c, "tune");
+}
+
+dmg_status tune_level(dmg_ctx *c, int l, int prec, cudaStream_t s) {
+    const std::string key = tune_key(prec, c->L[l].g, c->p.face_mean);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            c->tb[prec][l] = dim3(it->second.first, it->second.second);
+            return DMG_OK;
+        }
+    }
+    // the arrays hold zeros at setup: half-sweeps leave them zero
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    dim3 best = kTiles[0];
+    float best_ms = 0.f;
+    dmg_status st = DMG_OK;
+    for (size_t q = 0; q < sizeof(kTiles) / sizeof(kTiles[0]) && st == DMG_OK; q++) {
+        const dim3 b = kTiles[q];
+        for (int w = 0; w < 2 && st == DMG_OK; w++) st = tune_launch(c, l, prec, b, w, s);
+        if (st != DMG_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 8 && st == DMG_OK; r++) st = tune_launch(c, l, prec, b, r & 1, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(c, DMG_ECUDA, "autotuner timing failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (q == 0) best_ms = ms;
+        else if (ms < 0.97f * best_ms) { best = b; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != DMG_OK) return st;
+    c->tb[prec][l] = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store_locked(key, best);
+    return DMG_OK;
+}
+
+dmg_status autotune(dmg_ctx *c, cudaStream_t s) {
+    for (int l = 0; l < c->tail_first[0] && l < c->nlev - 1; l++) TRY(tune_level(c, l, 0, s));
+    if (c->p.precision == DMG_MIXED)
+        for (int l = 0; l < c->tail_first[1] && l < c->nlev - 1; l++) TRY(tune_level(c, l, 1, s));
     return DMG_OK;
 }
 
@@ -919,6 +1058,8 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     c->p = *p;
     c->nb = p->batch;
     const int nb = c->nb;
+    for (auto &row : c->tb)
+        for (dim3 &b : row) b = dim3(32, 8, 1);
     c->nlev = count_levels(p->nx, p->ny, p->nz);
     bool mixed = p->precision == DMG_MIXED;
     for (int l = 0; l < c->nlev; l++) {
@@ -1025,6 +1166,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     }
     TRY(build_coefficients(c, -1, D, mu, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (p->autotune) TRY(autotune(c, s));
     for (int b = 0; b < nb; b++)
         if (c->hstatus[b] != 0) {
             if (nb == 1)
@@ -1806,6 +1948,14 @@ dmg_status dmg_batch_info(const dmg_ctx *c, int *cycles, double *rel) {
 }
 
 int dmg_levels(const dmg_ctx *c) { return c ? c->nlev : 0; }
+
+dmg_status dmg_tile(const dmg_ctx *c, int level, int fp32, int *bx, int *by) {
+    if (!c || level < 0 || level >= c->nlev) return DMG_EINVAL;
+    const dim3 b = c->tb[fp32 ? 1 : 0][level];
+    if (bx) *bx = (int)b.x;
+    if (by) *by = (int)b.y;
+    return DMG_OK;
+}
 
 dmg_status dmg_level_shape(const dmg_ctx *c, int level, int *nx, int *ny, int *nz) {
     if (!c || level < 0 || level >= c->nlev) return DMG_EINVAL;

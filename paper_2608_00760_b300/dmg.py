@@ -34,7 +34,8 @@ class dmg_params(ctypes.Structure):
                 ("h", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("fixed_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("face_mean", ctypes.c_int),
-                ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("batch", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class dmg_info(ctypes.Structure):
@@ -51,7 +52,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
-           "dmg_response_vjp", "dmg_vjp_unrolled")
+           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile")
 
 _lib = None
 
@@ -98,6 +99,7 @@ def lib():
             "dmg_device_bytes": (ctypes.c_size_t, [vp]),
             "dmg_response": (i, [vp, vp, d, vp, vp, P(dmg_info), vp]),
             "dmg_vjp_unrolled": (i, [vp, vp, vp, i, i, vp, vp, vp, vp, vp]),
+            "dmg_tile": (i, [vp, i, i, P(i), P(i)]),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
         }
@@ -287,6 +289,12 @@ def dmg_level_shape(ctx, level):
     return st, (c.value, b.value, a.value)
 
 
+def dmg_tile(ctx, level, fp32=False):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    st = lib().dmg_tile(ctx, int(level), int(bool(fp32)), ctypes.byref(a), ctypes.byref(b))
+    return st, (a.value, b.value)
+
+
 def dmg_launch_count(ctx):
     return lib().dmg_launch_count(ctx)
 
@@ -352,6 +360,10 @@ class Solver:
 
     def levels(self):
         return [dmg_level_shape(self.ctx, l)[1] for l in range(dmg_levels(self.ctx))]
+
+    def tiles(self, fp32=False):
+        """Block shape (threads along the half-row, rows) of the colour kernels per level."""
+        return [dmg_tile(self.ctx, l, fp32)[1] for l in range(dmg_levels(self.ctx))]
 
     def solve(self, q, out=None, stream=None):
         u = out if out is not None else self._empty(q)
