@@ -58,7 +58,11 @@ def _axis_factor(n: int, h: float, corr: float) -> np.ndarray:
 
 
 def grf(shape, h: float, corr: float, std: float, rng: np.random.Generator) -> np.ndarray:
-    """Zero-mean SE-covariance Gaussian random field on a (nz, ny, nx) vertex grid."""
+    """Zero-mean SE-covariance Gaussian random field on a (nz, ny, nx) or (ny, nx) vertex grid."""
+    if len(shape) == 2:
+        Ly, Lx = (_axis_factor(n, h, corr) for n in shape)
+        xi = rng.standard_normal((Ly.shape[1], Lx.shape[1]))
+        return np.ascontiguousarray(std * (Ly @ xi @ Lx.T))
     nz, ny, nx = shape
     Lz, Ly, Lx = (_axis_factor(n, h, corr) for n in (nz, ny, nx))
     xi = rng.standard_normal((Lz.shape[1], Ly.shape[1], Lx.shape[1]))
@@ -168,6 +172,29 @@ def tissue_torch(shape, seed: int, h: float = 0.5, device="cuda", keys=("D", "mu
     if "dmu" in keys:
         out["dmu"] = 0.1 * out["mu"] * torch.randn(shape, generator=g, **f64)
     return {k: out[k] for k in keys}
+
+
+def tissue2d(n: int = 257, seed: int = 0, shape=None, h: float = 0.5) -> dict:
+    """The tissue recipe on a (ny, nx) grid for the 2D solver: the same GRF
+    coefficients (Eq. 19), a 2D Gaussian-blob source, cotangent and tangents."""
+    shape = tuple(shape) if shape is not None else (n, n)
+    r = _rngs(seed)
+    mus = 1.0 * np.exp(grf(shape, h, 5.0, 0.3, r["g1"]))
+    mua = 0.01 * np.exp(grf(shape, h, 5.0, 0.3, r["g2"]))
+    D = 1.0 / (3.0 * (mua + mus))
+    sig = 3.0
+    ext = [(s - 1) * h for s in shape]
+    lo = [min(3 * sig, e / 2) for e in ext]
+    c = [r["q"].uniform(l, e - l) for l, e in zip(lo, ext)]   # (y, x) centre
+    y, x = (np.arange(s) * h for s in shape)
+    q = np.exp(-((y - c[0]) ** 2) / (2 * sig * sig))[:, None] * np.exp(-((x - c[1]) ** 2) / (2 * sig * sig))[None, :]
+    inner = np.zeros(shape, dtype=bool)
+    inner[1:-1, 1:-1] = True
+    sel = (r["w_mask"].random(shape) < 0.10) & inner
+    w = np.where(sel, r["w"].standard_normal(shape), 0.0)
+    return dict(name="tissue2d", shape=shape, h=h, D=np.ascontiguousarray(D), mu=np.ascontiguousarray(mua),
+                q=np.ascontiguousarray(q), w=w, dq=r["dq"].standard_normal(shape),
+                dD=0.1 * D * r["dD"].standard_normal(shape), dmu=0.1 * mua * r["dmu"].standard_normal(shape))
 
 
 def vi_batch(n: int = 129, batch: int = 64, seed: int = 0, shape=None, h: float = 0.5,
