@@ -384,6 +384,60 @@ def run_unrolled(dmg, torch, args, world, local):
                      "gradient")
 
 
+def run_2d(dmg, torch, args, world, local, peaks, peak_src):
+    """The 2D solver (the paper's 2D benchmarks): fwd+VJP pairs at n^2, mixed and FP64."""
+    from paper_2608_00760_b300 import inputs
+    n = args.size_2d
+    dev = torch.device("cuda", local)
+    w = inputs.tissue2d_torch((n, n), 11, device=dev)
+    out = dict(workload="tissue-like %d^2 (2D, 5-point), fwd+VJP(q,D,mu), rtol 1e-10" % n)
+    for prec in ("mixed", "fp64"):
+        S = dmg.Solver(w["D"], w["mu"], w["h"], dim=2, rtol=RTOL, inner_cycles=args.inner,
+                       precision=dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64)
+        u = torch.empty_like(w["q"])
+        qb, Db, mb = torch.empty_like(u), torch.empty_like(u), torch.empty_like(u)
+        stream = torch.cuda.current_stream(dev)
+
+        def step():
+            assert dmg.dmg_solve(S.ctx, w["q"], u, None, stream, n=S.n) == dmg.DMG_OK
+            assert dmg.dmg_vjp(S.ctx, u, w["w"], 0, qb, Db, mb, None, stream, n=S.n) == dmg.DMG_OK
+
+        for _ in range(3):
+            step()
+        dmg.dmg_profile_begin(S.ctx, dmg.DMG_KERNEL_SMOOTH, 0, prec == "mixed", max_launches=4096)
+        steps = max(3, args.steps // 2)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for k in range(steps):
+            step()
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        _, nl, pms = dmg.dmg_profile_end(S.ctx)
+        S.close()
+        total = max_over_ranks(world, ev[0].elapsed_time(ev[steps]))
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        r = dict(value=world * steps / (total / 1e3), unit="fwd+VJP pairs/s", ms_per_step=total / steps,
+                 p50_ms=percentile(per, 50), p99_ms=percentile(per, 99))
+        if nl:
+            dur = pms / nl / 1e3
+            if prec == "mixed":
+                byt = HALF_SWEEP_BYTES_FP32 * (n - 2) ** 2
+                r["roofline"] = dict(kernel="rbgs_half_sweep_2d_fp32_level0", bound="hbm", achieved=byt / dur / 1e9,
+                                     peak=peaks.get("hbm_gbs", 6400.0), unit="GB/s",
+                                     frac=byt / dur / 1e9 / peaks.get("hbm_gbs", 6400.0), traffic=None,
+                                     peak_source=peak_src + " hbm_gbs", avg_us=dur * 1e6)
+            else:
+                ops = 2.5 * (n - 2) ** 2   # 4 FMA + 1 MUL per updated vertex
+                r["roofline"] = dict(kernel="rbgs_half_sweep_2d_fp64_level0", bound="alu",
+                                     achieved=ops / dur / 1e12, peak=FP64_OPS_PEAK / 1e12, unit="TFP64-op/s",
+                                     frac=ops / dur / FP64_OPS_PEAK, traffic=None, avg_us=dur * 1e6)
+        out[prec] = r
+    return out
+
+
 SERVE_SHAPES = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
 
 
@@ -521,6 +575,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream (0: skip it)")
     ap.add_argument("--unrolled-size", type=int, default=257, help="grid of the unrolled-gradient timing (0: skip)")
     ap.add_argument("--vi-only", action="store_true", help="run only the batched VI step and print its object")
+    ap.add_argument("--size-2d", type=int, default=4097, help="grid of the 2D solver timing (0: skip)")
     ap.add_argument("--autotune", type=int, default=1, help="tile autotuner at setup (dmg_params.autotune)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
@@ -638,6 +693,7 @@ def main():
     out["vi_batch"] = run_vi(dmg, torch, args, world, local, peaks, peak_src) if args.vi_batch > 0 else None
     out["serving"] = (run_serving(dmg, torch, args, world, rank, local) if args.serve_requests > 0 else None)
     out["unrolled"] = run_unrolled(dmg, torch, args, world, local) if args.unrolled_size > 0 else None
+    out["two_d"] = run_2d(dmg, torch, args, world, local, peaks, peak_src) if args.size_2d > 0 else None
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -22,6 +22,7 @@
 #include "../../include/dmg.h"
 #include "kernels.cuh"
 #include "unrolled.cuh"
+#include "kernels2d.cuh"
 
 using dmgk::Geom;
 
@@ -96,6 +97,7 @@ struct Slot {
 
 struct dmg_ctx {
     dmg_params p;
+    int dim = 3;                      // 3, or 2 for an (ny, nx) grid (nz == 1)
     int nb = 1;                       // samples in the batch
     // thread-block shape of the colour kernels (half-sweep, colour defect) per
     // level: [0] FP64, [1] FP32; 32 x 8 unless the autotuner chose another
@@ -192,6 +194,10 @@ inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (
 inline dim3 grid_half(const Geom &g) {
     return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
 }
+// 2D levels (nz == 1): blockIdx.z = sample
+inline dim3 grid_half2(const Geom &g) { return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nb); }
+inline dim3 grid_int2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nb); }
+inline dim3 grid_all2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb); }
 // the same with a tuned block shape b (b.x threads along the half-row, b.y rows)
 inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
@@ -365,6 +371,14 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
         for (int h = 0; h < 2; h++) {
             ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
             int color = h == 0 ? first : 1 - first;
+            if (c->dim == 2) {
+                TRY(dispatch<T>(c, l, [&](auto cf) {
+                    dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color,
+                                                                              c->mask);
+                    return check_launch(c, "smooth");
+                }));
+                continue;
+            }
             if constexpr (sizeof(T) == 4) {
                 TRY(with_coef32(c, l, [&](auto cf) {
                     constexpr bool H = decltype(cf)::harmonic;
@@ -396,6 +410,14 @@ template <class T>
 dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s) {
     Level &l = c->L[lev], &cl = c->L[lev + 1];
     ProfScope ps(c, DMG_KERNEL_RESTRICT, lev, sizeof(T) == 4, s);
+    if (c->dim == 2) {   // full defect and 9-point full weighting
+        TRY(dispatch<T>(c, l, [&](auto cf) {
+            dmgk::k_residual2<T><<<grid_int2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), c->mask);
+            return check_launch(c, "residual");
+        }));
+        dmgk::k_restrict2<T><<<grid_int2(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl), c->mask);
+        return check_launch(c, "restrict");
+    }
     if (zero_colour >= 0) {
         const int nz = 1 - zero_colour;   // colour carrying the defect
         if constexpr (sizeof(T) == 4) {
@@ -439,6 +461,11 @@ template <class T>
 dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
     Level &l = c->L[lev], &cl = c->L[lev + 1];
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
+    if (c->dim == 2) {
+        dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, c->nb);   // coarse cells
+        dmgk::k_prolong_add2<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
+        return check_launch(c, "prolong");
+    }
     dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, c->nb * (cl.g.nz - 1));   // coarse cells
     dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
     return check_launch(c, "prolong");
@@ -488,8 +515,12 @@ template <class T>
 dmg_status coarse_solve(dmg_ctx *c, cudaStream_t s) {
     Level &l = c->L[c->nlev - 1];
     int threads = c->nc < 32 ? 32 : (c->nc > 512 ? 512 : ((c->nc + 31) / 32) * 32);
-    dmgk::k_coarse_solve<T><<<c->nb, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l),
-                                                                       c->mask);
+    if (c->dim == 2)
+        dmgk::k_coarse_solve2<T><<<c->nb, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l),
+                                                                            c->mask);
+    else
+        dmgk::k_coarse_solve<T><<<c->nb, threads, c->nc * sizeof(T), s>>>(l.g, AINV<T>(c), c->nc, F<T>(l), U<T>(l),
+                                                                           c->mask);
     return check_launch(c, "coarse_solve");
 }
 
@@ -557,7 +588,10 @@ dmg_status finish_reduce(dmg_ctx *c, cudaStream_t s) {
 
 // ||x||_2^2 over interior of each sample of a level-0 FP64 array -> red[sample][slot]
 dmg_status norm2_async(dmg_ctx *c, const double *x, int slot, cudaStream_t s) {
-    dmgk::k_norm2<<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(c->L[0].g, x, c->partial);
+    if (c->dim == 2)
+        dmgk::k_norm2_2d<<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(c->L[0].g, x, c->partial);
+    else
+        dmgk::k_norm2<<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(c->L[0].g, x, c->partial);
     TRY(check_launch(c, "norm2"));
     dmgk::k_reduce_final<<<c->nb, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot, nullptr);
     return check_launch(c, "reduce");
@@ -570,8 +604,13 @@ dmg_status resid_norm_async(dmg_ctx *c, const double *u, const double *f, float 
     Level &l = c->L[0];
     {
         ProfScope ps(c, DMG_KERNEL_RESIDUAL, 0, 0, s);
-        dmgk::k_resid_norm<double><<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(l.g, u, f, coef64(l), (double *)nullptr,
-                                                                            r32, c->ms, c->partial, act);
+        if (c->dim == 2)
+            dmgk::k_resid_norm2<double><<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(l.g, u, f, coef64(l), r32, c->ms,
+                                                                                 c->partial, act);
+        else
+            dmgk::k_resid_norm<double><<<dim3(kNormBlocks, c->nb), 256, 0, s>>>(l.g, u, f, coef64(l),
+                                                                                (double *)nullptr, r32, c->ms,
+                                                                                c->partial, act);
         TRY(check_launch(c, "resid_norm"));
     }
     dmgk::k_reduce_final<<<c->nb, 256, 0, s>>>(c->partial, kNormBlocks, c->red, slot, act);
@@ -769,7 +808,10 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
     TRY(norm2_async(c, l.f, 0, s));
     dmgk::k_mix_init<<<(c->nb + 127) / 128, 128, 0, s>>>(c->red, 0, c->ms, c->nb);
     TRY(check_launch(c, "mix_init"));
-    dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
+    if (c->dim == 2)
+        dmgk::k_to_f32_2<<<grid_int2(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
+    else
+        dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
     TRY(check_launch(c, "to_f32"));
     TRY(finish_reduce(c, s));
     Progress P;
@@ -781,7 +823,10 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
         TRY(capture(c, G, [&](cudaStream_t cs) -> dmg_status {
             CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), cs));
             for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
-            dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+            if (c->dim == 2)
+                dmgk::k_update2<<<grid_int2(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+            else
+                dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
             TRY(check_launch(c, "update"));
             TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
             dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);
@@ -802,6 +847,16 @@ dmg_status iterate(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cudaS
 }
 
 int count_levels(int nx, int ny, int nz) {
+    if (nz == 1) {   // 2D: halve x and y while both have an odd count > 3
+        if (nx < 3 || ny < 3) return 0;
+        int n = 1;
+        while (nx > 3 && ny > 3 && (nx & 1) && (ny & 1)) {
+            nx = (nx - 1) / 2 + 1;
+            ny = (ny - 1) / 2 + 1;
+            if (++n > kMaxLevels) return 0;
+        }
+        return n;
+    }
     if (nx < 3 || ny < 3 || nz < 3) return 0;
     int n = 1;
     while (nx > 3 && ny > 3 && nz > 3 && (nx & 1) && (ny & 1) && (nz & 1)) {
@@ -822,16 +877,18 @@ Geom make_geom(int nx, int ny, int nz, int nb) {
     g.sb = g.sz * nz;
     g.nb = nb;
     for (int w = 0; w < 3; w++) {
-        const unsigned long long d = (unsigned long long)(nz - 2 + w);
-        g.mz[w] = d == 1 ? 0u : (unsigned)(((1ULL << 32) + d - 1) / d);
+        // a 2D grid (nz == 1) has no interior or cell planes: those entries are unused
+        const long long d = (long long)nz - 2 + w;
+        g.mz[w] = d <= 1 ? 0u : (unsigned)(((1ULL << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
     }
     return g;
 }
 
 dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (!p) return fail(c, DMG_EINVAL, "params is NULL");
-    if (p->nx < 3 || p->ny < 3 || p->nz < 3)
-        return fail(c, DMG_EINVAL, "grid %dx%dx%d: every axis needs >= 3 vertices", p->nx, p->ny, p->nz);
+    if (p->nx < 3 || p->ny < 3 || (p->nz < 3 && p->nz != 1))
+        return fail(c, DMG_EINVAL, "grid %dx%dx%d: every axis needs >= 3 vertices (nz = 1: a 2D grid)", p->nx,
+                    p->ny, p->nz);
     if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 1)
         return fail(c, DMG_EINVAL, "grid %dx%dx%d too large", p->nx, p->ny, p->nz);
     if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(c, DMG_EINVAL, "h must be > 0");
@@ -861,7 +918,7 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (nl == 0) return fail(c, DMG_EINVAL, "grid %dx%dx%d cannot be coarsened", p->nx, p->ny, p->nz);
     int cx = p->nx, cy = p->ny, cz = p->nz;
     for (int l = 1; l < nl; l++) { cx = (cx - 1) / 2 + 1; cy = (cy - 1) / 2 + 1; cz = (cz - 1) / 2 + 1; }
-    long long nc = (long long)(cx - 2) * (cy - 2) * (cz - 2);
+    long long nc = (long long)(cx - 2) * (cy - 2) * (p->nz == 1 ? 1 : cz - 2);
     if (nc > kMaxCoarse)
         return fail(c, DMG_EINVAL,
                     "grid %dx%dx%d coarsens to %dx%dx%d with %lld unknowns (> %d): use c*2^n+1 vertices with small c",
@@ -986,6 +1043,7 @@ dmg_status tune_level(dmg_ctx *c, int l, int prec, cudaStream_t s) {
 }
 
 dmg_status autotune(dmg_ctx *c, cudaStream_t s) {
+    if (c->dim == 2) return DMG_OK;   // the 2D kernels use the default shape
     for (int l = 0; l < c->tail_first[0] && l < c->nlev - 1; l++) TRY(tune_level(c, l, 0, s));
     if (c->p.precision == DMG_MIXED)
         for (int l = 0; l < c->tail_first[1] && l < c->nlev - 1; l++) TRY(tune_level(c, l, 1, s));
@@ -1020,6 +1078,13 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     TRY(stage_in(c, mu, V[0].mu, false, s, slot));
     for (int l = 1; l < c->nlev; l++) {
         Level &F = V[l - 1], &C = V[l];
+        if (c->dim == 2) {
+            dmgk::k_coarsen2<<<grid_all2(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
+            TRY(check_launch(c, "coarsen"));
+            dmgk::k_coarsen2<<<grid_all2(C.g), blk(), 0, s>>>(F.g, F.mu, C.g, C.mu, p->coarsen);
+            TRY(check_launch(c, "coarsen"));
+            continue;
+        }
         dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
         TRY(check_launch(c, "coarsen"));
         dmgk::k_coarsen<<<grid_all(C.g), blk(), 0, s>>>(F.g, F.mu, C.g, C.mu, p->coarsen);
@@ -1029,8 +1094,12 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     for (int l = 0; l < c->nlev; l++) {
         Level &L = V[l];
         const double ih2 = 1.0 / (L.h * L.h);
-        dmgk::k_build_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.cz,
-                                                            L.diag, L.invd);
+        if (c->dim == 2)
+            dmgk::k_build_faces2<<<grid_all2(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.diag,
+                                                                  L.invd);
+        else
+            dmgk::k_build_faces<<<grid_all(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.cz,
+                                                                L.diag, L.invd);
         TRY(check_launch(c, "build_faces"));
         if (mixed) {
             const double scale = harm ? ih2 : 0.5 * ih2;
@@ -1042,7 +1111,10 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     const size_t nc2 = (size_t)c->nc * c->nc;
     const int first = slot < 0 ? 0 : slot, count = slot < 0 ? c->nb : 1;
     CUDA_TRY(c, cudaMemsetAsync(c->gj_status + first, 0xff, count * sizeof(int), s));
-    dmgk::k_coarse_assemble<<<dim3(64, count), 256, 0, s>>>(LC.g, coef64(LC), c->nc, c->M + 2 * nc2 * first);
+    if (c->dim == 2)
+        dmgk::k_coarse_assemble2<<<dim3(64, count), 256, 0, s>>>(LC.g, coef64(LC), c->nc, c->M + 2 * nc2 * first);
+    else
+        dmgk::k_coarse_assemble<<<dim3(64, count), 256, 0, s>>>(LC.g, coef64(LC), c->nc, c->M + 2 * nc2 * first);
     TRY(check_launch(c, "coarse_assemble"));
     dmgk::k_gauss_jordan<<<count, 1024, 0, s>>>(c->M + 2 * nc2 * first, c->nc, c->Ainv + nc2 * first,
                                                 c->Ainv32 + nc2 * first, c->gj_status + first);
@@ -1061,6 +1133,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     for (auto &row : c->tb)
         for (dim3 &b : row) b = dim3(32, 8, 1);
     c->nlev = count_levels(p->nx, p->ny, p->nz);
+    c->dim = p->nz == 1 ? 2 : 3;
     bool mixed = p->precision == DMG_MIXED;
     for (int l = 0; l < c->nlev; l++) {
         Level &L = c->L[l];
@@ -1119,7 +1192,8 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     c->bcyc.assign(nb, 0);
     c->brel.assign(nb, 0.0);
     Level &LC0 = c->L[c->nlev - 1];
-    c->nc = (LC0.g.nx - 2) * (LC0.g.ny - 2) * (LC0.g.nz - 2);   // coarsest unknowns (the tail sizes its buffer by it)
+    // coarsest unknowns (the tail sizes its buffer by it)
+    c->nc = (LC0.g.nx - 2) * (LC0.g.ny - 2) * (c->dim == 2 ? 1 : LC0.g.nz - 2);
     // single-CTA tail: the small levels, as many as fit the shared-memory budget
     for (int t = 0; t < 2; t++) {
         const size_t esz = t ? sizeof(float) : sizeof(double);
@@ -1140,6 +1214,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
             first--;
         }
         if (bytes(first) > kTailSmemBudget) first = c->nlev;   // even the coarsest does not fit: no tail
+        if (c->dim == 2) first = c->nlev;   // the shared-memory tail is 3D only
         c->tail_first[t] = first;
         c->tail_smem[t] = first < c->nlev ? bytes(first) : 0;
     }
@@ -1195,6 +1270,7 @@ bool any_busy(const dmg_ctx *c) {
 }
 
 dmg_status check_slot(dmg_ctx *c, int slot) {
+    if (c->dim == 2) return fail(c, DMG_EINVAL, "the slot interface is 3D only");
     if (slot < 0 || slot >= c->nb) return fail(c, DMG_EINVAL, "slot %d out of range [0, %d)", slot, c->nb);
     if (c->p.fixed_cycles != 0) return fail(c, DMG_EINVAL, "the slot interface needs fixed_cycles == 0");
     return DMG_OK;
@@ -1550,6 +1626,7 @@ dmg_status rev_plain(dmg_ctx *c, int l, cudaStream_t s) {
 
 dmg_status vjp_unrolled_impl(dmg_ctx *c, const double *q, const double *w, int m, int stride, double *u,
                              double *qbar, double *Dbar, double *mubar, cudaStream_t s) {
+    if (c->dim == 2) return fail(c, DMG_EINVAL, "dmg_vjp_unrolled is 3D only");
     if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
     if (!q || !w) return fail(c, DMG_EINVAL, "q and w must not be NULL");
     if (m < 1 || m > 100000) return fail(c, DMG_EINVAL, "m must be in [1, 100000]");
@@ -1689,8 +1766,12 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
             if (dD) TRY(stage_in(c, dD, c->T1, false, s));
             if (dmu) TRY(stage_in(c, dmu, c->T2, false, s));
             double ih2 = 1.0 / (l.h * l.h);
-            dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0, dD ? c->T1 : nullptr, dmu ? c->T2 : nullptr,
-                                                       l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
+            if (c->dim == 2)
+                dmgk::k_dA2<<<grid_int2(l.g), blk(), 0, s>>>(l.g, c->U0, dD ? c->T1 : nullptr, dmu ? c->T2 : nullptr,
+                                                             l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
+            else
+                dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0, dD ? c->T1 : nullptr, dmu ? c->T2 : nullptr,
+                                                           l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
             TRY(check_launch(c, "dA"));
         }
         dmg_status st = iterate(c, false, c->p.fixed_cycles, info, s);
@@ -1720,9 +1801,14 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
             double ih2 = 1.0 / (l.h * l.h);
             {
                 ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
-                dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
-                                                             c->p.face_mean == DMG_FACE_HARMONIC,
-                                                             Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+                if (c->dim == 2)
+                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                                   c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                   Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+                else
+                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                                 c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                 Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
                 TRY(check_launch(c, "grad"));
             }
             if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
@@ -1739,6 +1825,7 @@ namespace {
 
 // first kept index per axis: the smallest m with m h >= edge (1 - 1e-12)
 dmg_status margins(dmg_ctx *c, double edge, dmgk::Margins *m) {
+    if (c->dim == 2) return fail(c, DMG_EINVAL, "the response operator is 3D only");
     if (!(edge >= 0.0) || !std::isfinite(edge)) return fail(c, DMG_EINVAL, "edge must be finite and >= 0");
     const double h = c->p.h, e = edge * (1.0 - 1e-12);
     auto first = [&](int n) {

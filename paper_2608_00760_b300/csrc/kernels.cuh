@@ -659,8 +659,9 @@ __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict
     const unsigned r = t / g.nx;
     const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
     double v = src[t];
-    if (zero_boundary && (i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1))
-        v = 0.0;
+    if (zero_boundary &&
+        (i == 0 || j == 0 || i == g.nx - 1 || j == g.ny - 1 || (g.nz > 1 && (k == 0 || k == g.nz - 1))))
+        v = 0.0;   // (a 2D grid, nz == 1, has no z boundary)
     dst[g.pos(i, j, k)] = v;
 }
 

@@ -2,7 +2,8 @@
 
 Argument marshalling only: every array argument may be a torch tensor (CUDA or
 CPU), a numpy array, or None where the C API allows NULL; each must be a
-C-contiguous float64 array of nx*ny*nz elements in [nz][ny][nx] order. The
+C-contiguous float64 array of nx*ny*nz elements in [nz][ny][nx] order (nz = 1:
+a 2D grid [ny][nx]). The
 stream defaults to torch's current CUDA stream. Every computation runs in the
 library's CUDA kernels; when the library is missing the first call raises.
 A context set up with ``batch = B`` takes B such fields back to back,
@@ -318,16 +319,24 @@ class Solver:
     raise on DMG_ENOCONV too (default True).
     """
 
-    def __init__(self, D, mu, h, shape=None, stream=None, strict=True, **params):
+    def __init__(self, D, mu, h, shape=None, stream=None, strict=True, dim=3, **params):
         import torch
         self.torch = torch
         shape = tuple(shape if shape is not None else D.shape)
-        if len(shape) == 4:
+        if dim == 2:   # a 2D grid (ny, nx), or a batch (B, ny, nx): nz = 1
+            if len(shape) == 3:
+                self.batch, (ny, nx), nz = shape[0], shape[1:], 1
+            elif len(shape) == 2:
+                self.batch, (ny, nx), nz = 1, shape, 1
+            else:
+                raise ValueError("expected a shape (ny, nx) or (B, ny, nx), got %r" % (shape,))
+        elif len(shape) == 4:
             self.batch, (nz, ny, nx) = shape[0], shape[1:]
         elif len(shape) == 3:
             self.batch, (nz, ny, nx) = 1, shape
         else:
             raise ValueError("expected a shape (nz, ny, nx) or (B, nz, ny, nx), got %r" % (shape,))
+        self.dim = dim
         self.shape, self.n = shape, nx * ny * nz * self.batch
         self.params = dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.batch, **params)
         self.strict = strict
@@ -422,7 +431,7 @@ class Solver:
         """(||q - A u||, ||q||), or a list of such pairs for a batch."""
         st, r = dmg_residual(self.ctx, q, u, stream, n=self.n, batch=self.batch)
         self._check(st)
-        if len(self.shape) == 3:
+        if self.batch == 1 and len(self.shape) == self.dim:
             return r
         return [(r[2 * b], r[2 * b + 1]) for b in range(self.batch)]
 

@@ -197,6 +197,56 @@ def tissue2d(n: int = 257, seed: int = 0, shape=None, h: float = 0.5) -> dict:
                 dD=0.1 * D * r["dD"].standard_normal(shape), dmu=0.1 * mua * r["dmu"].standard_normal(shape))
 
 
+def _gauss_filter_torch(x, h, corr, axis):
+    """x convolved along one axis with the Gaussian of std corr / sqrt(2) (zero padding)."""
+    import torch
+    s = corr / np.sqrt(2.0) / h
+    r = int(np.ceil(4 * s))
+    t = torch.arange(-r, r + 1, dtype=x.dtype, device=x.device)
+    k = torch.exp(-0.5 * (t / s) ** 2)
+    y = x.movedim(axis, -1)
+    shp = y.shape
+    y = torch.nn.functional.conv1d(y.reshape(-1, 1, shp[-1]), k.view(1, 1, -1), padding=r)
+    return y.reshape(shp).movedim(-1, axis), float(torch.sqrt((k * k).sum()))
+
+
+def grf_filter_torch(shape, h, corr, std, gen, device):
+    """Zero-mean Gaussian random field with (approximately) SE covariance
+    std^2 exp(-r^2 / (2 corr^2)): white noise filtered by a Gaussian of std
+    corr / sqrt(2) along each axis and normalised to unit variance. Linear cost,
+    for grids whose 1-D covariance factors would be too costly to decompose."""
+    import torch
+    x = torch.randn(shape, generator=gen, dtype=torch.float32, device=device)
+    norm = 1.0
+    for ax in range(len(shape)):
+        x, nk = _gauss_filter_torch(x, h, corr, ax)
+        norm *= nk
+    return (std / norm) * x.double()
+
+
+def tissue2d_torch(shape, seed: int, h: float = 0.5, device="cuda"):
+    """The 2D tissue recipe on a CUDA device (filtered-noise GRFs): D, mu, q, w, dq, dD, dmu."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device)
+    mus = torch.exp(grf_filter_torch(shape, h, 5.0, 0.3, g, device))
+    mua = 0.01 * torch.exp(grf_filter_torch(shape, h, 5.0, 0.3, g, device))
+    D = 1.0 / (3.0 * (mua + mus))
+    sig = 3.0
+    ext = [(n - 1) * h for n in shape]
+    lo = [min(3 * sig, e / 2) for e in ext]
+    u = torch.rand(2, generator=g, **f64).tolist()
+    c = [l + (e - 2 * l) * r for l, e, r in zip(lo, ext, u)]
+    y, x = (torch.arange(n, **f64) * h for n in shape)
+    q = (torch.exp(-((y - c[0]) ** 2) / (2 * sig * sig))[:, None] * torch.exp(-((x - c[1]) ** 2) / (2 * sig * sig))[None, :])
+    inner = torch.zeros(shape, dtype=torch.bool, device=device)
+    inner[1:-1, 1:-1] = True
+    sel = (torch.rand(shape, generator=g, **f64) < 0.10) & inner
+    w = torch.where(sel, torch.randn(shape, generator=g, **f64), torch.zeros((), **f64))
+    return dict(D=D.contiguous(), mu=mua.contiguous(), q=q.contiguous(), w=w, h=h, shape=tuple(shape))
+
+
 def vi_batch(n: int = 129, batch: int = 64, seed: int = 0, shape=None, h: float = 0.5,
              keys=("D", "mu", "q", "w")) -> dict:
     """B tissue samples stacked along a leading axis: arrays of shape (B, nz, ny, nx)."""

@@ -73,3 +73,12 @@ def test_null_context_calls(dmg):
     assert dmg.dmg_solve(None, 0, 0) == dmg.DMG_EINVAL
     assert dmg.dmg_destroy(None) == dmg.DMG_OK
     assert dmg.dmg_levels(None) == 0
+
+
+def test_2d_parameter_validation():
+    from paper_2608_00760_b300 import dmg
+    # nz = 2 is neither 2D nor a valid 3D grid; a 2D grid whose coarsest level is too large is refused
+    for (nx, ny, nz), msg in (((17, 17, 2), "3 vertices"), ((33, 34, 1), "unknowns")):
+        p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=1.0)
+        st, ctx = dmg.dmg_setup(p, None, None)
+        assert st == dmg.DMG_EINVAL and ctx is None and msg in dmg.dmg_last_error(None)
