@@ -676,9 +676,9 @@ def main():
         r.pop("out", None)
 
     if not args.no_e2e:
+        ns = max(6, args.steps // 2)
         e = run_e2e(dmg, torch, w, dmg.DMG_MIXED if precisions[0] == "mixed" else dmg.DMG_FP64,
-                    max(2, args.steps // 4), 1, world, local, inner=args.inner)
-        ns = max(2, args.steps // 4)
+                    ns, 1, world, local, inner=args.inner)
         out["e2e"] = dict(value=world * ns / e["seconds"], unit=UNIT, h2d_bytes_per_step=e["h2d"],
                           d2h_bytes_per_step=e["d2h"], steps=ns, api="dmg_solve + dmg_vjp with pinned host buffers")
     else:

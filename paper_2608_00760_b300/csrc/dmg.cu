@@ -113,6 +113,9 @@ struct dmg_ctx {
     int *hstatus = nullptr;           // pinned host copy
     float *Ainv32 = nullptr;
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
+    double *stage2 = nullptr;         // a second one, for transfers on the side stream
+    cudaStream_t side = nullptr;      // overlaps host transfers with the iteration on the caller's stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
@@ -303,13 +306,14 @@ inline Geom geom0(const dmg_ctx *c, int slot) {
 
 // src (caller layout, every sample or one slot's sample) -> dst (split layout of
 // the same samples; dst already points at the slot's part)
-dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s, int slot = -1) {
+dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_boundary, cudaStream_t s, int slot = -1,
+                    double *buf = nullptr) {
     const Geom g = geom0(c, slot);
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     const size_t bytes = n * g.nb * sizeof(double);
     const double *from = src;
     if (!is_device_ptr(src)) {
-        double *st = c->stage + (slot < 0 ? 0 : n * slot);
+        double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : n * slot);
         CUDA_TRY(c, cudaMemcpyAsync(st, src, bytes, cudaMemcpyHostToDevice, s));
         from = st;
     }
@@ -317,7 +321,8 @@ dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_bounda
     return check_launch(c, "gather");
 }
 
-dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s, int slot = -1) {
+dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s, int slot = -1,
+                     double *buf = nullptr) {
     const Geom g = geom0(c, slot);
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     const size_t bytes = n * g.nb * sizeof(double);
@@ -325,7 +330,7 @@ dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s,
         dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
         return check_launch(c, "scatter");
     }
-    double *st = c->stage + (slot < 0 ? 0 : n * slot);
+    double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : n * slot);
     dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, st);
     TRY(check_launch(c, "scatter"));
     CUDA_TRY(c, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyDeviceToHost, s));
@@ -1161,6 +1166,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     }
     Level &L0 = c->L[0];
     TRY(dalloc(c, &c->stage, (size_t)p->nx * p->ny * p->nz * nb));
+    TRY(dalloc(c, &c->stage2, (size_t)p->nx * p->ny * p->nz * nb));
     for (double **q : {&c->U0, &c->T1, &c->T2, &c->T3}) {
         TRY(dalloc(c, q, L0.n));
         CUDA_TRY(c, cudaMemsetAsync(*q, 0, L0.n * sizeof(double), s));
@@ -1171,6 +1177,9 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     TRY(dalloc(c, &c->act, nb));
     CUDA_TRY(c, cudaMemsetAsync(c->ms, 0, nb * sizeof(dmgk::MixScalars), s));
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     CUDA_TRY(c, cudaMemsetAsync(c->red, 0, (size_t)kSlots * nb * sizeof(double), s));
     {
         cudaError_t e = cudaMallocHost(&c->hred, (size_t)kSlots * nb * sizeof(double));
@@ -1792,12 +1801,32 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
         info_reset(info);
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
+        // u is needed only by the gradient kernel at the end: its transfer and
+        // gather run on the side stream while the adjoint iterates
+        const bool need_u = Dbar || mubar;
+        if (need_u) {
+            CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            TRY(stage_in(c, u, c->U0, true, c->side, -1, c->stage2));
+            CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
+        }
         TRY(stage_in(c, w, l.f, false, s));
         dmg_status st = iterate(c, true, cycles, info, s);
-        if (st != DMG_OK && st != DMG_ENOCONV) return st;
-        if (qbar) TRY(stage_out(c, l.u, qbar, s));
+        if (st != DMG_OK && st != DMG_ENOCONV) {
+            if (need_u) cudaStreamSynchronize(c->side);
+            return st;
+        }
+        if (need_u) CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+        if (qbar && need_u) {
+            // qbar's read-out on the side stream overlaps the gradient kernel
+            CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            TRY(stage_out(c, l.u, qbar, c->side, -1, c->stage2));
+            CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
+        } else if (qbar) {
+            TRY(stage_out(c, l.u, qbar, s));
+        }
         if (Dbar || mubar) {
-            TRY(stage_in(c, u, c->U0, true, s));
             double ih2 = 1.0 / (l.h * l.h);
             {
                 ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
@@ -1813,6 +1842,7 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
             }
             if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
             if (mubar) TRY(stage_out(c, c->T2, mubar, s));
+            if (qbar) CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
         }
         TRY(end_call(c, s));
         return st;
@@ -1960,6 +1990,12 @@ dmg_status dmg_destroy(dmg_ctx *c) {
     if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     graphs_reset(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (void *q : c->dev_allocs) cudaFree(q);
     if (c->hred) cudaFreeHost(c->hred);
