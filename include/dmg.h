@@ -315,6 +315,12 @@ dmg_status dmg_slot_result(const dmg_ctx *ctx, int slot, int *status, int *cycle
 dmg_status dmg_slot_read(dmg_ctx *ctx, int slot, double *u, double *x, double *Dbar, double *mubar,
                          void *stream);
 
+/* Testing hook (fault injection on the host): the n-th device allocation made
+   by the library from now on, process-wide, fails as if the device were out of
+   memory (the call that made it returns DMG_ENOMEM and releases what it had
+   allocated); n <= 0 turns it off. */
+void dmg_debug_fail_alloc(long long n);
+
 /* Device memory held by the context, in bytes (for admission by memory budget). */
 size_t dmg_device_bytes(const dmg_ctx *ctx);
 

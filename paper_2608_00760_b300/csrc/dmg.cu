@@ -6,10 +6,12 @@
 // (Sec. 2.4, Eq. 18), the convergence loop, mixed-precision refinement and the
 // derivative kernels. It computes nothing itself.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -213,9 +215,17 @@ dmg_status check_launch(dmg_ctx *c, const char *what) {
     return DMG_OK;
 }
 
+// Host-side fault injection for tests: when > 0, the allocation with this
+// ordinal (counting from the next one, process-wide) fails as if the device
+// were out of memory.
+std::atomic<long long> g_fail_alloc_at{0};
+
 template <class T>
 dmg_status dalloc(dmg_ctx *c, T **p, size_t n) {
     void *q = nullptr;
+    const long long k = g_fail_alloc_at.load();
+    if (k > 0 && g_fail_alloc_at.fetch_sub(1) == 1)
+        return fail(c, DMG_ENOMEM, "cudaMalloc of %zu bytes failed: injected allocation failure", n * sizeof(T));
     cudaError_t e = cudaMalloc(&q, n * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1228,14 +1238,19 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         c->tail_smem[t] = first < c->nlev ? bytes(first) : 0;
     }
     {
-        static bool attr = false;
-        if (!attr) {
+        // the attribute belongs to the device's context: set it once per device
+        static std::mutex mu;
+        static bool done[256] = {false};
+        int dev = 0;
+        CUDA_TRY(c, cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 256 && !done[dev]) {
             for (auto fn : {(const void *)dmgk::k_vcycle_tail<double, dmgk::FaceCoef<double>>,
                             (const void *)dmgk::k_vcycle_tail<float, dmgk::VertCoef<float, false>>,
                             (const void *)dmgk::k_vcycle_tail<float, dmgk::VertCoef<float, true>>})
                 CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kTailSmemBudget));
-            attr = true;
+            done[dev] = true;
         }
     }
     // exact coarsest solve: dense SPD inverse of every sample by in-block Gauss-Jordan
@@ -1504,6 +1519,8 @@ dmg_status slot_read_impl(dmg_ctx *c, int slot, double *u, double *x, double *Db
 int n_states(const dmg_ctx *c) { return 2 * (c->p.nu1 + c->p.nu2) + 1; }
 
 dmg_status unrolled_alloc(dmg_ctx *c, int nck) {
+    // a failed attempt leaves un_ready false: the next call allocates a complete
+    // set again (the partial one stays with the context until dmg_destroy)
     if (!c->un_ready) {
         for (int l = 0; l < c->nlev; l++) {
             ULevel &W = c->un[l];
@@ -1690,9 +1707,16 @@ dmg_status vjp_unrolled_impl(dmg_ctx *c, const double *q, const double *w, int m
     return end_call(c, s);
 }
 
+// an NVTX range around one API call (visible in ncu / nsys timelines)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 template <class F>
-dmg_status guarded(dmg_ctx *c, F fn) {
+dmg_status guarded(dmg_ctx *c, F fn, const char *name = "dmg") {
     if (!c) return DMG_EINVAL;
+    Range r(name);
     c->err[0] = 0;
     return fn();
 }
@@ -1726,6 +1750,7 @@ void dmg_default_params(dmg_params *p) {
 
 dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, void *stream, dmg_ctx **out) {
     if (!out) return DMG_EINVAL;
+    Range r("dmg_setup");
     *out = nullptr;
     dmg_ctx *c = new (std::nothrow) dmg_ctx();
     if (!c) return DMG_ENOMEM;
@@ -1753,7 +1778,7 @@ dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, voi
         TRY(stage_out(c, l.u, u, s));
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_solve");
 }
 
 dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
@@ -1788,7 +1813,7 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
         TRY(stage_out(c, l.u, du, s));
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_jvp");
 }
 
 dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, double *qbar, double *Dbar,
@@ -1846,7 +1871,7 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
         }
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_vjp");
 }
 
 }  // extern "C"
@@ -1892,7 +1917,7 @@ dmg_status dmg_response(dmg_ctx *c, const double *q, double edge, double *Le, do
         TRY(stage_out(c, c->T3, Le, s));
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_response");
 }
 
 dmg_status dmg_response_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
@@ -1927,7 +1952,7 @@ dmg_status dmg_response_jvp(dmg_ctx *c, const double *u, const double *dq, const
         TRY(stage_out(c, c->T3, dLe, s));
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_response_jvp");
 }
 
 dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, double edge, double *qbar,
@@ -1963,7 +1988,7 @@ dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, dou
         }
         TRY(end_call(c, s));
         return st;
-    });
+    }, "dmg_response_vjp");
 }
 
 dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *out, void *stream) {
@@ -1982,7 +2007,7 @@ dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *ou
             out[2 * b + 1] = std::sqrt(hred(c, b, 1));
         }
         return DMG_OK;
-    });
+    }, "dmg_residual");
 }
 
 dmg_status dmg_destroy(dmg_ctx *c) {
@@ -2026,24 +2051,24 @@ const char *dmg_last_error(const dmg_ctx *c) {
 
 dmg_status dmg_vjp_unrolled(dmg_ctx *c, const double *q, const double *w, int m, int stride, double *u,
                             double *qbar, double *Dbar, double *mubar, void *stream) {
-    return guarded(c, [&]() { return vjp_unrolled_impl(c, q, w, m, stride, u, qbar, Dbar, mubar, S(stream)); });
+    return guarded(c, [&]() { return vjp_unrolled_impl(c, q, w, m, stride, u, qbar, Dbar, mubar, S(stream)); }, "dmg_vjp_unrolled");
 }
 
 dmg_status dmg_slot_load(dmg_ctx *c, int slot, const double *D, const double *mu, void *stream) {
-    return guarded(c, [&]() { return slot_load_impl(c, slot, D, mu, S(stream)); });
+    return guarded(c, [&]() { return slot_load_impl(c, slot, D, mu, S(stream)); }, "dmg_slot_load");
 }
 
 dmg_status dmg_slot_begin(dmg_ctx *c, int slot, int phase, const double *a, const double *b, const double *d,
                           void *stream) {
-    return guarded(c, [&]() { return slot_begin_impl(c, slot, phase, a, b, d, S(stream)); });
+    return guarded(c, [&]() { return slot_begin_impl(c, slot, phase, a, b, d, S(stream)); }, "dmg_slot_begin");
 }
 
 dmg_status dmg_step_launch(dmg_ctx *c, void *stream) {
-    return guarded(c, [&]() { return step_launch_impl(c, S(stream)); });
+    return guarded(c, [&]() { return step_launch_impl(c, S(stream)); }, "dmg_step_launch");
 }
 
 dmg_status dmg_step_finish(dmg_ctx *c, void *stream, int *ended, int *nended) {
-    return guarded(c, [&]() { return step_finish_impl(c, S(stream), ended, nended); });
+    return guarded(c, [&]() { return step_finish_impl(c, S(stream), ended, nended); }, "dmg_step_finish");
 }
 
 dmg_status dmg_slot_result(const dmg_ctx *c, int slot, int *status, int *cycles, double *rel) {
@@ -2056,10 +2081,12 @@ dmg_status dmg_slot_result(const dmg_ctx *c, int slot, int *status, int *cycles,
 }
 
 dmg_status dmg_slot_read(dmg_ctx *c, int slot, double *u, double *x, double *Dbar, double *mubar, void *stream) {
-    return guarded(c, [&]() { return slot_read_impl(c, slot, u, x, Dbar, mubar, S(stream)); });
+    return guarded(c, [&]() { return slot_read_impl(c, slot, u, x, Dbar, mubar, S(stream)); }, "dmg_slot_read");
 }
 
 size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes : 0; }
+
+void dmg_debug_fail_alloc(long long n) { g_fail_alloc_at.store(n > 0 ? n : 0); }
 
 dmg_status dmg_batch_info(const dmg_ctx *c, int *cycles, double *rel) {
     if (!c) return DMG_EINVAL;

@@ -53,7 +53,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
-           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile")
+           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc")
 
 _lib = None
 
@@ -101,6 +101,7 @@ def lib():
             "dmg_response": (i, [vp, vp, d, vp, vp, P(dmg_info), vp]),
             "dmg_vjp_unrolled": (i, [vp, vp, vp, i, i, vp, vp, vp, vp, vp]),
             "dmg_tile": (i, [vp, i, i, P(i), P(i)]),
+            "dmg_debug_fail_alloc": (None, [ctypes.c_longlong]),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
         }
@@ -288,6 +289,11 @@ def dmg_level_shape(ctx, level):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     st = lib().dmg_level_shape(ctx, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return st, (c.value, b.value, a.value)
+
+
+def dmg_debug_fail_alloc(n):
+    """Testing hook: the n-th device allocation from now on fails with DMG_ENOMEM (n <= 0: off)."""
+    lib().dmg_debug_fail_alloc(int(n))
 
 
 def dmg_tile(ctx, level, fp32=False):

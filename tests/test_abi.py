@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -82,3 +83,18 @@ def test_2d_parameter_validation():
         p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=1.0)
         st, ctx = dmg.dmg_setup(p, None, None)
         assert st == dmg.DMG_EINVAL and ctx is None and msg in dmg.dmg_last_error(None)
+
+
+def test_injected_allocation_failure_is_reported_without_a_device():
+    # the first allocation of dmg_setup fails (injected on the host before any
+    # CUDA call): ENOMEM, no context, and the message names the injection
+    from paper_2608_00760_b300 import dmg
+    p = dmg.dmg_default_params(nx=17, ny=17, nz=17, h=1.0)
+    D = np.ones(17 ** 3)
+    dmg.dmg_debug_fail_alloc(1)
+    try:
+        st, ctx = dmg.dmg_setup(p, D, D)
+    finally:
+        dmg.dmg_debug_fail_alloc(0)
+    assert st == dmg.DMG_ENOMEM and ctx is None
+    assert "injected" in dmg.dmg_last_error(None)
