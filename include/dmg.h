@@ -242,6 +242,21 @@ dmg_status dmg_response_vjp(dmg_ctx *ctx, const double *u, const double *rbar, d
                             double *qbar, double *Dbar, double *mubar, dmg_info *info, void *stream);
 
 /*
+ * dmg_solve_vjp -- dmg_solve followed by dmg_vjp (converged adjoint) in one
+ * call: u = S(q), then (qbar, Dbar, mubar) of <w, u>. The forward solution
+ * stays on the device for the gradients, and host transfers run on a second
+ * stream where they overlap the iterations: w is uploaded during the forward
+ * solve, u is read out during the adjoint solve, qbar during the gradient
+ * kernel. Results are bit for bit those of the two calls. u, qbar, Dbar,
+ * mubar may each be NULL; info_fwd / info_adj report the two iterations.
+ * Returns the first non-OK status of the two (DMG_ENOCONV still writes every
+ * output).
+ */
+dmg_status dmg_solve_vjp(dmg_ctx *ctx, const double *q, const double *w, double *u, double *qbar,
+                         double *Dbar, double *mubar, dmg_info *info_fwd, dmg_info *info_adj,
+                         void *stream);
+
+/*
  * dmg_residual -- out[2b] = ||q_b - A_b u_b||_2 and out[2b+1] = ||q_b||_2 over
  * interior vertices of every sample b, in FP64 (out is a host array of
  * 2 * batch doubles).

@@ -117,7 +117,7 @@ struct dmg_ctx {
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
     double *stage2 = nullptr;         // a second one, for transfers on the side stream
     cudaStream_t side = nullptr;      // overlaps host transfers with the iteration on the caller's stream
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_aux = nullptr;
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
@@ -1190,6 +1190,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
     CUDA_TRY(c, cudaMemsetAsync(c->red, 0, (size_t)kSlots * nb * sizeof(double), s));
     {
         cudaError_t e = cudaMallocHost(&c->hred, (size_t)kSlots * nb * sizeof(double));
@@ -1816,6 +1817,68 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
     }, "dmg_jvp");
 }
 
+dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u, double *qbar, double *Dbar,
+                         double *mubar, dmg_info *info_fwd, dmg_info *info_adj, void *stream) {
+    return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        if (!q || !w) return fail(c, DMG_EINVAL, "q and w must not be NULL");
+        info_reset(info_fwd);
+        info_reset(info_adj);
+        cudaStream_t s = S(stream);
+        Level &l = c->L[0];
+        // w goes to T3 on the side stream while the forward iterates
+        CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        TRY(stage_in(c, w, c->T3, false, c->side, -1, c->stage2));
+        CUDA_TRY(c, cudaEventRecord(c->ev_aux, c->side));
+        TRY(stage_in(c, q, l.f, false, s));
+        dmg_status st = iterate(c, false, c->p.fixed_cycles, info_fwd, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) {
+            cudaStreamSynchronize(c->side);
+            return st;
+        }
+        // the forward solution stays on the device for the gradient; its read-out
+        // (side stream) overlaps the adjoint iteration
+        CUDA_TRY(c, cudaMemcpyAsync(c->U0, l.u, l.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_aux, 0));
+        CUDA_TRY(c, cudaMemcpyAsync(l.f, c->T3, l.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (u) {
+            CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            TRY(stage_out(c, c->U0, u, c->side, -1, c->stage2));
+        }
+        dmg_status st2 = iterate(c, true, 0, info_adj, s);
+        if (st2 != DMG_OK && st2 != DMG_ENOCONV) {
+            cudaStreamSynchronize(c->side);
+            return st2;
+        }
+        if (qbar) {   // overlaps the gradient kernel
+            CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            TRY(stage_out(c, l.u, qbar, c->side, -1, c->stage2));
+        }
+        CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
+        if (Dbar || mubar) {
+            const double ih2 = 1.0 / (l.h * l.h);
+            ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+            if (c->dim == 2)
+                dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                               c->p.face_mean == DMG_FACE_HARMONIC,
+                                                               Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+            else
+                dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                             c->p.face_mean == DMG_FACE_HARMONIC,
+                                                             Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+            TRY(check_launch(c, "grad"));
+            if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
+            if (mubar) TRY(stage_out(c, c->T2, mubar, s));
+        }
+        CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+        TRY(end_call(c, s));
+        return st != DMG_OK ? st : st2;
+    }, "dmg_solve_vjp");
+}
+
 dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, double *qbar, double *Dbar,
                    double *mubar, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
@@ -2021,6 +2084,7 @@ dmg_status dmg_destroy(dmg_ctx *c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_aux) cudaEventDestroy(c->ev_aux);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (void *q : c->dev_allocs) cudaFree(q);
     if (c->hred) cudaFreeHost(c->hred);

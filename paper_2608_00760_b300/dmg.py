@@ -53,7 +53,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
-           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc")
+           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp")
 
 _lib = None
 
@@ -101,6 +101,7 @@ def lib():
             "dmg_response": (i, [vp, vp, d, vp, vp, P(dmg_info), vp]),
             "dmg_vjp_unrolled": (i, [vp, vp, vp, i, i, vp, vp, vp, vp, vp]),
             "dmg_tile": (i, [vp, i, i, P(i), P(i)]),
+            "dmg_solve_vjp": (i, [vp, vp, vp, vp, vp, vp, vp, P(dmg_info), P(dmg_info), vp]),
             "dmg_debug_fail_alloc": (None, [ctypes.c_longlong]),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
@@ -180,6 +181,12 @@ def dmg_solve(ctx, q, u, info=None, stream=None, n=None):
 def dmg_jvp(ctx, u, dq, dD, dmu, du, info=None, stream=None, n=None):
     return lib().dmg_jvp(ctx, _ptr(u, n), _ptr(dq, n), _ptr(dD, n), _ptr(dmu, n), _ptr(du, n),
                          ctypes.byref(info) if info is not None else None, _stream(stream))
+
+
+def dmg_solve_vjp(ctx, q, w, u, qbar, Dbar, mubar, info_fwd=None, info_adj=None, stream=None, n=None):
+    return lib().dmg_solve_vjp(ctx, _ptr(q, n), _ptr(w, n), _ptr(u, n), _ptr(qbar, n), _ptr(Dbar, n),
+                               _ptr(mubar, n), ctypes.byref(info_fwd) if info_fwd is not None else None,
+                               ctypes.byref(info_adj) if info_adj is not None else None, _stream(stream))
 
 
 def dmg_vjp(ctx, u, w, cycles, qbar, Dbar, mubar, info=None, stream=None, n=None):
