@@ -383,6 +383,47 @@ def run_unrolled(dmg, torch, args, world, local):
                      "gradient")
 
 
+def run_513(dmg, torch, args, world, local):
+    """The larger headline size (513^3, tissue-like): fwd+VJP pairs/s mixed and FP64, and the mixed results'
+    relative error against the FP64 GPU path (the oracle is too slow at this size)."""
+    from paper_2608_00760_b300 import inputs
+    n = args.size_513
+    dev = torch.device("cuda", local)
+    w = inputs.tissue_torch((n, n, n), 13, device=dev, keys=("D", "mu", "q", "w"))
+    stream = torch.cuda.current_stream(dev)
+    out = dict(workload="tissue-like %d^3 fwd+VJP(q,D,mu), rtol 1e-10" % n)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        S = dmg.Solver(w["D"], w["mu"], 0.5, rtol=RTOL, inner_cycles=args.inner,
+                       precision=dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64)
+        outs = [torch.empty_like(w["q"]) for _ in range(4)]
+        fi, ai = dmg.dmg_info(), dmg.dmg_info()
+
+        def step():
+            st = dmg.dmg_solve_vjp(S.ctx, w["q"], w["w"], *outs, fi, ai, stream, n=S.n)
+            assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+
+        step()
+        steps = 3
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        ms = max_over_ranks(world, e0.elapsed_time(e1)) / steps
+        out[prec] = dict(value=world * 1e3 / ms, unit="fwd+VJP pairs/s", ms_per_step=ms, cycles=[fi.cycles, ai.cycles],
+                         context_gb=dmg.dmg_device_bytes(S.ctx) / 1e9)
+        res[prec] = [x.clone() for x in outs]
+        S.close()
+    out["mixed_vs_fp64_rel_err"] = {k: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+                                    for k, a, b in zip(("u", "qbar", "Dbar", "mubar"), res["mixed"], res["fp64"])}
+    return out
+
+
 def run_2d(dmg, torch, args, world, local, peaks, peak_src):
     """The 2D solver (the paper's 2D benchmarks): fwd+VJP pairs at n^2, mixed and FP64."""
     from paper_2608_00760_b300 import inputs
@@ -575,6 +616,7 @@ def main():
     ap.add_argument("--unrolled-size", type=int, default=257, help="grid of the unrolled-gradient timing (0: skip)")
     ap.add_argument("--vi-only", action="store_true", help="run only the batched VI step and print its object")
     ap.add_argument("--size-2d", type=int, default=4097, help="grid of the 2D solver timing (0: skip)")
+    ap.add_argument("--size-513", type=int, default=513, help="larger 3D grid timed next to the headline (0: skip)")
     ap.add_argument("--autotune", type=int, default=1, help="tile autotuner at setup (dmg_params.autotune)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
@@ -658,6 +700,9 @@ def main():
                cycles=dict(fwd=head["fwd_cycles"], adj=head["adj_cycles"], fwd_outer=head["fwd_outer"],
                            adj_outer=head["adj_outer"], fwd_rel=head["fwd_rel"], adj_rel=head["adj_rel"]),
                gpu_launches=head["launches"], gpu_launches_per_step=head["launches"] / args.steps,
+               device_memory_gb=dict(context=dmg.dmg_device_bytes(S.ctx) / 1e9,
+                                     note="everything the fwd+VJP pair uses is allocated at setup: the pull-back "
+                                          "adds no device memory to the forward"),
                roofline=roofline(head, precisions[0]), clocks=head["clocks"])
     for prec in precisions[1:]:
         r = results[prec]
@@ -694,6 +739,7 @@ def main():
     out["serving"] = (run_serving(dmg, torch, args, world, rank, local) if args.serve_requests > 0 else None)
     out["unrolled"] = run_unrolled(dmg, torch, args, world, local) if args.unrolled_size > 0 else None
     out["two_d"] = run_2d(dmg, torch, args, world, local, peaks, peak_src) if args.size_2d > 0 else None
+    out["c3_large"] = run_513(dmg, torch, args, world, local) if args.size_513 > 0 else None
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
