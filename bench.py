@@ -602,8 +602,8 @@ def reference_arm(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="dmg", choices=["dmg", "reference"])
     ap.add_argument("--size", type=int, default=N_SIDE)
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
