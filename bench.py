@@ -32,6 +32,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -75,7 +76,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d_%d.csv" % (os.getpid(), index))
+        self.path = os.path.join(tempfile.gettempdir(), "dmg_clocks_%d_%d.csv" % (os.getpid(), index))
 
     def __enter__(self):
         try:
