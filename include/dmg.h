@@ -61,7 +61,8 @@ typedef enum {
     DMG_ENOCONV = 4,  /* rtol not reached within max_cycles; outputs hold the last
                          iterate and info->rel_residual its residual */
     DMG_ENAN = 5,     /* a residual norm was not finite (NaN/Inf in inputs) */
-    DMG_ETIMEOUT = 6  /* reserved for bounded device waits */
+    DMG_ETIMEOUT = 6  /* reserved for bounded device waits (no kernel of the library
+                         waits on a flag, so no call returns it) */
 } dmg_status;
 
 enum { DMG_FP64 = 0, DMG_MIXED = 1 };

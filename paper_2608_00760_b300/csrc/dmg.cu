@@ -121,8 +121,7 @@ struct dmg_ctx {
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
-    double *red = nullptr;            // reduction results (device, kRedSlots doubles per sample;
-                                      // slot 3 of sample 0 = kernel error flag)
+    double *red = nullptr;            // reduction results (device, kRedSlots doubles per sample)
     double *hred = nullptr;           // pinned host copy of red
     int *act = nullptr;               // device mask: sample still iterating
     const int *mask = nullptr;        // mask argument of the launches being issued: act, or NULL
@@ -562,21 +561,17 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
 // --- reductions ------------------------------------------------------------------
 constexpr int kSlots = dmgk::kRedSlots;
 
-// copy the reduction slots of every sample (and the kernel error flag) to pinned host memory
+// copy the reduction slots of every sample to pinned host memory
 dmg_status enqueue_readback(dmg_ctx *c, cudaStream_t s) {
     CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, (size_t)kSlots * c->nb * sizeof(double), cudaMemcpyDeviceToHost,
                                 s));
     return DMG_OK;
 }
 
-// wait for the stream, check the kernel error flag; the results are in
-// hred[sample * kSlots + slot]
+// wait for the stream; the results are in hred[sample * kSlots + slot]
 dmg_status sync_read(dmg_ctx *c, cudaStream_t s) {
     CUDA_TRY(c, cudaStreamSynchronize(s));
     prof_harvest(c, c->prof_direct, true);
-    int kerr = 0;
-    memcpy(&kerr, c->hred + 3, sizeof(int));
-    if (kerr != 0) return fail(c, DMG_ETIMEOUT, "a bounded device wait ran out (kernel error flag %d)", kerr);
     return DMG_OK;
 }
 
@@ -1422,9 +1417,6 @@ dmg_status step_finish_impl(dmg_ctx *c, cudaStream_t s, int *ended_out, int *nen
     CUDA_TRY(c, cudaStreamSynchronize(s));
     prof_harvest(c, c->prof_direct, true);
     for (Graph &G : c->g_srv) prof_harvest(c, G.prof, false);
-    int kerr = 0;
-    memcpy(&kerr, c->hred + 3, sizeof(int));
-    if (kerr != 0) return fail(c, DMG_ETIMEOUT, "a bounded device wait ran out (kernel error flag %d)", kerr);
     std::vector<int> ended;
     const int per_step = c->p.precision == DMG_MIXED ? c->p.inner_cycles : 1;
     for (int b = 0; b < c->nb; b++) {
