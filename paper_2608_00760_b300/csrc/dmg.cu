@@ -2,23 +2,26 @@
 //
 // The runtime owns the grid hierarchy (Sec. 2.2 of arXiv 2608.00760: levels
 // h_k = 2 h_{k-1}, operator rediscretised per level) and schedules the kernels
-// of kernels.cuh on the caller's stream: the V-cycle (Eq. 5), its transpose
-// (Sec. 2.4, Eq. 18), the convergence loop, mixed-precision refinement and the
-// derivative kernels. It computes nothing itself.
+// on the caller's stream: the V-cycle (Eq. 5), its transpose (Sec. 2.4,
+// Eq. 18), the convergence loop, mixed-precision refinement and the derivative
+// kernels (kernels.cuh; 2D grids: kernels2d.cuh; the unrolled gradient:
+// unrolled.cuh). Around them: batches of independent problems, the slot-level
+// serving interface, CUDA graphs per step, the tile autotuner and the
+// response operator. It computes nothing itself.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
-#include <cmath>
-#include <cstdlib>
 #include <atomic>
-#include <map>
-#include <mutex>
-#include <string>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/dmg.h"
