@@ -337,6 +337,12 @@ dmg_status dmg_slot_read(dmg_ctx *ctx, int slot, double *u, double *x, double *D
    allocated); n <= 0 turns it off. */
 void dmg_debug_fail_alloc(long long n);
 
+/* Bounds-checked builds (compiled with -DDMG_BOUNDS_CHECK, the library's stand-in
+   for a memory checker): the number of device accesses counted outside their
+   arrays so far (every call also returns DMG_ECUDA when it added to it); -1 in
+   normal builds. */
+long long dmg_debug_oob_count(void);
+
 /* Device memory held by the context, in bytes (for admission by memory budget). */
 size_t dmg_device_bytes(const dmg_ctx *ctx);
 

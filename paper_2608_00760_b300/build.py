@@ -35,18 +35,25 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    if not force and os.path.exists(OUT):
-        t = os.path.getmtime(OUT)
+OUT_CHECK = os.path.join(PKG, "_lib", "libdmg_check.so")
+
+
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile the library; check=True builds the bounds-checked variant
+    (-DDMG_BOUNDS_CHECK) as _lib/libdmg_check.so."""
+    out = OUT_CHECK if check else OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(d) <= t for d in DEPS):
-            return OUT
-    tmp = OUT + ".tmp.%d" % os.getpid()
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp] + SOURCES
+            return out
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = ([nvcc()] + NVCC_FLAGS + (["-DDMG_BOUNDS_CHECK"] if check else []) +
+           (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp] + SOURCES)
     subprocess.check_call(cmd)
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

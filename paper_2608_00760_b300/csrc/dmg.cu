@@ -49,6 +49,8 @@ inline Geom smem_geom(const Geom &g) {
     s.hx = g.nhalf();
     s.sy = 2 * s.hx;
     s.sz = (long long)s.sy * g.ny;
+    s.sb = s.sz * g.nz;   // the staged array's extent (the tail shifts global pointers by g.sb)
+    s.nb = 1;
     return s;
 }
 
@@ -521,6 +523,7 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
         a.pre_first = pre_first;
         a.post_first = post_first;
         a.act = c->mask;
+        a.load_u = l0 == 0;   // the V-cycle of the finest level continues from the current iterate
         dmgk::k_vcycle_tail<T, C><<<c->nb, 1024, c->tail_smem[t], s>>>(a);
         return check_launch(c, "vcycle_tail");
     });
@@ -1709,12 +1712,33 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 
+#ifdef DMG_BOUNDS_CHECK
+// checked builds: accesses counted outside their arrays since the last call
+unsigned long long oob_delta() {
+    static unsigned long long seen = 0;
+    unsigned long long n = 0;
+    if (cudaMemcpyFromSymbol(&n, dmgk::dmg_oob_count, sizeof(n)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const unsigned long long d = n - seen;
+    seen = n;
+    return d;
+}
+#endif
+
 template <class F>
 dmg_status guarded(dmg_ctx *c, F fn, const char *name = "dmg") {
     if (!c) return DMG_EINVAL;
     Range r(name);
     c->err[0] = 0;
-    return fn();
+    dmg_status st = fn();
+#ifdef DMG_BOUNDS_CHECK
+    cudaDeviceSynchronize();
+    if (const unsigned long long d = oob_delta())
+        return fail(c, DMG_ECUDA, "%s: %llu accesses outside their arrays", name, d);
+#endif
+    return st;
 }
 
 }  // namespace
@@ -2146,6 +2170,19 @@ dmg_status dmg_slot_read(dmg_ctx *c, int slot, double *u, double *x, double *Dba
 size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes : 0; }
 
 void dmg_debug_fail_alloc(long long n) { g_fail_alloc_at.store(n > 0 ? n : 0); }
+
+long long dmg_debug_oob_count(void) {
+#ifdef DMG_BOUNDS_CHECK
+    unsigned long long n = 0;
+    if (cudaMemcpyFromSymbol(&n, dmgk::dmg_oob_count, sizeof(n)) != cudaSuccess) {
+        cudaGetLastError();
+        return -2;
+    }
+    return (long long)n;
+#else
+    return -1;
+#endif
+}
 
 dmg_status dmg_batch_info(const dmg_ctx *c, int *cycles, double *rel) {
     if (!c) return DMG_EINVAL;

@@ -26,6 +26,22 @@
 
 namespace dmgk {
 
+// Bounds-checked build (-DDMG_BOUNDS_CHECK, the stand-in for a memory checker):
+// the per-vertex bodies and colour kernels count every position that falls
+// outside its array (a sample's padded extent) or every sample index outside
+// the batch; the runtime reads the count after each call. Off by default.
+#ifdef DMG_BOUNDS_CHECK
+__device__ unsigned long long dmg_oob_count;
+#define DMG_CHECK(cond)                                             \
+    do {                                                            \
+        if (!(cond)) atomicAdd(&dmg_oob_count, 1ULL);               \
+    } while (0)
+#else
+#define DMG_CHECK(cond) \
+    do {                \
+    } while (0)
+#endif
+
 struct Geom {
     int nx, ny, nz;   // vertices per axis, boundary included
     int hx;           // half-row length (elements)
@@ -46,6 +62,8 @@ struct Geom {
     __host__ __device__ __forceinline__ int xp(int i) const { return (i & 1) ? 1 - hx : hx; }
     // number of x positions of one parity: even i = 0..nx-1 -> (nx+1)/2
     __host__ __device__ __forceinline__ int nhalf() const { return (nx + 1) / 2; }
+    // position inside one sample's array (bounds-checked builds only)
+    __device__ __forceinline__ void check(long long p) const { DMG_CHECK(p >= 0 && p < sb); }
 };
 
 enum { kInterior = 0, kCells = 1, kAll = 2 };
@@ -56,6 +74,7 @@ __device__ __forceinline__ int zsplit(const Geom &g, int which, int &plane) {
     const unsigned z = blockIdx.z, m = g.mz[which];
     const int smp = m ? (int)__umulhi(z, m) : (int)z;
     plane = (int)z - smp * (g.nz - 2 + which);
+    DMG_CHECK(smp < g.nb && plane >= 0 && plane < g.nz - 2 + which);
     return smp;
 }
 
@@ -169,6 +188,9 @@ template <class T, class C>
 __device__ __forceinline__ void smooth_point(const Geom &g, T *u, const T *f, const C &c, int i, int j, int k) {
     const long long p = g.pos(i, j, k);
     const Nbr n = neighbours(g, i);
+    g.check(p);
+#pragma unroll
+    for (int q = 0; q < 6; q++) g.check(p + n.o[q]);
     T a[6];
     c.couplings(p, n, a);
     const T s = coupled_sum(f[p], u, p, n, a);
@@ -191,6 +213,9 @@ __device__ __forceinline__ void restrict_point(const Geom &gf, const T *r, const
                                                int K) {
     const long long p = gf.pos(2 * I, 2 * J, 2 * K);
     const int om = gf.xm(2 * I), op = gf.xp(2 * I);
+    gc.check(gc.pos(I, J, K));
+    gf.check(p - gf.sz - gf.sy + om);
+    gf.check(p + gf.sz + gf.sy + op);
     T s = T(0);
 #pragma unroll
     for (int c = -1; c <= 1; c++) {
@@ -213,6 +238,9 @@ __device__ __forceinline__ void restrict_point(const Geom &gf, const T *r, const
 // e is zero on the coarse boundary; only fine interior vertices are written.
 template <class T>
 __device__ __forceinline__ void prolong_cell(const Geom &gc, const T *e, const Geom &gf, T *u, int I, int J, int K) {
+    gc.check(gc.pos(I, J, K));
+    gc.check(gc.pos(I + 1, J + 1, K + 1));
+    gf.check(gf.pos(2 * I, 2 * J, 2 * K));
     T c[2][2][2];
 #pragma unroll
     for (int z = 0; z < 2; z++)
@@ -352,6 +380,10 @@ __device__ __forceinline__ bool colour_vertex32(const Geom &g, int color, const 
     base = BATCH ? (long long)smp * g.sb : 0;
     p = k * (int)g.sz + j * g.sy + par * g.hx + (t + 1 - par);   // i = 2t + 2 - par
     xm = par ? -g.hx : g.hx - 1;
+    g.check(p - g.sz);
+    g.check(p + g.sz);
+    g.check(p + xm);
+    g.check(p + xm + 1);
     return true;
 }
 
@@ -470,6 +502,7 @@ __device__ __forceinline__ void coarse_solve_block(const Geom &g, const T *Ainv,
     const int nxi = g.nx - 2, nyi = g.ny - 2;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         const int i = c % nxi + 1, j = (c / nxi) % nyi + 1, k = c / (nxi * nyi) + 1;
+        g.check(g.pos(i, j, k));
         fs[c] = f[g.pos(i, j, k)];
     }
     __syncthreads();
@@ -521,6 +554,8 @@ struct TailArgs {
     int nc;
     int npre, npost, pre_first, post_first;
     const int *act;
+    int load_u;  // 1: the first tail level starts from its iterate in global memory (the tail
+                 // begins at the finest level); 0: from zero (a coarse level, Sec. 2.3.1)
 };
 
 // shared-memory coefficient copies
@@ -586,6 +621,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
         for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
             const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
             sf[0][gs.pos(i, j, k)] = a.L[0].f[smp * g.sb + g.pos(i, j, k)];
+            if (a.load_u) su[0][gs.pos(i, j, k)] = a.L[0].u[smp * g.sb + g.pos(i, j, k)];
         }
     }
     __syncthreads();
@@ -658,6 +694,8 @@ __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict
     dst += blockIdx.y * g.sb;
     const unsigned r = t / g.nx;
     const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
+    g.check(g.pos(i, j, k));
+    DMG_CHECK(blockIdx.y < (unsigned)g.nb);
     double v = src[t];
     if (zero_boundary &&
         (i == 0 || j == 0 || i == g.nx - 1 || j == g.ny - 1 || (g.nz > 1 && (k == 0 || k == g.nz - 1))))
@@ -674,6 +712,8 @@ __global__ void __launch_bounds__(256) k_scatter(Geom g, const double *__restric
     dst += (long long)blockIdx.y * n;
     const unsigned r = t / g.nx;
     const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
+    g.check(g.pos(i, j, k));
+    DMG_CHECK(blockIdx.y < (unsigned)g.nb);
     dst[t] = src[g.pos(i, j, k)];
 }
 

@@ -79,6 +79,11 @@ __global__ void __launch_bounds__(256) k_smooth_half2(Geom g, T *__restrict__ u,
     c = c.shifted(o);
     const long long p = g.pos(i, j, 0);
     const int xm = g.xm(i);
+    DMG_CHECK(smp < g.nb);
+    g.check(p - g.sy);
+    g.check(p + g.sy);
+    g.check(p + xm);
+    g.check(p + xm + 1);
     T a[4];
     couplings2(c, p, xm, g.sy, a);
     u[p] = finish2(c, coupled_sum2(f[p], u, p, xm, g.sy, a), p, a);
@@ -125,6 +130,9 @@ __global__ void __launch_bounds__(256) k_restrict2(Geom gf, const T *__restrict_
         const T row = r[q + om] + T(2) * r[q] + r[q + op];
         s += (b == 0 ? T(2) : T(1)) * row;
     }
+    gf.check(p - gf.sy + om);
+    gf.check(p + gf.sy + op);
+    gc.check(gc.pos(I, J, 0));
     fc[pc] = s * T(1.0 / 16.0);
     uc[pc] = T(0);
 }

@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(256) k_rev_own(Geom g, FaceCoef<double> c, int
     if (j > g.ny - 2 || i > g.nx - 2) return;
     const long long p = g.pos(i, j, k);
     const Nbr n = neighbours(g, i);
+    g.check(p);
+#pragma unroll
+    for (int q = 0; q < 6; q++) g.check(p + n.o[q]);
     const double t = ub[p] * __ldg(c.invd + p);
     const double up = U[p];
     fb[p] += t;

@@ -20,6 +20,16 @@ import os
 import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libdmg.so")
+_CHECK_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libdmg_check.so")
+
+
+def use_check_library():
+    """Load the bounds-checked build (libdmg_check.so) instead of libdmg.so; call
+    before the first use of the library in the process."""
+    global _LIB_PATH
+    if _lib is not None and _LIB_PATH != _CHECK_PATH:
+        raise RuntimeError("the library is already loaded")
+    _LIB_PATH = _CHECK_PATH
 
 DMG_OK, DMG_EINVAL, DMG_ENOMEM, DMG_ECUDA, DMG_ENOCONV, DMG_ENAN, DMG_ETIMEOUT = range(7)
 DMG_FP64, DMG_MIXED = 0, 1
@@ -53,7 +63,8 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_launch_count", "dmg_profile_begin", "dmg_profile_end", "dmg_residual_static",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
-           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp")
+           "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp",
+           "dmg_debug_oob_count")
 
 _lib = None
 
@@ -103,6 +114,7 @@ def lib():
             "dmg_tile": (i, [vp, i, i, P(i), P(i)]),
             "dmg_solve_vjp": (i, [vp, vp, vp, vp, vp, vp, vp, P(dmg_info), P(dmg_info), vp]),
             "dmg_debug_fail_alloc": (None, [ctypes.c_longlong]),
+            "dmg_debug_oob_count": (ctypes.c_longlong, []),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
         }
@@ -301,6 +313,11 @@ def dmg_level_shape(ctx, level):
 def dmg_debug_fail_alloc(n):
     """Testing hook: the n-th device allocation from now on fails with DMG_ENOMEM (n <= 0: off)."""
     lib().dmg_debug_fail_alloc(int(n))
+
+
+def dmg_debug_oob_count():
+    """Accesses counted outside their arrays (bounds-checked build), -1 in normal builds."""
+    return lib().dmg_debug_oob_count()
 
 
 def dmg_tile(ctx, level, fp32=False):

@@ -331,3 +331,30 @@ def test_long_thin_single_level_grid(dmg, precision):
     assert S.levels() == [shape]
     u = S.solve(T(q))
     assert rel(u, oracle.direct_solve(D, mu, 0.1, q)) <= 1e-10
+
+
+# grids small enough that the single-CTA tail starts at the finest level
+# (<= 512 interior vertices in FP64, <= 4096 in FP32): each V-cycle must continue
+# from the current iterate, so the FP64 solve converges at the V-cycle's rate
+@pytest.mark.parametrize("shape", [(5, 5, 5), (9, 9, 9), (5, 9, 17), (17, 17, 17), (9, 17, 33)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tail_at_the_finest_level(dmg, shape, precision):
+    w = inputs.tissue(seed=7, shape=shape)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision)
+    u = S.solve(T(w["q"]))
+    cycles = S.last_info.cycles
+    qb, Db, mb = S.vjp(u, T(w["w"]))
+    S.close()
+    assert cycles <= 16
+    H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
+    ur, _, _ = H.solve(w["q"], rtol=1e-10)
+    qr, Dr, mr, _ = H.vjp(ur, w["w"], rtol=1e-10)
+    for got, ref in ((u, ur), (qb, qr), (Db, Dr), (mb, mr)):
+        assert rel(got, ref) <= TOL_CONV
+    # the fixed-cycle FP64 iterate equals the oracle's m-cycle iterate (the same V-cycle)
+    if precision == 0:
+        S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], fixed_cycles=3)
+        u3 = S.solve(T(w["q"]))
+        S.close()
+        ref3, _, _ = H.solve(w["q"], fixed=3)
+        assert rel(u3, ref3) <= 1e-11
