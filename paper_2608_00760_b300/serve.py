@@ -30,6 +30,34 @@ import numpy as np
 
 from . import dmg
 
+class _Cuda:
+    """The streams and events the server uses (tests of the scheduling logic
+    replace this with a host-only fake)."""
+
+    @staticmethod
+    def stream(device):
+        import torch
+        return torch.cuda.Stream(device)
+
+    @staticmethod
+    def use(stream):
+        import torch
+        return torch.cuda.stream(stream)
+
+    @staticmethod
+    def event(stream):
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
+    @staticmethod
+    def sync(stream):
+        stream.synchronize()
+
+
+_dev = _Cuda()
+
 PHASES = {"fwd": (dmg.DMG_PHASE_FORWARD,),
           "jvp": (dmg.DMG_PHASE_FORWARD, dmg.DMG_PHASE_TANGENT),
           "vjp": (dmg.DMG_PHASE_FORWARD, dmg.DMG_PHASE_ADJOINT)}
@@ -76,13 +104,13 @@ class Pool:
         self.shape, self.slots = tuple(shape), int(slots)
         self.n = int(np.prod(self.shape))
         self.device = device
-        self.stream = torch.cuda.Stream(device)
+        self.stream = _dev.stream(device)
         nz, ny, nx = self.shape
         p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.slots, **params)
-        with torch.cuda.stream(self.stream):
+        with _dev.use(self.stream):
             ones = torch.ones((self.slots,) + self.shape, dtype=torch.float64, device=device)
             st, self.ctx = dmg.dmg_setup(p, ones, torch.zeros_like(ones), stream=self.stream)
-        self.stream.synchronize()
+        _dev.sync(self.stream)
         del ones
         if st != dmg.DMG_OK:
             raise dmg.DMGError(st, dmg.dmg_last_error(None))
@@ -105,7 +133,7 @@ class Pool:
     def admit(self, req, now):
         torch = self.torch
         slot = self.free.pop()
-        with torch.cuda.stream(self.stream):
+        with _dev.use(self.stream):
             x = req.make_inputs(self.device)
         self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=self.n))
         self._check(dmg.dmg_slot_begin(self.ctx, slot, dmg.DMG_PHASE_FORWARD, x["q"], None, None, self.stream,
@@ -116,8 +144,7 @@ class Pool:
 
     def launch(self):
         self._check(dmg.dmg_step_launch(self.ctx, self.stream))
-        self.step_event = self.torch.cuda.Event()
-        self.step_event.record(self.stream)
+        self.step_event = _dev.event(self.stream)
 
     def in_flight(self):
         return self.step_event is not None
@@ -154,7 +181,7 @@ class Pool:
                 continue
             req.status = status
             if ok:
-                with torch.cuda.stream(self.stream):
+                with _dev.use(self.stream):
                     out = {k: torch.empty(self.shape, dtype=torch.float64, device=self.device)
                            for k in OUTPUT_KEYS[req.kind]}
                 if req.kind == "fwd":
@@ -169,8 +196,7 @@ class Pool:
                 req.outputs = out
             done.append((slot, req))
         if done:
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
+            ev = _dev.event(self.stream)
             for slot, req in done:
                 req.pool_steps = (req.pool_steps[0], self.steps)
                 self.busy[slot][2] = None
@@ -282,6 +308,9 @@ class Server:
             for p in pools:
                 if p.step_done():
                     p.finish()
+                    # slots freed by this step take waiting requests before the
+                    # next step is launched, so they lose no step
+                    self._admit(queue, clock())
                     moved = True
                 if not p.in_flight() and p.active():
                     p.launch()
