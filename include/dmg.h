@@ -104,6 +104,12 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 reused within the process for the same device, precision,
  *                 grid, batch and face mean, and, if the environment variable
  *                 DMG_TUNE_CACHE names a file, read from and appended to it.
+ *   split_prolong 0 (default): on 3D levels of the FP32 V-cycle, the
+ *                 prolongation is fused into the first post-smoothing
+ *                 half-sweep (the corrected values are formed where that
+ *                 half-sweep reads them and never stored); 1: separate
+ *                 prolongation and half-sweep kernels. Both give the same
+ *                 results bit for bit.
  */
 typedef struct {
     int nx, ny, nz;
@@ -119,6 +125,7 @@ typedef struct {
     int inner_cycles;
     int batch;
     int autotune;
+    int split_prolong;
 } dmg_params;
 
 #define DMG_HIST_LEN 64
@@ -404,7 +411,8 @@ dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 enum {
     DMG_KERNEL_SMOOTH = 0,     /* one RB-GS half-sweep (one colour) */
     DMG_KERNEL_RESTRICT = 1,   /* defect + full-weighting restriction */
-    DMG_KERNEL_PROLONG = 2,    /* prolongation + correction */
+    DMG_KERNEL_PROLONG = 2,    /* prolongation + correction (FP32 3D levels with
+                                  post-smoothing: fused with the first post half-sweep) */
     DMG_KERNEL_RESIDUAL = 3,   /* FP64 residual + norm */
     DMG_KERNEL_GRAD = 4        /* coefficient gradients */
 };

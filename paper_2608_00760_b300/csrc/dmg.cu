@@ -382,41 +382,42 @@ dmg_status dispatch(dmg_ctx *c, Level &l, Fn fn) {
     else return with_coef32(c, l, fn);
 }
 
+// one RB-GS half-sweep of `color` on level lev
+template <class T>
+dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
+    Level &l = c->L[lev];
+    ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
+    if (c->dim == 2) {
+        return dispatch<T>(c, l, [&](auto cf) {
+            dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color, c->mask);
+            return check_launch(c, "smooth");
+        });
+    }
+    if constexpr (sizeof(T) == 4) {
+        return with_coef32(c, l, [&](auto cf) {
+            constexpr bool H = decltype(cf)::harmonic;
+            const dim3 b = c->tb[1][lev];
+            if (c->nb == 1)
+                dmgk::k_smooth_half32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                 nullptr);
+            else
+                dmgk::k_smooth_half32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                                                                                c->mask);
+            return check_launch(c, "smooth");
+        });
+    } else {
+        const dim3 b = c->tb[0][lev];
+        dmgk::k_smooth_half<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color, c->mask);
+        return check_launch(c, "smooth");
+    }
+}
+
 // nsweeps RB-GS sweeps; each sweep is the half-sweep of colour `first` then the other
 template <class T>
 dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
-    Level &l = c->L[lev];
     for (int it = 0; it < nsweeps; it++) {
-        for (int h = 0; h < 2; h++) {
-            ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
-            int color = h == 0 ? first : 1 - first;
-            if (c->dim == 2) {
-                TRY(dispatch<T>(c, l, [&](auto cf) {
-                    dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color,
-                                                                              c->mask);
-                    return check_launch(c, "smooth");
-                }));
-                continue;
-            }
-            if constexpr (sizeof(T) == 4) {
-                TRY(with_coef32(c, l, [&](auto cf) {
-                    constexpr bool H = decltype(cf)::harmonic;
-                    const dim3 b = c->tb[1][lev];
-                    if (c->nb == 1)
-                        dmgk::k_smooth_half32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                         nullptr);
-                    else
-                        dmgk::k_smooth_half32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                        c->mask);
-                    return check_launch(c, "smooth");
-                }));
-            } else {
-                const dim3 b = c->tb[0][lev];
-                dmgk::k_smooth_half<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color,
-                                                                       c->mask);
-                TRY(check_launch(c, "smooth"));
-            }
-        }
+        TRY(half_sweep<T>(c, lev, first, s));
+        TRY(half_sweep<T>(c, lev, 1 - first, s));
     }
     return DMG_OK;
 }
@@ -474,6 +475,25 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
         TRY(check_launch(c, "restrict"));
     }
     return DMG_OK;
+}
+
+// u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev, in one
+// FP32 launch that stores only the colour's new values (k_prolong_smooth32);
+// the half-sweep of the other colour must follow.
+dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
+    Level &l = c->L[lev], &cl = c->L[lev + 1];
+    ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
+    return with_coef32(c, l, [&](auto cf) {
+        constexpr bool H = decltype(cf)::harmonic;
+        const dim3 b = c->tb[1][lev];
+        if (c->nb == 1)
+            dmgk::k_prolong_smooth32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
+                                                                                color, nullptr);
+        else
+            dmgk::k_prolong_smooth32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
+                                                                               color, c->mask);
+        return check_launch(c, "prolong_smooth");
+    });
 }
 
 template <class T>
@@ -559,6 +579,12 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
     // after pre-smoothing the defect is zero on the colour updated last
     TRY(restrict_defect<T>(c, lev, npre > 0 ? 1 - pre_first : -1, s));
     TRY(vcycle<T>(c, lev + 1, transposed, s));
+    if (sizeof(T) == 4 && c->dim == 3 && npost > 0 && !c->p.split_prolong) {
+        // correction fused into the first post half-sweep; its other half next
+        TRY(prolong_smooth32(c, lev, postf, s));
+        TRY(half_sweep<T>(c, lev, 1 - postf, s));
+        return smooth<T>(c, lev, postf, npost - 1, s);
+    }
     TRY(prolong<T>(c, lev, s));
     TRY(smooth<T>(c, lev, postf, npost, s));
     return DMG_OK;
@@ -922,6 +948,7 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (p->symmetric != 0 && p->symmetric != 1) return fail(c, DMG_EINVAL, "symmetric must be 0 or 1");
     if (p->batch < 1) return fail(c, DMG_EINVAL, "batch must be >= 1");
     if (p->autotune != 0 && p->autotune != 1) return fail(c, DMG_EINVAL, "autotune must be 0 or 1");
+    if (p->split_prolong != 0 && p->split_prolong != 1) return fail(c, DMG_EINVAL, "split_prolong must be 0 or 1");
     {
         const Geom g0 = make_geom(p->nx, p->ny, p->nz, 1);
         if (g0.sb > (long long)INT32_MAX)

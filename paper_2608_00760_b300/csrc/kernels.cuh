@@ -445,6 +445,136 @@ __global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *
     r[p] = coupled_sum32(fmaf(-dg, u[p], f[p]), u, p, xm, sy, sz, a);
 }
 
+// ---------------------------------------------------------------------------
+// Prolongation fused into the first post-smoothing half-sweep (FP32).
+//
+// A half-sweep of colour c sets u_p = (f_p + sum_n a_n u_n) / diag_p from the
+// other-colour neighbours n alone: it never reads the old u_p. The half-sweep
+// of the other colour that follows overwrites every other-colour vertex, again
+// without reading it. So after the correction u += P e (Eq. 17), only the
+// corrected other-colour values are ever read, and only by the first
+// half-sweep. k_prolong_smooth32 forms them on the fly, u_n + (P e)_n, and
+// stores nothing but the new colour-c values: with the other colour's
+// half-sweep after it, the level ends bitwise where k_prolong_add and both
+// half-sweeps end, without the read and write of the whole fine array that
+// the separate correction costs.
+//
+// (P e) at a fine vertex repeats prolong_cell's operations in its order: along
+// y, then z, then x. In one row (j, k) of one colour every thread has the same
+// parities of i, j and k, so a warp runs one specialisation, PX/PY/PZ the
+// parities of the vertex it updates. The coarse values its six neighbours
+// interpolate from lie in a 3x3x3 box around (i>>1, j>>1, k>>1); box entry
+// (x, y, z) is loaded only when one of the six needs it (7 to 12 values).
+
+// coarse offset (relative to fine index >> 1) and oddness of the fine index
+// whose parity is par, displaced by d in {-1, 0, 1}
+__host__ __device__ constexpr int fuse_lo(int par, int d) { return (par + d + 2) / 2 - 1; }
+__host__ __device__ constexpr int fuse_odd(int par, int d) { return (par + d + 2) & 1; }
+
+// does the neighbour at fine displacement (dx, dy, dz) interpolate from box
+// entry (x, y, z) (entries -1..1 per axis)?
+__host__ __device__ constexpr bool fuse_uses(int px, int py, int pz, int dx, int dy, int dz, int x, int y, int z) {
+    return (x == fuse_lo(px, dx) || (fuse_odd(px, dx) && x == fuse_lo(px, dx) + 1)) &&
+           (y == fuse_lo(py, dy) || (fuse_odd(py, dy) && y == fuse_lo(py, dy) + 1)) &&
+           (z == fuse_lo(pz, dz) || (fuse_odd(pz, dz) && z == fuse_lo(pz, dz) + 1));
+}
+
+__host__ __device__ constexpr bool fuse_needed(int px, int py, int pz, int x, int y, int z) {
+    return fuse_uses(px, py, pz, -1, 0, 0, x, y, z) || fuse_uses(px, py, pz, 1, 0, 0, x, y, z) ||
+           fuse_uses(px, py, pz, 0, -1, 0, x, y, z) || fuse_uses(px, py, pz, 0, 1, 0, x, y, z) ||
+           fuse_uses(px, py, pz, 0, 0, -1, x, y, z) || fuse_uses(px, py, pz, 0, 0, 1, x, y, z);
+}
+
+// (P e) at the fine neighbour (dx, dy, dz) from the box B[z + 1][y + 1][x + 1]
+template <int PX, int PY, int PZ, int DX, int DY, int DZ>
+__device__ __forceinline__ float fuse_interp(const float (&B)[3][3][3]) {
+    constexpr int lx = fuse_lo(PX, DX) + 1, ly = fuse_lo(PY, DY) + 1, lz = fuse_lo(PZ, DZ) + 1;
+    constexpr bool ox = fuse_odd(PX, DX), oy = fuse_odd(PY, DY), oz = fuse_odd(PZ, DZ);
+    float row[2];
+#pragma unroll
+    for (int x = 0; x < (ox ? 2 : 1); x++) {
+        float lo = oy ? 0.5f * (B[lz][ly][lx + x] + B[lz][ly + 1][lx + x]) : B[lz][ly][lx + x];
+        if (oz) {
+            const float hi = oy ? 0.5f * (B[lz + 1][ly][lx + x] + B[lz + 1][ly + 1][lx + x]) : B[lz + 1][ly][lx + x];
+            lo = 0.5f * (lo + hi);
+        }
+        row[x] = lo;
+    }
+    return ox ? 0.5f * (row[0] + row[1]) : row[0];
+}
+
+template <int PX, int PY, int PZ, bool HARM>
+__device__ __forceinline__ void prolong_smooth_point32(const Geom &g, float *u, const float *f, const float *Dh,
+                                                       const float *mu, const Geom &gc, const float *e, int p, int xm,
+                                                       int i, int j, int k) {
+    const int sy = g.sy, sz = (int)g.sz;
+    const int I = (i >> 1) - 1, J = (j >> 1) - 1, K = (k >> 1) - 1;
+    const int csy = gc.sy, csz = (int)gc.sz;
+    float B[3][3][3];
+#pragma unroll
+    for (int z = 0; z < 3; z++)
+#pragma unroll
+        for (int y = 0; y < 3; y++)
+#pragma unroll
+            for (int x = 0; x < 3; x++) {
+                if (!fuse_needed(PX, PY, PZ, x - 1, y - 1, z - 1)) continue;
+                const int X = I + x;
+                const int q = (K + z) * csz + (J + y) * csy + (X & 1) * gc.hx + (X >> 1);
+                gc.check(q);
+                B[z][y][x] = __ldg(e + q);
+            }
+    float a[6];
+    couplings32<HARM>(Dh, p, xm, sy, sz, a);
+    const float v0 = u[p + xm] + fuse_interp<PX, PY, PZ, -1, 0, 0>(B);
+    const float v1 = u[p + xm + 1] + fuse_interp<PX, PY, PZ, 1, 0, 0>(B);
+    const float v2 = u[p - sy] + fuse_interp<PX, PY, PZ, 0, -1, 0>(B);
+    const float v3 = u[p + sy] + fuse_interp<PX, PY, PZ, 0, 1, 0>(B);
+    const float v4 = u[p - sz] + fuse_interp<PX, PY, PZ, 0, 0, -1>(B);
+    const float v5 = u[p + sz] + fuse_interp<PX, PY, PZ, 0, 0, 1>(B);
+    // the pairing of coupled_sum32
+    float s0 = fmaf(a[0], v0, f[p]);
+    float s1 = a[2] * v2;
+    float s2 = a[4] * v4;
+    s0 = fmaf(a[1], v1, s0);
+    s1 = fmaf(a[3], v3, s1);
+    s2 = fmaf(a[5], v5, s2);
+    const float s = (s0 + s1) + s2;
+    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
+    u[p] = __fdividef(s, dg);
+}
+
+// u: fine level (its colour-`color` vertices updated, the other colour left
+// stale for the next half-sweep to overwrite); e: the coarse correction, zero
+// on the coarse boundary.
+template <bool HARM, bool BATCH>
+__global__ void __launch_bounds__(256) k_prolong_smooth32(Geom g, float *__restrict__ u, const float *__restrict__ f,
+                                                          VertCoef<float, HARM> c, Geom gc,
+                                                          const float *__restrict__ e, int color, const int *act) {
+    long long base;
+    int p, xm;
+    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
+    int k, smp = 0;
+    if (BATCH) smp = zsplit(g, kInterior, k);
+    else k = blockIdx.z;
+    k += 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - ((color + j + k) & 1);
+    u += base;
+    f += base;
+    e += BATCH ? (long long)smp * gc.sb : 0;
+    const float *Dh = c.Dh + base, *mu = c.mu + base;
+    switch ((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) {
+    case 0: prolong_smooth_point32<0, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 1: prolong_smooth_point32<1, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 2: prolong_smooth_point32<0, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 3: prolong_smooth_point32<1, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 4: prolong_smooth_point32<0, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 5: prolong_smooth_point32<1, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    case 6: prolong_smooth_point32<0, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    default: prolong_smooth_point32<1, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    }
+}
+
 // Full weighting of a defect that vanishes on one colour: fine vertex
 // (2I+a, 2J+b, 2K+c) has colour (a+b+c) mod 2, so only the 13 (PAR = 0: centre
 // and edges) or 14 (PAR = 1: faces and corners) offsets of that parity carry a
@@ -1065,16 +1195,26 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, const double *__restrict__
     if (mubar) mubar += o;
     long long p = g.pos(i, j, k);
     double uv = u[p], lv = lam[p];
-    double dv = harm ? D[p] : 0.0;
     double s = 0.0;
     Nbr n = neighbours(g, i);
     bool ok[6] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1, k > 0, k < g.nz - 1};
+    if (harm) {
+        const double dv = D[p];
 #pragma unroll
-    for (int q = 0; q < 6; q++) {
-        if (!ok[q]) continue;
-        long long r = p + n.o[q];
-        double w = harm ? face_da(dv, D[r], 1) : 0.5;
-        s = fma(w * (lv - lam[r]), uv - u[r], s);
+        for (int q = 0; q < 6; q++) {
+            if (!ok[q]) continue;
+            long long r = p + n.o[q];
+            s = fma(face_da(dv, D[r], 1) * (lv - lam[r]), uv - u[r], s);
+        }
+    } else {
+        // dface/dD_v = 1/2 on every face: factored out of the sum (3 FP64 ops per face)
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            if (!ok[q]) continue;
+            long long r = p + n.o[q];
+            s = fma(lv - lam[r], uv - u[r], s);
+        }
+        s *= 0.5;
     }
     if (Dbar) Dbar[p] = -s * ih2;
     if (mubar) mubar[p] = -lv * uv;

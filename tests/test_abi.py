@@ -43,6 +43,7 @@ def test_library_is_built_for_sm_103a(dmg):
 def test_default_params_and_strerror(dmg):
     p = dmg.dmg_default_params()
     assert (p.nu1, p.nu2, p.max_cycles, p.rtol, p.precision, p.inner_cycles) == (2, 2, 100, 1e-10, 0, 3)
+    assert (p.batch, p.autotune, p.split_prolong) == (1, 0, 0)
     assert dmg.dmg_strerror(dmg.DMG_OK) == "ok"
     assert dmg.dmg_strerror(dmg.DMG_ENOCONV) == "did not converge"
 
@@ -57,6 +58,7 @@ def test_default_params_and_strerror(dmg):
     dict(nx=9, ny=9, nz=9, h=1.0, rtol=0.0),
     dict(nx=9, ny=9, nz=9, h=1.0, max_cycles=0),
     dict(nx=9, ny=9, nz=9, h=1.0, inner_cycles=0),
+    dict(nx=9, ny=9, nz=9, h=1.0, split_prolong=2),
     dict(nx=65, ny=257, nz=257, h=1.0),              # coarsens to 3x9x9: fine; 7x7x513 is not
     dict(nx=7, ny=7, nz=513, h=1.0),                 # 7 -> 4 stops coarsening at 4x4x257: 1020 unknowns
 ])
