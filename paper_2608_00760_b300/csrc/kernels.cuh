@@ -717,12 +717,19 @@ __device__ __forceinline__ VertCoef<T, H, false> stage_coef(const VertCoef<T, H,
     return VertCoef<T, H, false>{dh, mu};
 }
 
+// The vertices of one colour only: 2^lx slots per interior row (2^lx >= the
+// colour's ceil(nxi / 2) vertices in a row), slot x of row (j, k) being
+// i = 2x + 2 - parity as in the grid kernels; one division per slot.
 template <class T, class CS>
 __device__ __forceinline__ void tail_half(const Geom &g, T *u, const T *f, const CS &c, int color) {
-    const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
-        if (((i + j + k) & 1) == color) smooth_point(g, u, f, c, i, j, k);
+    const int nxi = g.nx - 2, nyi = g.ny - 2;
+    int lx = 0;
+    while ((1 << lx) < (nxi + 1) / 2) lx++;
+    const int nslot = (nyi * (g.nz - 2)) << lx;
+    for (int s = threadIdx.x; s < nslot; s += blockDim.x) {
+        const int row = s >> lx, k = row / nyi + 1, j = row - (k - 1) * nyi + 1;
+        const int i = 2 * (s & ((1 << lx) - 1)) + 2 - ((color + j + k) & 1);
+        if (i <= g.nx - 2) smooth_point(g, u, f, c, i, j, k);
     }
     __syncthreads();
 }
