@@ -43,6 +43,16 @@ constexpr int kNormBlocks = 148 * 4;
 constexpr long long kTailMaxInterior[2] = {512, 4096};
 constexpr size_t kTailSmemBudget = 200 * 1024;
 
+// ceil(2^32 / d) for dmgk::mdiv (0 for d <= 1)
+inline unsigned magic_div(int d) {
+    return d <= 1 ? 0u : (unsigned)(((1ULL << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+
+inline dmgk::TailDiv tail_div(const Geom &g) {
+    return dmgk::TailDiv{magic_div(g.nx), magic_div(g.ny), magic_div(g.nx - 2), magic_div(g.ny - 2),
+                         magic_div(g.nx - 1), magic_div(g.ny - 1)};
+}
+
 // unpadded split-row geometry of a level staged in shared memory
 inline Geom smem_geom(const Geom &g) {
     Geom s = g;
@@ -535,6 +545,7 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
             a.L[l].u = U<T>(lv);
             a.L[l].f = F<T>(lv);
             a.L[l].c = make_coef(lv, cf0);
+            a.L[l].dv = tail_div(lv.g);
         }
         a.Ainv = AINV<T>(c);
         a.nc = c->nc;

@@ -668,12 +668,34 @@ __global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const 
 
 constexpr int kTailMaxLevels = 10;
 
+// floor(t / d) by one multiply: m = ceil(2^32 / d) (0 for d = 1), exact for
+// t, d < 2^16 (every tail index is below 2^16)
+__device__ __forceinline__ int mdiv(int t, unsigned m) {
+    DMG_CHECK(t >= 0 && t < 65536);
+    return m ? (int)__umulhi((unsigned)t, m) : t;
+}
+
+// magic divisors of one tail level for its index loops: vertices per row and
+// per column (nx, ny), interior ones (nx - 2, ny - 2) and cells (nx - 1, ny - 1)
+struct TailDiv {
+    unsigned nx, ny, nxi, nyi, cx, cy;
+};
+
+// (i, j, k) = (t mod a, (t / a) mod b, t / (a b)) with ma, mb the magic divisors of a, b
+__device__ __forceinline__ void tail_decode(int t, int a, unsigned ma, int b, unsigned mb, int &i, int &j, int &k) {
+    const int row = mdiv(t, ma);
+    i = t - row * a;
+    k = mdiv(row, mb);
+    j = row - k * b;
+}
+
 template <class T, class C>
 struct TailLevel {
     Geom g;      // global geometry
     Geom gs;     // shared-memory geometry (hx = number of x positions of one parity)
     T *u, *f;    // global u and f (used for the first tail level)
     C c;         // global coefficients
+    TailDiv dv;  // magic divisors of the loops over this level
 };
 
 template <class T, class C>
@@ -691,12 +713,13 @@ struct TailArgs {
 // shared-memory coefficient copies
 template <class T>
 __device__ __forceinline__ FaceCoef<T, false> stage_coef(const FaceCoef<T, true> &cg, const Geom &g, const Geom &gs,
-                                                         T *&cur) {
+                                                         const TailDiv &dv, T *&cur) {
     const int n = (int)(gs.sz * gs.nz);
     T *cx = cur, *cy = cur + n, *cz = cur + 2 * n, *dg = cur + 3 * n, *iv = cur + 4 * n;
     cur += 5 * n;
     for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-        const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+        int i, j, k;
+        tail_decode(t, g.nx, dv.nx, g.ny, dv.ny, i, j, k);
         const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
         cx[ps] = cg.cx[pg]; cy[ps] = cg.cy[pg]; cz[ps] = cg.cz[pg]; dg[ps] = cg.diag[pg]; iv[ps] = cg.invd[pg];
     }
@@ -705,12 +728,13 @@ __device__ __forceinline__ FaceCoef<T, false> stage_coef(const FaceCoef<T, true>
 
 template <class T, bool H>
 __device__ __forceinline__ VertCoef<T, H, false> stage_coef(const VertCoef<T, H, true> &cg, const Geom &g,
-                                                            const Geom &gs, T *&cur) {
+                                                            const Geom &gs, const TailDiv &dv, T *&cur) {
     const int n = (int)(gs.sz * gs.nz);
     T *dh = cur, *mu = cur + n;
     cur += 2 * n;
     for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-        const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+        int i, j, k;
+        tail_decode(t, g.nx, dv.nx, g.ny, dv.ny, i, j, k);
         const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
         dh[ps] = cg.Dh[pg]; mu[ps] = cg.mu[pg];
     }
@@ -721,13 +745,14 @@ __device__ __forceinline__ VertCoef<T, H, false> stage_coef(const VertCoef<T, H,
 // colour's ceil(nxi / 2) vertices in a row), slot x of row (j, k) being
 // i = 2x + 2 - parity as in the grid kernels; one division per slot.
 template <class T, class CS>
-__device__ __forceinline__ void tail_half(const Geom &g, T *u, const T *f, const CS &c, int color) {
+__device__ __forceinline__ void tail_half(const Geom &g, const TailDiv &dv, T *u, const T *f, const CS &c,
+                                          int color) {
     const int nxi = g.nx - 2, nyi = g.ny - 2;
     int lx = 0;
     while ((1 << lx) < (nxi + 1) / 2) lx++;
     const int nslot = (nyi * (g.nz - 2)) << lx;
     for (int s = threadIdx.x; s < nslot; s += blockDim.x) {
-        const int row = s >> lx, k = row / nyi + 1, j = row - (k - 1) * nyi + 1;
+        const int row = s >> lx, k = mdiv(row, dv.nyi) + 1, j = row - (k - 1) * nyi + 1;
         const int i = 2 * (s & ((1 << lx) - 1)) + 2 - ((color + j + k) & 1);
         if (i <= g.nx - 2) smooth_point(g, u, f, c, i, j, k);
     }
@@ -737,7 +762,7 @@ __device__ __forceinline__ void tail_half(const Geom &g, T *u, const T *f, const
 // one block per sample
 template <class T, class C>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
-    using CS = decltype(stage_coef(a.L[0].c, a.L[0].g, a.L[0].gs, *(T **)nullptr));
+    using CS = decltype(stage_coef(a.L[0].c, a.L[0].g, a.L[0].gs, a.L[0].dv, *(T **)nullptr));
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int smp = blockIdx.x;
     if (inactive(a.act, smp)) return;
@@ -748,15 +773,18 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
         const int n = (int)(a.L[l].gs.sz * a.L[l].gs.nz);
         su[l] = cur; sf[l] = cur + n; sr[l] = cur + 2 * n;
         cur += 3 * n;
-        for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) su[l][t] = T(0);
-        sc[l] = stage_coef(a.L[l].c.shifted(smp * a.L[l].g.sb), a.L[l].g, a.L[l].gs, cur);
+        // u starts at zero (boundary included); f and r are read on interior
+        // vertices only, after they are written there
+        for (int t = threadIdx.x; t < n; t += blockDim.x) su[l][t] = T(0);
+        sc[l] = stage_coef(a.L[l].c.shifted(smp * a.L[l].g.sb), a.L[l].g, a.L[l].gs, a.L[l].dv, cur);
     }
     T *fs = cur;   // coarsest right-hand side for the dense solve
     {
         const Geom &g = a.L[0].g, &gs = a.L[0].gs;
         __syncthreads();
         for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-            const int i = t % g.nx, j = (t / g.nx) % g.ny, k = t / (g.nx * g.ny);
+            int i, j, k;
+            tail_decode(t, g.nx, a.L[0].dv.nx, g.ny, a.L[0].dv.ny, i, j, k);
             sf[0][gs.pos(i, j, k)] = a.L[0].f[smp * g.sb + g.pos(i, j, k)];
             if (a.load_u) su[0][gs.pos(i, j, k)] = a.L[0].u[smp * g.sb + g.pos(i, j, k)];
         }
@@ -764,20 +792,25 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
     __syncthreads();
     for (int l = 0; l < a.nl - 1; l++) {
         const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
+        const TailDiv &dv = a.L[l].dv, &dvc = a.L[l + 1].dv;
         for (int sw = 0; sw < a.npre; sw++) {
-            tail_half(g, su[l], sf[l], sc[l], a.pre_first);
-            tail_half(g, su[l], sf[l], sc[l], 1 - a.pre_first);
+            tail_half(g, dv, su[l], sf[l], sc[l], a.pre_first);
+            tail_half(g, dv, su[l], sf[l], sc[l], 1 - a.pre_first);
         }
         const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
+            int i, j, k;
+            tail_decode(t, nxi, dv.nxi, nyi, dv.nyi, i, j, k);
+            i++, j++, k++;
             const long long p = g.pos(i, j, k);
             sr[l][p] = residual_at(su[l], sf[l], sc[l], p, neighbours(g, i));
         }
         __syncthreads();
         const int cxi = gc.nx - 2, cyi = gc.ny - 2, nc = cxi * cyi * (gc.nz - 2);
         for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-            const int I = t % cxi + 1, J = (t / cxi) % cyi + 1, K = t / (cxi * cyi) + 1;
+            int I, J, K;
+            tail_decode(t, cxi, dvc.nxi, cyi, dvc.nyi, I, J, K);
+            I++, J++, K++;
             restrict_point(g, sr[l], gc, sf[l + 1], I, J, K);
             su[l + 1][gc.pos(I, J, K)] = T(0);
         }
@@ -788,22 +821,26 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
     __syncthreads();
     for (int l = a.nl - 2; l >= 0; l--) {
         const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
+        const TailDiv &dv = a.L[l].dv, &dvc = a.L[l + 1].dv;
         const int cx = gc.nx - 1, cy = gc.ny - 1, ncell = cx * cy * (gc.nz - 1);
         for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-            const int I = t % cx, J = (t / cx) % cy, K = t / (cx * cy);
+            int I, J, K;
+            tail_decode(t, cx, dvc.cx, cy, dvc.cy, I, J, K);
             prolong_cell(gc, su[l + 1], g, su[l], I, J, K);
         }
         __syncthreads();
         for (int sw = 0; sw < a.npost; sw++) {
-            tail_half(g, su[l], sf[l], sc[l], a.post_first);
-            tail_half(g, su[l], sf[l], sc[l], 1 - a.post_first);
+            tail_half(g, dv, su[l], sf[l], sc[l], a.post_first);
+            tail_half(g, dv, su[l], sf[l], sc[l], 1 - a.post_first);
         }
     }
     // the first tail level's solution back to global memory (interior)
     const Geom &g = a.L[0].g, &gs = a.L[0].gs;
     const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int i = t % nxi + 1, j = (t / nxi) % nyi + 1, k = t / (nxi * nyi) + 1;
+        int i, j, k;
+        tail_decode(t, nxi, a.L[0].dv.nxi, nyi, a.L[0].dv.nyi, i, j, k);
+        i++, j++, k++;
         a.L[0].u[smp * g.sb + g.pos(i, j, k)] = su[0][gs.pos(i, j, k)];
     }
 }
