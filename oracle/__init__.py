@@ -42,9 +42,12 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle. The environment variable DMG_ORACLE_LIB names another
+    build of dmg_oracle.c to load instead; the mutation test uses it to run the
+    pins against copies with planted mistakes."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("DMG_ORACLE_LIB") or build())
         i, d, p = ctypes.c_int, ctypes.c_double, _dp
         sig = {
             "orc_face": (d, [d, d, i]),

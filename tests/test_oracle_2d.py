@@ -79,12 +79,27 @@ def test_transposed_cycle_is_the_exact_transpose(kw):
     assert np.abs(ST - S.T).max() <= 1e-13 * np.abs(S).max()
 
 
-def test_gradients_and_tangent_match_finite_differences():
+def test_first_half_sweep_updates_the_red_vertices():
+    # red = even i + j (Sec. 2.2): from u = 0, the colour-0 half-sweep changes
+    # exactly the interior vertices with i + j even, the colour-1 one the others
+    w = inputs.tissue2d(seed=85, shape=(9, 12))
+    ny, nx = w["shape"]
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    inner = (ii > 0) & (jj > 0) & (ii < nx - 1) & (jj < ny - 1)
+    f = np.abs(w["q"]) + 1.0
+    for colour in (0, 1):
+        u = np.zeros(w["shape"])
+        dmg2d.gs_half(w["D"], w["mu"], w["h"], f, u, colour)
+        assert np.array_equal(u != 0.0, inner & ((ii + jj) % 2 == colour))
+
+
+@pytest.mark.parametrize("harmonic", [False, True])
+def test_gradients_and_tangent_match_finite_differences(harmonic):
     w = inputs.tissue2d(seed=84, shape=(17, 17))
     D, mu, q, h = w["D"], w["mu"], w["q"], w["h"]
     rng = np.random.default_rng(2)
     wv = dmg2d._zero_boundary(rng.standard_normal(D.shape))
-    H = dmg2d.Hierarchy(D, mu, h)
+    H = dmg2d.Hierarchy(D, mu, h, harmonic=harmonic)
     u, _ = H.solve(q, rtol=1e-13)
     qb, Db, mb, _ = H.vjp(u, wv, rtol=1e-13)
     eps = 1e-6
@@ -93,8 +108,8 @@ def test_gradients_and_tangent_match_finite_differences():
         dq = rng.standard_normal(D.shape)
         dD = 0.1 * D * rng.standard_normal(D.shape)
         dm = 0.1 * mu * rng.standard_normal(D.shape)
-        up = dmg2d.direct_solve(D + eps * dD, mu + eps * dm, h, q + eps * dq)
-        um = dmg2d.direct_solve(D - eps * dD, mu - eps * dm, h, q - eps * dq)
+        up = dmg2d.direct_solve(D + eps * dD, mu + eps * dm, h, q + eps * dq, harmonic)
+        um = dmg2d.direct_solve(D - eps * dD, mu - eps * dm, h, q - eps * dq, harmonic)
         fd = (up - um) / (2 * eps)
         du, _ = H.jvp(u, dq, dD, dm, rtol=1e-13)
         assert np.linalg.norm(du - fd) <= 1e-7 * np.linalg.norm(fd)

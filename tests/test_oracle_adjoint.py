@@ -41,6 +41,21 @@ def test_brute_force_transpose(shape, m, harmonic):
     assert np.abs(S - S.T).max() > 1e-6 * scale
 
 
+@pytest.mark.parametrize("nu1,nu2,symmetric", [(1, 3, False), (3, 1, False), (1, 2, True)])
+def test_brute_force_transpose_with_unequal_sweep_counts(nu1, nu2, symmetric):
+    # the transposed cycle runs nu2 pre- and nu1 post-sweeps (Sec. 2.4); with
+    # nu1 != nu2 a cycle that kept the forward counts would not be the transpose
+    shape = (9, 5, 9)
+    w = inputs.unit_cube(shape=shape, seed=11)
+    H = oracle.Hierarchy(w["D"], w["mu"], w["h"], nu1=nu1, nu2=nu2, symmetric=symmetric)
+    S = explicit(lambda e: H.solve(e, fixed=2)[0], shape)
+    ST = explicit(lambda e: H.adjoint(e, fixed=2)[0], shape)
+    SL = explicit(lambda e: H.adjoint_literal(e, 2), shape)
+    scale = np.abs(S).max()
+    assert np.abs(ST - S.T).max() <= 1e-13 * scale
+    assert np.abs(SL - S.T).max() <= 1e-13 * scale
+
+
 def test_symmetric_schedule_special_case():
     # post-smoothing black->red with nu1 == nu2 makes the V-cycle symmetric: S_m^T = S_m
     w = inputs.unit_cube(shape=(9, 9, 9), seed=8)

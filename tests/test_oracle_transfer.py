@@ -68,6 +68,12 @@ def test_level_count_and_shapes():
     assert oracle.count_levels((129, 257, 257)) == 7
     assert oracle.count_levels((3, 3, 3)) == 1
     assert oracle.count_levels((33, 17, 9)) == 3
+    # coarsening stops as soon as any one axis cannot be halved (shapes are (nz, ny, nx))
+    assert oracle.count_levels((17, 10, 17)) == 1
+    assert oracle.count_levels((17, 17, 10)) == 1
+    assert oracle.count_levels((10, 17, 17)) == 1
+    assert oracle.count_levels((17, 3, 17)) == 1
+    assert oracle.count_levels((33, 5, 17)) == 2
     w = inputs.constant((129, 257, 257), 1.0)
     H = oracle.Hierarchy(w["D"][:3, :5, :5].copy(), w["mu"][:3, :5, :5].copy(), 1.0)
     assert H.nlev == 1
