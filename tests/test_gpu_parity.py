@@ -190,6 +190,38 @@ def test_mixed_matches_fp64_gpu_at_full_size(dmg, n):
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-8
 
 
+def test_full_size_mixed_certified_by_the_oracle(dmg):
+    # The 257^3 workload in the precision the bench times (mixed, rtol 1e-10).
+    # Properties that hold at any size, checked with the oracle's own arithmetic:
+    # the oracle's operator gives the forward, adjoint and tangent solutions a
+    # relative residual within rtol (plus FP64 rounding of the residual itself),
+    # and the oracle's gradient formula, applied vertex by vertex to the GPU's
+    # u and lambda = qbar, gives the GPU's Dbar and mubar.
+    n, h, rtol = 257, 0.5, 1e-10
+    w = inputs.tissue_torch((n, n, n), 10, h=h, device="cuda")
+    S = dmg.Solver(w["D"], w["mu"], h, precision=dmg.DMG_MIXED, rtol=rtol)
+    u = S.solve(w["q"])
+    qb, Db, mb = S.vjp(u, w["w"])
+    du = S.jvp(u, w["dq"], w["dD"], w["dmu"])
+    S.close()
+    D, mu, q, wv, dq, dD, dmu = (N(w[k]) for k in ("D", "mu", "q", "w", "dq", "dD", "dmu"))
+    u, lam, Db, mb, du = (N(x) for x in (u, qb, Db, mb, du))
+    inner = inputs.interior_mask((n, n, n))
+
+    def rel_residual(rhs, x):
+        r = (rhs - oracle.apply(D, mu, h, x)) * inner
+        return float(np.linalg.norm(r) / np.linalg.norm(rhs * inner))
+
+    bound = rtol * (1 + 1e-2) + 1e-12
+    assert rel_residual(q, u) <= bound
+    assert rel_residual(wv, lam) <= bound
+    assert rel_residual(dq - oracle.dA_apply(D, h, dD, dmu, u), du) <= bound
+    Dbr, mbr = oracle.grad(D, h, u, lam)
+    # plain numpy norms: numpy arrays also carry a .device attribute
+    assert np.linalg.norm(Db - Dbr) <= 1e-12 * np.linalg.norm(Dbr)
+    assert np.linalg.norm(mb - mbr) <= 1e-14 * np.linalg.norm(mbr)
+
+
 def test_host_pointers_give_device_results(dmg):
     w = make("unit_cube", dict(n=17), seed=6)
     S = dmg.Solver(w["D"], w["mu"], w["h"])            # numpy (host) coefficients
