@@ -49,3 +49,32 @@ def test_single_rank_defaults():
     import bench
     assert bench.max_over_ranks(1, 3.5) == 3.5
     assert bench.job_throughput(1, 20, 1000.0) == pytest.approx(20.0)
+
+
+def test_reference_arm_prints_one_complete_line():
+    # the oracle arm on a small grid: one JSON line with the contract's keys,
+    # the timed steps' own duration as ms_per_step, and host-only e2e bytes
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--size", "33", "--steps", "2",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["ms_per_step"] < d["ms_per_pair"] and abs(d["value"] - 1e3 / d["ms_per_pair"]) <= 1e-9 * d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    import subprocess
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--size", "33", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "{" not in r.stdout
