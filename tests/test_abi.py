@@ -100,3 +100,40 @@ def test_injected_allocation_failure_is_reported_without_a_device():
         dmg.dmg_debug_fail_alloc(0)
     assert st == dmg.DMG_ENOMEM and ctx is None
     assert "injected" in dmg.dmg_last_error(None)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    # the binding's mirrors of dmg_params and dmg_info must have the C layout:
+    # compile the header with gcc and compare the size and every field offset
+    import subprocess
+    from paper_2608_00760_b300 import dmg
+    lines = ['#include <stdio.h>', '#include "dmg.h"', "int main(void) {"]
+    for st in (dmg.dmg_params, dmg.dmg_info):
+        name = st.__name__
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in st._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for st in (dmg.dmg_params, dmg.dmg_info):
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
+    # and the same field names in the same order as the header declares
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dmg.h")).read(), flags=re.S)
+    for st in (dmg.dmg_params, dmg.dmg_info):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*%s;" % st.__name__, hdr).group(1)
+        names = []
+        for decl in body.split(";"):
+            decl = re.sub(r"\[[^]]*\]", "", decl).strip()
+            if decl:
+                names += [v.strip() for v in decl.split(None, 1)[1].split(",")]
+        assert names == [f for f, _ in st._fields_], st.__name__
