@@ -84,6 +84,7 @@ class Request:
     cycles: list = dataclasses.field(default_factory=list)
     rel: list = dataclasses.field(default_factory=list)
     outputs: dict = None
+    error: str = None          # why the request failed before it ran (see Server.run)
     pool_steps: tuple = None   # (step of the pool at admission, at completion)
 
     @property
@@ -131,13 +132,19 @@ class Pool:
             raise dmg.DMGError(st, dmg.dmg_last_error(self.ctx))
 
     def admit(self, req, now):
-        torch = self.torch
+        """Load the request into a free slot and stage its forward phase. If its
+        inputs cannot be made or the library refuses them, the slot goes back
+        to the free list and the exception propagates."""
         slot = self.free.pop()
-        with _dev.use(self.stream):
-            x = req.make_inputs(self.device)
-        self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=self.n))
-        self._check(dmg.dmg_slot_begin(self.ctx, slot, dmg.DMG_PHASE_FORWARD, x["q"], None, None, self.stream,
-                                       n=self.n))
+        try:
+            with _dev.use(self.stream):
+                x = req.make_inputs(self.device)
+            self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=self.n))
+            self._check(dmg.dmg_slot_begin(self.ctx, slot, dmg.DMG_PHASE_FORWARD, x["q"], None, None, self.stream,
+                                           n=self.n))
+        except Exception:
+            self.free.append(slot)
+            raise
         self.busy[slot] = [req, 0, x]
         req.t_admit = now
         req.pool_steps = (self.steps, None)
@@ -269,9 +276,13 @@ class Server:
     def _admit(self, queue, now):
         """FIFO per shape: the oldest waiting request of each shape is admitted
         when its pool has a free slot and its tensors fit the budget; a full
-        pool does not hold back requests of other shapes."""
+        pool does not hold back requests of other shapes. Returns the requests
+        that failed at admission (their inputs could not be made, or the
+        library refused them): they end at once with a status and a message,
+        and the others go on."""
         blocked = set()
         kept = collections.deque()
+        failed = []
         while queue:
             req = queue.popleft()
             pool = self.pools[tuple(req.shape)]
@@ -281,9 +292,17 @@ class Server:
                 blocked.add(req.shape)
                 kept.append(req)
                 continue
+            try:
+                pool.admit(req, now)
+            except Exception as e:   # noqa: BLE001 - one request's failure is reported, not raised
+                req.status = e.status if isinstance(e, dmg.DMGError) else dmg.DMG_EINVAL
+                req.error = "%s: %s" % (type(e).__name__, e)
+                req.t_admit = req.t_done = now
+                failed.append(req)
+                continue
             self.io_bytes += need
-            pool.admit(req, now)
         queue.extend(kept)
+        return failed
 
     def run(self, requests, realtime=True, keep_outputs=True):
         """Serve the requests (arrival times in seconds from the start). With
@@ -300,7 +319,7 @@ class Server:
             now = clock()
             while pending and (not realtime or pending[0].arrival <= now):
                 queue.append(pending.popleft())
-            self._admit(queue, now)
+            served += self._admit(queue, now)
             # each pool advances on its own: a finished step is taken and the
             # next one launched at once, so pools with short steps do not wait
             # for pools with long ones
@@ -310,7 +329,7 @@ class Server:
                     p.finish()
                     # slots freed by this step take waiting requests before the
                     # next step is launched, so they lose no step
-                    self._admit(queue, clock())
+                    served += self._admit(queue, clock())
                     moved = True
                 if not p.in_flight() and p.active():
                     p.launch()
@@ -335,8 +354,10 @@ class Server:
 
 
 def summarize(served, wall):
-    lat = [1e3 * (r.t_done - r.arrival) for r in served if r.t_done is not None]
+    """Rates over the requests that ended with DMG_OK; latency percentiles over
+    those requests too (arrival to the end of the read-back)."""
     ok = [r for r in served if r.status == dmg.DMG_OK]
+    lat = [1e3 * (r.t_done - r.arrival) for r in ok if r.t_done is not None]
     first = min((r.arrival for r in served), default=0.0)
     last = max((r.t_done for r in served if r.t_done is not None), default=wall)
     span = max(last - first, 1e-9)

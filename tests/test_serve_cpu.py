@@ -279,14 +279,15 @@ def test_memory_budget_bounds_the_admitted_requests(fake, monkeypatch):
     # pools take 4000 bytes; room for exactly two vjp requests' tensors
     srv = serve.Server([S1], budget_bytes=4000 + 2 * io + io // 2, device="cpu", slots={S1: 4})
     peak = [0]
-    admit = serve.Pool.admit
+    admit = serve.Server._admit
 
-    def tracking(self, r, now):
-        admit(self, r, now)
-        peak[0] = max(peak[0], srv.io_bytes)
-        assert srv.pool_bytes + srv.io_bytes <= srv.budget
+    def tracking(self, queue, now):
+        out = admit(self, queue, now)
+        peak[0] = max(peak[0], self.io_bytes)
+        assert self.pool_bytes + self.io_bytes <= self.budget
+        return out
 
-    monkeypatch.setattr(serve.Pool, "admit", tracking)
+    monkeypatch.setattr(serve.Server, "_admit", tracking)
     served, summ = srv.run([req(i, "vjp", S1, (2, 2)) for i in range(1, 7)], realtime=False)
     assert summ["ok"] == 6 and peak[0] == 2 * io and srv.io_bytes == 0
     # with room for two, six requests of four steps each take three rounds
@@ -316,3 +317,42 @@ def test_realtime_arrivals_and_dropped_outputs(fake):
     assert summ["ok"] == 10 and all(r.outputs is None for r in served)
     assert all(r.t_admit >= r.arrival and r.t_done > r.t_admit for r in served)
     assert summ["p50_ms"] > 0 and summ["p99_ms"] >= summ["p50_ms"]
+
+
+def test_a_request_that_fails_at_admission_ends_alone(fake):
+    abi = fake()
+    srv = serve.Server([S1], budget_bytes=1e9, device="cpu", slots={S1: 2})
+
+    def broken(device):
+        raise RuntimeError("no such sample")
+
+    bad = serve.Request(rid=9, kind="fwd", shape=S1, make_inputs=broken, arrival=0.0)
+    reqs = [req(1, "vjp", S1, (2, 2)), bad, req(2, "fwd", S1, (3,)), req(3, "jvp", S1, (1, 1))]
+    served, summ = srv.run(reqs, realtime=False)
+    by = {r.rid: r for r in served}
+    assert set(by) == {1, 2, 3, 9}
+    assert by[9].status == real_dmg.DMG_EINVAL and "no such sample" in by[9].error and by[9].outputs is None
+    assert all(by[r].status == real_dmg.DMG_OK and by[r].error is None for r in (1, 2, 3))
+    assert summ["ok"] == 3 and summ["requests"] == 4
+    # the slot it was offered went back to the pool, and its bytes were never counted
+    pool = srv.pools[S1]
+    assert sorted(pool.free) == [0, 1] and not pool.busy and srv.io_bytes == 0
+    assert [rid for rid, _ in abi.admissions] == [1, 2, 3]
+
+
+def test_a_refused_slot_load_ends_that_request_with_the_library_status(fake, monkeypatch):
+    abi = fake()
+    load = abi.dmg_slot_load
+
+    def refusing(ctx, slot, D, mu, stream=None, n=None):
+        if float(D.flatten()[0]) == 7.0:
+            return abi.DMG_ENOMEM
+        return load(ctx, slot, D, mu, stream, n)
+
+    monkeypatch.setattr(abi, "dmg_slot_load", refusing)
+    srv = serve.Server([S1], budget_bytes=1e9, device="cpu", slots={S1: 1})
+    served, summ = srv.run([req(7, "fwd", S1, (2,)), req(8, "fwd", S1, (2,))], realtime=False)
+    by = {r.rid: r for r in served}
+    assert by[7].status == real_dmg.DMG_ENOMEM and by[7].error.startswith("DMGError")
+    assert by[8].status == real_dmg.DMG_OK and by[8].pool_steps == (0, 2)
+    assert summ["ok"] == 1 and summ["p50_ms"] is not None
