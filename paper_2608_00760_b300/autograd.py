@@ -116,6 +116,11 @@ class _Cache:
     An entry holds weak references to the D and mu tensors it was built from and
     their versions; it matches only the same live tensor objects, unchanged (a
     new tensor that happens to reuse a freed address never matches).
+
+    Dropping an entry (eviction, dead tensors, clear) only drops the cache's
+    reference: an autograd graph that still needs the solver for its backward
+    or forward-mode rule keeps it alive, and the solver's context is destroyed
+    when the last reference goes (Solver.__del__).
     """
 
     def __init__(self, size=8):
@@ -132,12 +137,10 @@ class _Cache:
         self.items.append((weakref.ref(D), weakref.ref(mu), D._version, mu._version, key, s))
         self.items = [e for e in self.items if e[0]() is not None and e[1]() is not None or e[5] is s]
         while len(self.items) > self.size:
-            self.items.pop(0)[5].close()
+            self.items.pop(0)
         return s
 
     def clear(self):
-        for e in self.items:
-            e[5].close()
         self.items = []
 
 
