@@ -137,3 +137,33 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
             if decl:
                 names += [v.strip() for v in decl.split(None, 1)[1].split(",")]
         assert names == [f for f, _ in st._fields_], st.__name__
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(nx=9, ny=9, nz=9, h=float("inf")), "h must be > 0"),
+    (dict(nx=9, ny=9, nz=9, h=float("nan")), "h must be > 0"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, nu1=-1), "nu1, nu2"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, nu2=65), "nu1, nu2"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, fixed_cycles=-1), "fixed_cycles"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, coarsen=2), "bad coarsen"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, inner_cycles=17), "inner_cycles"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, symmetric=2), "symmetric"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, batch=0), "batch must be"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, autotune=-1), "autotune"),
+    (dict(nx=9, ny=9, nz=9, h=1.0, batch=7282), "batch * nz"),         # 7282 * 9 > 65535
+    (dict(nx=2049, ny=1025, nz=1025, h=1.0), "too large"),             # > 2^31 - 1 vertices
+    (dict(nx=1025, ny=1025, nz=1993, h=1.0), "padded sample"),         # < 2^31 vertices, padded rows beyond
+    (dict(nx=9, ny=9, nz=2, h=1.0), "3 vertices"),
+])
+def test_each_validation_rule_names_itself(dmg, bad, msg):
+    st, ctx = dmg.dmg_setup(dmg.dmg_default_params(**bad), 0, 0)
+    assert st == dmg.DMG_EINVAL and ctx is None
+    assert msg in dmg.dmg_last_error(None)
+
+
+def test_fixed_cycles_need_no_rtol(dmg):
+    # rtol is only checked when iterating to a tolerance: a fixed-count setup
+    # with rtol = 0 passes validation and fails later, at the missing device
+    # arrays (NULL coefficient pointers), not at rtol
+    st, ctx = dmg.dmg_setup(dmg.dmg_default_params(nx=9, ny=9, nz=9, h=1.0, fixed_cycles=15, rtol=0.0), 0, 0)
+    assert ctx is None and "rtol" not in dmg.dmg_last_error(None)
