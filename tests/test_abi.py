@@ -167,3 +167,31 @@ def test_fixed_cycles_need_no_rtol(dmg):
     # arrays (NULL coefficient pointers), not at rtol
     st, ctx = dmg.dmg_setup(dmg.dmg_default_params(nx=9, ny=9, nz=9, h=1.0, fixed_cycles=15, rtol=0.0), 0, 0)
     assert ctx is None and "rtol" not in dmg.dmg_last_error(None)
+
+
+def test_context_free_error_message_is_per_thread(dmg):
+    # dmg_last_error(NULL) reports the last failed context-free call of the
+    # calling thread: thread A fails, thread B fails with another message, and
+    # A still reads its own
+    import threading
+    bar = threading.Barrier(2)
+    seen = {}
+
+    def a():
+        dmg.dmg_setup(dmg.dmg_default_params(nx=9, ny=9, nz=9, h=1.0, symmetric=2), 0, 0)
+        bar.wait()
+        bar.wait()
+        seen["a"] = dmg.dmg_last_error(None)
+
+    def b():
+        bar.wait()
+        dmg.dmg_setup(dmg.dmg_default_params(nx=9, ny=9, nz=9, h=1.0, batch=0), 0, 0)
+        seen["b"] = dmg.dmg_last_error(None)
+        bar.wait()
+
+    ts = [threading.Thread(target=a), threading.Thread(target=b)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=60)
+    assert "symmetric" in seen["a"] and "batch" in seen["b"]
