@@ -73,10 +73,11 @@ def test_tangent_operator_matches_difference_of_operators(harmonic):
     assert np.abs(out - fd).max() <= tol * np.abs(fd).max()
 
 
-def test_jvp_vjp_duality_and_fd():
+@pytest.mark.parametrize("harmonic", [False, True])
+def test_jvp_vjp_duality_and_fd(harmonic):
     wl = inputs.tissue(9, seed=13)
     D, mu, h, q = wl["D"], wl["mu"], wl["h"], wl["q"]
-    H = oracle.Hierarchy(D, mu, h)
+    H = oracle.Hierarchy(D, mu, h, harmonic=harmonic)
     u, _, _ = H.solve(q, rtol=1e-13)
     du, _ = H.jvp(u, wl["dq"], wl["dD"], wl["dmu"], rtol=1e-13)
     qb, Db, mb, _ = H.vjp(u, wl["w"], rtol=1e-13)
@@ -85,7 +86,7 @@ def test_jvp_vjp_duality_and_fd():
     rhs = np.sum(qb[m] * wl["dq"][m]) + np.sum(Db * wl["dD"]) + np.sum(mb * wl["dmu"])
     assert lhs == pytest.approx(rhs, rel=1e-10)
     eps = 1e-5
-    up = oracle.direct_solve(D + eps * wl["dD"], mu + eps * wl["dmu"], h, q + eps * wl["dq"])
-    um = oracle.direct_solve(D - eps * wl["dD"], mu - eps * wl["dmu"], h, q - eps * wl["dq"])
+    up = oracle.direct_solve(D + eps * wl["dD"], mu + eps * wl["dmu"], h, q + eps * wl["dq"], harmonic)
+    um = oracle.direct_solve(D - eps * wl["dD"], mu - eps * wl["dmu"], h, q - eps * wl["dq"], harmonic)
     fd = (up - um) / (2 * eps)
     assert np.linalg.norm(du - fd) <= 1e-7 * np.linalg.norm(fd)

@@ -128,6 +128,18 @@ PY_MUTANTS = [
      "    if not inject:\n        out[1:-1, 1:-1, 1:-1]", "    if False:\n        out[1:-1, 1:-1, 1:-1]", _PU),
     ("unrolled.py", "directional derivative from the real part",
      "return float(np.sum(w * u).imag / eps)", "return float(np.sum(w * u).real / eps)", _PU),
+    ("__init__.py", "tangent right-hand side adds dA u instead of subtracting it",
+     "rhs = rhs - dA_apply(self.D, self.h, dD, dmu, u, self.harmonic)",
+     "rhs = rhs + dA_apply(self.D, self.h, dD, dmu, u, self.harmonic)", PINS),
+    ("__init__.py", "pull-back gradients ignore the harmonic face mean",
+     "Db, mb = grad(self.D, self.h, u, lam, self.harmonic)", "Db, mb = grad(self.D, self.h, u, lam, False)", PINS),
+    ("__init__.py", "tangent operator wrapper swaps the D and mu directions",
+     "_ptr(D), _ptr(dD), _ptr(dmu), _ptr(u),", "_ptr(D), _ptr(dmu), _ptr(dD), _ptr(u),", PINS),
+    ("__init__.py", "assembled matrix with the wrong sign",
+     "vals.append(col[nz_])", "vals.append(-col[nz_])", PINS),
+    ("__init__.py", "interior index includes the last plane of every axis",
+     "np.meshgrid(np.arange(1, nz - 1), np.arange(1, ny - 1), np.arange(1, nx - 1),",
+     "np.meshgrid(np.arange(1, nz), np.arange(1, ny), np.arange(1, nx),", PINS),
     ("__init__.py", "edge mask measures the distance to the lower face only",
      "dist = np.minimum(x, (n - 1) * h - x)", "dist = x", _PR),
     ("__init__.py", "edge mask drops voxels exactly at the edge depth",
