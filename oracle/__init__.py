@@ -12,7 +12,9 @@ all vertices, boundary planes included.
 Parity status: pinned. Each function is checked by CPU tests against something
 other than itself (closed-form eigenmodes, the PDE to O(h^2), a library sparse
 direct solve, trilinear interpolation by a library routine, brute-force
-transposes, finite differences); see ``tests/test_oracle_*.py``.
+transposes, finite differences); see ``tests/test_oracle_*.py``. The strength of
+those pins is itself tested: ``tests/test_oracle_mutants.py`` plants single
+mistakes in copies of this package and requires each to fail a pin.
 """
 from __future__ import annotations
 

@@ -40,7 +40,9 @@
  *
  * Parity status: every function here is pinned by a CPU test (closed-form
  * eigenmodes, the PDE itself to O(h^2), a library sparse direct solve,
- * brute-force transposes, finite differences, trilinear reproduction).
+ * brute-force transposes, finite differences, trilinear reproduction), and a
+ * mutation test compiles copies of this file with single planted mistakes and
+ * requires each copy to fail one of those pins.
  */
 #include <math.h>
 #include <stdlib.h>
