@@ -195,3 +195,23 @@ def test_context_free_error_message_is_per_thread(dmg):
     for t in ts:
         t.join(timeout=60)
     assert "symmetric" in seen["a"] and "batch" in seen["b"]
+
+
+def test_array_arguments_are_checked_before_any_call():
+    # the binding passes raw addresses, so it refuses what the C side would
+    # misread: other dtypes, strided views and wrong element counts
+    torch = pytest.importorskip("torch")
+    from paper_2608_00760_b300 import dmg
+    a = np.zeros((4, 5, 6))
+    assert dmg._ptr(a, 120) == a.ctypes.data and dmg._ptr(None) is None and dmg._ptr(1234) == 1234
+    for bad, n in ((a.astype(np.float32), 120), (a[:, :, ::2], 60), (a.T, 120), (a, 121)):
+        with pytest.raises(ValueError):
+            dmg._ptr(bad, n)
+    t = torch.zeros((4, 5, 6), dtype=torch.float64)
+    assert dmg._ptr(t, 120) == t.data_ptr()
+    for bad, n in ((t.float(), 120), (t.transpose(0, 2), 120), (t[:, :, ::2], 60), (t.to(torch.complex64), 120),
+                   (t, 7)):
+        with pytest.raises(ValueError):
+            dmg._ptr(bad, n)
+    with pytest.raises(TypeError):
+        dmg._ptr([0.0] * 120, 120)
