@@ -22,3 +22,10 @@ def test_fused_prolongation_box_covers_exactly_the_interpolation_supports(tmp_pa
     subprocess.check_call([_nvcc(), "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "host", "fuse_box.cu")])
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
+def test_split_row_layout_positions_and_neighbour_offsets(tmp_path):
+    exe = str(tmp_path / "geom_layout")
+    subprocess.check_call([_nvcc(), "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "host", "geom_layout.cu")])
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
