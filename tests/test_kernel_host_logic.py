@@ -29,3 +29,28 @@ def test_split_row_layout_positions_and_neighbour_offsets(tmp_path):
     subprocess.check_call([_nvcc(), "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "host", "geom_layout.cu")])
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
+def _extract_device_function(src, name):
+    """Source text of a __device__ __forceinline__ function of kernels.cuh, from
+    its signature to the closing brace at column 0."""
+    start = src.rindex("\n", 0, src.index(" %s(" % name)) + 1
+    end = src.index("\n}\n", start) + 3
+    return src[start:end]
+
+
+def test_mixed_precision_conversions_round_like_c(tmp_path):
+    # the conversions' own source, pasted into a host program (bit-cast stand-ins
+    # for the CUDA intrinsics) and compared with C's conversions
+    src = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "kernels.cuh")).read()
+    funcs = "\n".join(_extract_device_function(src, n) for n in ("exponent_of", "f64_to_f32_shift",
+                                                                 "f32_to_f64_shift"))
+    assert funcs.count("__device__ __forceinline__") == 3
+    tmpl = open(os.path.join(ROOT, "tests", "host", "bitconv_check.cpp")).read()
+    assert tmpl.count("// @EXTRACTED@") == 1
+    cpp = tmp_path / "bitconv.cpp"
+    cpp.write_text(tmpl.replace("// @EXTRACTED@", funcs))
+    exe = str(tmp_path / "bitconv")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
