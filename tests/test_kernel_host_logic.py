@@ -32,8 +32,8 @@ def test_split_row_layout_positions_and_neighbour_offsets(tmp_path):
 
 
 def _extract_device_function(src, name):
-    """Source text of a __device__ __forceinline__ function of kernels.cuh, from
-    its signature to the closing brace at column 0."""
+    """Source text of a function defined at column 0 in a CUDA source (from the
+    line of its signature to its closing brace at column 0)."""
     start = src.rindex("\n", 0, src.index(" %s(" % name)) + 1
     end = src.index("\n}\n", start) + 3
     return src[start:end]
@@ -51,6 +51,23 @@ def test_mixed_precision_conversions_round_like_c(tmp_path):
     cpp = tmp_path / "bitconv.cpp"
     cpp.write_text(tmpl.replace("// @EXTRACTED@", funcs))
     exe = str(tmp_path / "bitconv")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
+def test_tail_index_decoding_is_exact_division(tmp_path):
+    # the host's magic divisor and the kernel's multiply-high division and
+    # decode, their own source pasted into a host program
+    dev = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "kernels.cuh")).read()
+    host = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "dmg.cu")).read()
+    funcs = "\n".join([_extract_device_function(host, "magic_div")] +
+                      [_extract_device_function(dev, n) for n in ("mdiv", "tail_decode")])
+    assert funcs.count("magic_div(int d)") == 1 and funcs.count("__device__ __forceinline__") == 2
+    tmpl = open(os.path.join(ROOT, "tests", "host", "tail_decode_check.cpp")).read()
+    cpp = tmp_path / "tail_decode.cpp"
+    cpp.write_text(tmpl.replace("// @EXTRACTED@", funcs))
+    exe = str(tmp_path / "tail_decode")
     subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
