@@ -71,3 +71,25 @@ def test_tail_index_decoding_is_exact_division(tmp_path):
     subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
+def _extract_struct(src, name):
+    start = src.index("struct %s {" % name)
+    return src[start:src.index("\n};\n", start) + 4]
+
+
+def test_batch_plane_split_is_exact_division(tmp_path):
+    # the runtime's make_geom and the kernels' zsplit, their own source pasted
+    # into a host program
+    dev = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "kernels.cuh")).read()
+    host = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "dmg.cu")).read()
+    code = "\n".join([_extract_struct(dev, "Geom"), "enum { kInterior = 0, kCells = 1, kAll = 2 };",
+                      _extract_device_function(host, "make_geom"), _extract_device_function(dev, "zsplit")])
+    assert "Geom make_geom(int nx, int ny, int nz, int nb)" in code
+    tmpl = open(os.path.join(ROOT, "tests", "host", "zsplit_check.cpp")).read()
+    cpp = tmp_path / "zsplit.cpp"
+    cpp.write_text(tmpl.replace("// @EXTRACTED@", code))
+    exe = str(tmp_path / "zsplit")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
