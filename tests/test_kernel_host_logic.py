@@ -93,3 +93,21 @@ def test_batch_plane_split_is_exact_division(tmp_path):
     subprocess.check_call(["g++", "-std=c++17", "-O2", "-o", exe, str(cpp)])
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
+
+
+def test_fused_interpolation_is_bitwise_the_separate_prolongation(tmp_path):
+    # fuse_interp (with the box helpers) and prolong_cell, their own source
+    dev = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "kernels.cuh")).read()
+    a = dev.index("__host__ __device__ constexpr int fuse_lo")
+    b = dev.index("\n}\n", dev.index(" fuse_interp(")) + 3
+    pc = dev.index(" prolong_cell(")
+    start = dev.rindex("template <class T>", 0, pc)
+    code = "\n".join([_extract_struct(dev, "Geom"), dev[start:dev.index("\n}\n", pc) + 3], dev[a:b]])
+    assert code.count("fuse_interp(") == 1 and code.count("prolong_cell(") == 1
+    tmpl = open(os.path.join(ROOT, "tests", "host", "fuse_interp_check.cpp")).read()
+    cpp = tmp_path / "fuse_interp.cpp"
+    cpp.write_text(tmpl.replace("// @EXTRACTED@", code))
+    exe = str(tmp_path / "fuse_interp")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-o", exe, str(cpp)])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout
