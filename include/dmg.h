@@ -146,7 +146,9 @@ typedef struct {
     double hist[DMG_HIST_LEN];
 } dmg_info;
 
-/* Fills *p with the defaults listed above (nx = ny = nz = 0, h = 0). */
+/* Fills *p with the defaults listed above (nx = ny = nz = 0, h = 0): the V(2,2)
+   red-black schedule of Sec. 2.2 and the stopping rule of a 1e-10 relative
+   residual. p may be NULL (no effect). */
 void dmg_default_params(dmg_params *p);
 
 /*
@@ -251,7 +253,9 @@ dmg_status dmg_response_vjp(dmg_ctx *ctx, const double *u, const double *rbar, d
 
 /*
  * dmg_solve_vjp -- dmg_solve followed by dmg_vjp (converged adjoint) in one
- * call: u = S(q), then (qbar, Dbar, mubar) of <w, u>. The forward solution
+ * call: u = S(q) (Eq. 2), then (qbar, Dbar, mubar) of <w, u> through the
+ * transposed V-cycle (Sec. 2.4, Eq. 18). Fusing the two calls has no
+ * counterpart in the paper; it exists to overlap host transfers. The forward solution
  * stays on the device for the gradients, and host transfers run on a second
  * stream where they overlap the iterations: w is uploaded during the forward
  * solve, u is read out during the adjoint solve, qbar during the gradient
@@ -267,13 +271,18 @@ dmg_status dmg_solve_vjp(dmg_ctx *ctx, const double *q, const double *w, double 
 /*
  * dmg_residual -- out[2b] = ||q_b - A_b u_b||_2 and out[2b+1] = ||q_b||_2 over
  * interior vertices of every sample b, in FP64 (out is a host array of
- * 2 * batch doubles).
+ * 2 * batch doubles): the defect of Eqs. 13-14 on the finest level and the
+ * norms of the stopping rule. q and u: caller arrays as in dmg_solve (device or
+ * host, [batch][nz][ny][nx]). DMG_EINVAL for NULL arguments; synchronises the
+ * stream before returning.
  */
 dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *out,
                         void *stream);
 
 /*
- * dmg_batch_info -- per-sample report of the last solve/jvp/vjp on the context:
+ * dmg_batch_info -- per-sample report of the last solve/jvp/vjp on the context
+ * (the Monte Carlo samples of a variational-inference step, Sec. 2.5, each with
+ * its own coefficients; reporting per sample has no counterpart in the paper):
  * cycles[b] (V-cycles, or FP32 inner V-cycles in mixed mode) and rel[b] (final
  * relative residual; 0 for a zero right-hand side), host arrays of batch
  * entries each; either may be NULL. Before any such call every entry is 0.
@@ -281,7 +290,8 @@ dmg_status dmg_residual(dmg_ctx *ctx, const double *q, const double *u, double *
 dmg_status dmg_batch_info(const dmg_ctx *ctx, int *cycles, double *rel);
 
 /*
- * Slot-level interface (serving). A context set up with batch = S is also a
+ * Slot-level interface (serving; no counterpart in the paper, whose solver
+ * serves one call at a time). A context set up with batch = S is also a
  * pool of S slots for requests that arrive at different times: each slot holds
  * one request's coefficient hierarchy (kept resident while the request needs
  * it) and runs one phase at a time; every dmg_step_launch advances all running
@@ -338,19 +348,20 @@ dmg_status dmg_slot_result(const dmg_ctx *ctx, int slot, int *status, int *cycle
 dmg_status dmg_slot_read(dmg_ctx *ctx, int slot, double *u, double *x, double *Dbar, double *mubar,
                          void *stream);
 
-/* Testing hook (fault injection on the host): the n-th device allocation made
-   by the library from now on, process-wide, fails as if the device were out of
-   memory (the call that made it returns DMG_ENOMEM and releases what it had
-   allocated); n <= 0 turns it off. */
+/* Testing hook (fault injection on the host; no counterpart in the paper): the
+   n-th device allocation made by the library from now on, process-wide, fails
+   as if the device were out of memory (the call that made it returns
+   DMG_ENOMEM and releases what it had allocated); n <= 0 turns it off. */
 void dmg_debug_fail_alloc(long long n);
 
-/* Bounds-checked builds (compiled with -DDMG_BOUNDS_CHECK, the library's stand-in
-   for a memory checker): the number of device accesses counted outside their
-   arrays so far (every call also returns DMG_ECUDA when it added to it); -1 in
-   normal builds. */
+/* Testing hook, no counterpart in the paper. Bounds-checked builds (compiled
+   with -DDMG_BOUNDS_CHECK, the library's stand-in for a memory checker): the
+   number of device accesses counted outside their arrays so far (every call
+   also returns DMG_ECUDA when it added to it); -1 in normal builds. */
 long long dmg_debug_oob_count(void);
 
-/* Device memory held by the context, in bytes (for admission by memory budget). */
+/* Device memory held by the context, in bytes (for admission by memory budget;
+   no counterpart in the paper). 0 for NULL. */
 size_t dmg_device_bytes(const dmg_ctx *ctx);
 
 /*
@@ -380,7 +391,9 @@ size_t dmg_device_bytes(const dmg_ctx *ctx);
 dmg_status dmg_residual_static(const dmg_params *p, const double *D, const double *mu,
                                const double *q, const double *u, double *out, void *stream);
 
-/* Frees every resource of the context. NULL is accepted. */
+/* Frees every resource of the context (device and pinned host memory, streams,
+   events, graphs). NULL is accepted. The context must not be in use on any
+   stream; the call synchronises its own streams first. */
 dmg_status dmg_destroy(dmg_ctx *ctx);
 
 /* Static text for a status code. */
@@ -391,16 +404,20 @@ const char *dmg_strerror(dmg_status s);
    calling thread. */
 const char *dmg_last_error(const dmg_ctx *ctx);
 
-/* Number of hierarchy levels and the vertex counts of level l (0 = finest). */
+/* Number of hierarchy levels and the vertex counts of level l (0 = finest): the
+   grids of Sec. 2.2, h_l = 2^l h (Eq. 6). dmg_levels returns 0 for NULL;
+   dmg_level_shape returns DMG_EINVAL for NULL or a level out of range. */
 int dmg_levels(const dmg_ctx *ctx);
 dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int *nz);
 
 /* Thread-block shape (threads along the half-row, rows) of the colour kernels
-   on a level, FP32 (fp32 != 0) or FP64: 32 x 8 unless autotuned. */
+   on a level, FP32 (fp32 != 0) or FP64: 32 x 8 unless autotuned (no counterpart
+   in the paper). DMG_EINVAL for NULL or a level out of range. */
 dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 
 /*
- * Instrumentation (for benchmarks).
+ * Instrumentation (for benchmarks; no counterpart in the paper, which times
+ * whole calls).
  * dmg_launch_count: kernels this context has launched so far.
  * dmg_profile_begin(ctx, kernel, level): from now on, bracket every launch of
  *   `kernel` (a DMG_KERNEL_* id) on `level` with CUDA events on its stream;
