@@ -131,7 +131,7 @@ def load_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-# FP64 pipe rate measured on this machine's B300 with a dependent-chain-free DFMA
+# FP64 pipe rate measured on a B300 with a dependent-chain-free DFMA
 # loop (0.565e12 DFMA/s at 1.93 GHz, i.e. 2 DFMA/clk/SM x 148 SMs); used as the
 # ALU roofline of the FP64 kernels (ops = DFMA/DMUL instructions).
 FP64_OPS_PEAK = 0.565e12

@@ -1,5 +1,5 @@
 """The bounds-checked build (libdmg_check.so, compiled with -DDMG_BOUNDS_CHECK,
-the stand-in for a memory checker, which is closed on this machine): every
+the library's own stand-in for an external memory checker): every
 per-vertex body and colour kernel counts positions outside their arrays and
 sample indices outside the batch. A child process loads that build, runs the
 solver's paths on odd, thin, batched and 2D grids, and must see zero such
