@@ -382,7 +382,12 @@ size_t dmg_device_bytes(const dmg_ctx *ctx);
  * grid: (ny-2)*(nz-2) <= 262144 interior rows (513^3 fits); larger grids get
  * DMG_EINVAL with the reason in dmg_last_error(NULL).
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * cudaGetSymbolAddress and keeps it; make that first call before any stream
+ * capture. The kept address does not survive cudaDeviceReset(): do not use
+ * this entry point on a device after resetting it.
+ * The call never reads or clears the thread's last CUDA error: an error the
+ * caller left pending stays pending, and each CUDA call made here is checked
+ * by its own return value.
  * All calls share the one array: calls that overlap on the GPU (other streams
  * or host threads) race and must be serialised by the caller. Each call writes
  * every scratch slot it reads, so no clearing is needed between calls. The

@@ -45,15 +45,12 @@ std::mutex g_static_mu;
 double *g_static_ptr[DMG_STATIC_MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device, looked up once per
-// device. In host code the array's name is only a host-side handle; kernels
-// must be given this address.
-dmg_status static_scratch(double **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        dmg_detail_set_noctx_error("dmg_residual_static: cudaGetDevice failed");
-        return DMG_ECUDA;
-    }
+// device (the first call on that device) and kept for the life of the process.
+// In host code the array's name is only a host-side handle; kernels must be
+// given this address. A cudaDeviceReset() unloads the module that holds the
+// array, so the kept address would be stale afterwards: this entry point does
+// not support being used across a device reset.
+dmg_status static_scratch(int dev, double **out) {
     if (dev < 0 || dev >= DMG_STATIC_MAX_DEVICES) {
         dmg_detail_set_noctx_error("dmg_residual_static: device ordinal out of range");
         return DMG_EINVAL;
@@ -61,7 +58,7 @@ dmg_status static_scratch(double **out) {
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_ptr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, dmg_static_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, dmg_static_scratch);
         if (e != cudaSuccess || !p) {
             char m[256];
             snprintf(m, sizeof(m), "dmg_residual_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
@@ -145,12 +142,13 @@ __global__ void __launch_bounds__(256) k_static_final(double *scratch, int rows)
     }
 }
 
+// The runtime keeps one "last error" per host thread. This file never reads it
+// with cudaGetLastError(), which would also clear an error that the caller's
+// earlier, unrelated work left pending; every runtime call here is checked by
+// its own return value instead.
 bool on_current_device(const void *ptr, int dev) {
     cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) return false;
     return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
@@ -179,7 +177,6 @@ extern "C" dmg_status dmg_residual_static(const dmg_params *p, const double *D, 
     }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
         dmg_detail_set_noctx_error("dmg_residual_static: no CUDA device");
         return DMG_ECUDA;
     }
@@ -189,7 +186,7 @@ extern "C" dmg_status dmg_residual_static(const dmg_params *p, const double *D, 
         return DMG_EINVAL;
     }
     double *scratch = nullptr;
-    dmg_status st = static_scratch(&scratch);
+    dmg_status st = static_scratch(dev, &scratch);
     if (st != DMG_OK) return st;
     Grid g;
     g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
@@ -199,10 +196,14 @@ extern "C" dmg_status dmg_residual_static(const dmg_params *p, const double *D, 
     double s = harm ? 1.0 / (p->h * p->h) : 0.5 / (p->h * p->h);
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     // every slot the final kernel reads is written by k_static_rows first, so
-    // nothing has to be cleared between calls
-    k_static_rows<<<(unsigned)rows, 128, 0, cs>>>(g, D, mu, q, u, s, harm, scratch);
-    k_static_final<<<1, 256, 0, cs>>>(scratch, (int)rows);
-    cudaError_t e = cudaGetLastError();
+    // nothing has to be cleared between calls. Each launch is checked by the
+    // status cudaLaunchKernel returns for it.
+    const double *cD = D, *cmu = mu, *cq = q, *cu = u;
+    void *rows_args[] = {&g, &cD, &cmu, &cq, &cu, &s, &harm, &scratch};
+    cudaError_t e = cudaLaunchKernel((const void *)k_static_rows, dim3((unsigned)rows), dim3(128), rows_args, 0, cs);
+    int nrows = (int)rows;
+    void *final_args[] = {&scratch, &nrows};
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)k_static_final, dim3(1), dim3(256), final_args, 0, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, scratch + 2 * DMG_STATIC_MAX_ROWS, 2 * sizeof(double), cudaMemcpyDefault, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);

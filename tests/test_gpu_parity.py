@@ -41,9 +41,22 @@ def N(t):
 
 
 def rel(a, b):
-    a = N(a) if hasattr(a, "device") else a
+    a = N(a) if torch.is_tensor(a) else a
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def close(a, b, tol):
+    """Relative L2 error <= tol and, entry by entry, |a - b| <= tol max|b|: a
+    localised error (one boundary plane of Dbar, one colour, one corner) that
+    a whole-field norm would average away still fails the second bound."""
+    a = N(a) if torch.is_tensor(a) else np.asarray(a)
+    b = N(b) if torch.is_tensor(b) else np.asarray(b)
+    e2 = rel(a, b)
+    mb = float(np.max(np.abs(b))) if b.size else 0.0
+    einf = float(np.max(np.abs(a - b))) / (mb if mb > 0 else 1.0) if b.size else 0.0
+    assert e2 <= tol and einf <= tol, "relative L2 %.3e, max-entry %.3e, tolerance %.1e" % (e2, einf, tol)
+    return True
 
 
 WORKLOADS = [
@@ -70,10 +83,10 @@ def test_forward_and_vjp_converged(dmg, name, kw):
     H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
     ur, _, _ = H.solve(w["q"], rtol=1e-10)
     qbr, Dbr, mbr, _ = H.vjp(ur, w["w"], rtol=1e-10)
-    assert rel(u, ur) <= TOL_CONV
-    assert rel(qb, qbr) <= TOL_CONV
-    assert rel(Db, Dbr) <= TOL_CONV
-    assert rel(mb, mbr) <= TOL_CONV
+    assert close(u, ur, TOL_CONV)
+    assert close(qb, qbr, TOL_CONV)
+    assert close(Db, Dbr, TOL_CONV)
+    assert close(mb, mbr, TOL_CONV)
     # Dirichlet boundary: outputs are zero there, Dbar is not
     m = inputs.interior_mask(w["shape"])
     assert not N(u)[~m].any() and not N(qb)[~m].any() and not N(mb)[~m].any()
@@ -94,10 +107,31 @@ def test_fixed_cycles_match_oracle_schedule(dmg, name, kw, m):
     ur, _, _ = H.solve(w["q"], fixed=m)
     lam = H.adjoint(w["w"], fixed=m)[0]
     Dbr, mbr = oracle.grad(w["D"], w["h"], ur, lam)
-    assert rel(u, ur) <= TOL_SAME
-    assert rel(qb, lam) <= TOL_SAME
-    assert rel(Db, Dbr) <= TOL_SAME
-    assert rel(mb, mbr) <= TOL_SAME
+    assert close(u, ur, TOL_SAME)
+    assert close(qb, lam, TOL_SAME)
+    assert close(Db, Dbr, TOL_SAME)
+    assert close(mb, mbr, TOL_SAME)
+
+
+def test_fixed_cycles_match_oracle_schedule_129(dmg):
+    # 129^3: the FP64 cycle runs five grid levels (129, 65, 33, 17, 9) and the
+    # shared-memory tail below them; two cycles forward and two transposed
+    # cycles must be the oracle's schedule to rounding, entry by entry
+    w = make("tissue", dict(n=129), seed=12)
+    m = 2
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], fixed_cycles=m)
+    assert len(S.levels()) == 7
+    u = S.solve(T(w["q"]))
+    qb, Db, mb = S.vjp(u, T(w["w"]), cycles=m)
+    S.close()
+    H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
+    ur, _, _ = H.solve(w["q"], fixed=m)
+    lam = H.adjoint(w["w"], fixed=m)[0]
+    Dbr, mbr = oracle.grad(w["D"], w["h"], ur, lam)
+    assert close(u, ur, TOL_SAME)
+    assert close(qb, lam, TOL_SAME)
+    assert close(Db, Dbr, TOL_SAME)
+    assert close(mb, mbr, TOL_SAME)
 
 
 @pytest.mark.parametrize("opts", [dict(face_mean=1), dict(coarsen=1), dict(symmetric=1),
@@ -114,10 +148,10 @@ def test_schedule_options_match_oracle(dmg, opts):
     ur, _, _ = H.solve(w["q"], fixed=m)
     lam = H.adjoint(w["w"], fixed=m)[0]
     Dbr, mbr = oracle.grad(w["D"], w["h"], ur, lam, harmonic=bool(opts.get("face_mean", 0)))
-    assert rel(u, ur) <= TOL_SAME
-    assert rel(qb, lam) <= TOL_SAME
-    assert rel(Db, Dbr) <= TOL_SAME
-    assert rel(mb, mbr) <= TOL_SAME
+    assert close(u, ur, TOL_SAME)
+    assert close(qb, lam, TOL_SAME)
+    assert close(Db, Dbr, TOL_SAME)
+    assert close(mb, mbr, TOL_SAME)
 
 
 def test_count_matched_adjoint_dot_product(dmg):
@@ -145,9 +179,9 @@ def test_jvp_matches_oracle_and_duality(dmg):
     ref_q, _ = H.jvp(ur, w["dq"], rtol=1e-10)
     ref, _ = H.jvp(ur, w["dq"], w["dD"], w["dmu"], rtol=1e-10)
     ref_D, _ = H.jvp(ur, np.zeros(w["shape"]), w["dD"], None, rtol=1e-10)
-    assert rel(du_q, ref_q) <= TOL_CONV
-    assert rel(du, ref) <= TOL_CONV
-    assert rel(du_D, ref_D) <= TOL_CONV
+    assert close(du_q, ref_q, TOL_CONV)
+    assert close(du, ref, TOL_CONV)
+    assert close(du_D, ref_D, TOL_CONV)
     # <w, J t> = <J^T w, t> with both sides converged
     qb, Db, mb = S.vjp(u, T(w["w"]))
     msk = inputs.interior_mask(w["shape"])
@@ -166,10 +200,10 @@ def test_mixed_precision_matches_fp64_oracle(dmg):
     H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
     ur, _, _ = H.solve(w["q"], rtol=1e-10)
     qbr, Dbr, mbr, _ = H.vjp(ur, w["w"], rtol=1e-10)
-    assert rel(u, ur) <= TOL_CONV
-    assert rel(qb, qbr) <= TOL_CONV
-    assert rel(Db, Dbr) <= TOL_CONV
-    assert rel(mb, mbr) <= TOL_CONV
+    assert close(u, ur, TOL_CONV)
+    assert close(qb, qbr, TOL_CONV)
+    assert close(Db, Dbr, TOL_CONV)
+    assert close(mb, mbr, TOL_CONV)
 
 
 @pytest.mark.parametrize("n", [257, 513])
@@ -188,6 +222,7 @@ def test_mixed_matches_fp64_gpu_at_full_size(dmg, n):
         S.close()
     for a, b in zip(out[dmg.DMG_MIXED], out[dmg.DMG_FP64]):
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-8
+        assert float((a - b).abs().max() / b.abs().max()) <= 1e-8
 
 
 def test_full_size_mixed_certified_by_the_oracle(dmg):
@@ -244,14 +279,14 @@ def test_edge_cases(dmg):
     S = dmg.Solver(T(D), T(mu), 0.5, rtol=1e-14)
     u = S.solve(T(q))
     assert S.last_info.cycles == 1
-    assert rel(u, oracle.direct_solve(D, mu, 0.5, q)) <= 1e-14
+    assert close(u, oracle.direct_solve(D, mu, 0.5, q), 1e-14)
     # single-level anisotropic grid (3 x 5 x 9 vertices, 21 unknowns)
     D = np.exp(rng.standard_normal((3, 5, 9)))
     mu = np.full((3, 5, 9), 0.1)
     q = rng.uniform(size=(3, 5, 9))
     S = dmg.Solver(T(D), T(mu), 0.2, rtol=1e-13)
     assert S.levels() == [(3, 5, 9)]
-    assert rel(S.solve(T(q)), oracle.direct_solve(D, mu, 0.2, q)) <= 1e-13
+    assert close(S.solve(T(q)), oracle.direct_solve(D, mu, 0.2, q), 1e-13)
     # zero source: zero solution, zero cycles
     w = make("unit_cube", dict(n=9))
     S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"])
@@ -306,7 +341,7 @@ def test_tissue_129_converged(dmg):
     ur, _, _ = H.solve(w["q"], rtol=1e-10)
     qbr, Dbr, mbr, _ = H.vjp(ur, w["w"], rtol=1e-10)
     for a, b in ((u, ur), (qb, qbr), (Db, Dbr), (mb, mbr)):
-        assert rel(a, b) <= TOL_CONV
+        assert close(a, b, TOL_CONV)
 
 
 FUSED_SHAPES = [(65, 65, 65), (33, 49, 97), (129, 33, 65), (17, 33, 161), (9, 9, 257)]
@@ -316,8 +351,9 @@ FUSED_SHAPES = [(65, 65, 65), (33, 49, 97), (129, 33, 65), (17, 33, 161), (9, 9,
 @pytest.mark.parametrize("face_mean,nu", [(0, (2, 2)), (1, (2, 2)), (0, (3, 1))])
 def test_fp32_vcycle_matches_fp64_vcycle(dmg, shape, face_mean, nu):
     # one mixed refinement step is s * V32(q / s); one FP64 cycle is V64(q). The FP32
-    # V-cycle (fused TMA sweeps on the wide levels, ragged tiles and z-chunks
-    # included) must be the same linear map up to FP32 rounding.
+    # V-cycle (colour half-sweeps, the prolongation fused into the first
+    # post-smoothing half-sweep, ragged rows and planes included) must be the
+    # same linear map up to FP32 rounding.
     w = inputs.tissue(shape=shape, seed=8)
     kw = dict(max_cycles=1, strict=False, face_mean=face_mean, nu1=nu[0], nu2=nu[1])
     Sm = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=1, **kw)
@@ -328,7 +364,7 @@ def test_fp32_vcycle_matches_fp64_vcycle(dmg, shape, face_mean, nu):
             u6, _, _ = S6.vjp(None, T(w["w"]), need=(True, False, False))
         else:
             um, u6 = Sm.solve(T(w["q"])), S6.solve(T(w["q"]))
-        assert rel(um, N(u6)) <= 2e-6
+        assert close(um, N(u6), 2e-6)
 
 
 @pytest.mark.parametrize("shape", FUSED_SHAPES[:2])
@@ -341,13 +377,14 @@ def test_mixed_iterates_track_fp64_iterates(dmg, shape):
     S6 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"])
     um, u6 = Sm.solve(T(w["q"])), S6.solve(T(w["q"]))
     assert abs(Sm.last_info.outer - S6.last_info.cycles) <= 1
-    assert rel(um, N(u6)) <= 1e-12
+    assert close(um, N(u6), 1e-12)
     # three FP32 cycles per FP64 step (the default): same total cycle count, a third of the steps
     S3 = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED, inner_cycles=3)
     u3 = S3.solve(T(w["q"]))
     assert S3.last_info.cycles <= S6.last_info.cycles + 3
     assert S3.last_info.outer <= (S6.last_info.cycles + 2) // 3 + 1
-    assert S3.last_info.rel_residual <= 1e-10 and rel(u3, N(u6)) <= 1e-9
+    assert S3.last_info.rel_residual <= 1e-10
+    assert close(u3, N(u6), 1e-9)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -362,7 +399,7 @@ def test_long_thin_single_level_grid(dmg, precision):
     S = dmg.Solver(T(D), T(mu), 0.1, precision=precision, rtol=1e-12)
     assert S.levels() == [shape]
     u = S.solve(T(q))
-    assert rel(u, oracle.direct_solve(D, mu, 0.1, q)) <= 1e-10
+    assert close(u, oracle.direct_solve(D, mu, 0.1, q), 1e-10)
 
 
 # grids small enough that the single-CTA tail starts at the finest level
@@ -382,11 +419,11 @@ def test_tail_at_the_finest_level(dmg, shape, precision):
     ur, _, _ = H.solve(w["q"], rtol=1e-10)
     qr, Dr, mr, _ = H.vjp(ur, w["w"], rtol=1e-10)
     for got, ref in ((u, ur), (qb, qr), (Db, Dr), (mb, mr)):
-        assert rel(got, ref) <= TOL_CONV
+        assert close(got, ref, TOL_CONV)
     # the fixed-cycle FP64 iterate equals the oracle's m-cycle iterate (the same V-cycle)
     if precision == 0:
         S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], fixed_cycles=3)
         u3 = S.solve(T(w["q"]))
         S.close()
         ref3, _, _ = H.solve(w["q"], fixed=3)
-        assert rel(u3, ref3) <= 1e-11
+        assert close(u3, ref3, 1e-11)

@@ -1,11 +1,15 @@
 """Serving: forward, JVP and VJP requests of two grid shapes arrive while others
 run, are admitted into slots of per-shape pools as slots free up, and advance
-together step by step. Every served result must be bit for bit the result of
-the same request run alone on a context of batch 1; a request with invalid
+together step by step. Every served result must match the FP64 CPU oracle on
+the request's own coefficients and inputs (relative L2 and entry by entry
+<= 1e-8, both sides at relative residual 1e-10) and be bit for bit the result
+of the same request run alone on a context of batch 1; a request with invalid
 coefficients or non-finite input fails alone without disturbing the others.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -20,6 +24,32 @@ def serve():
     from paper_2608_00760_b300 import build, serve as m
     build.build()
     return m
+
+
+TOL_CONV = 1e-8
+
+
+def oracle_outputs(req, h=0.5):
+    """The request's outputs from the FP64 oracle, on the same inputs (drawn
+    again from the request's seed) and the same stopping rule."""
+    x = {k: v.detach().cpu().numpy() for k, v in req.make_inputs("cuda").items()}
+    H = oracle.Hierarchy(x["D"], x["mu"], h)
+    u, _, _ = H.solve(x["q"], rtol=1e-10)
+    if req.kind == "fwd":
+        return {"u": u}
+    if req.kind == "jvp":
+        du, _ = H.jvp(u, x["dq"], x["dD"], x["dmu"], rtol=1e-10)
+        return {"u": u, "du": du}
+    qb, Db, mb, _ = H.vjp(u, x["w"], rtol=1e-10)
+    return {"u": u, "qbar": qb, "Dbar": Db, "mubar": mb}
+
+
+def assert_close(got, ref, tol, what):
+    got = got.detach().cpu().numpy()
+    nb, mb = np.linalg.norm(ref), np.max(np.abs(ref))
+    e2 = np.linalg.norm(got - ref) / (nb if nb > 0 else 1.0)
+    einf = np.max(np.abs(got - ref)) / (mb if mb > 0 else 1.0)
+    assert e2 <= tol and einf <= tol, (what, e2, einf)
 
 
 def overlapped(served, shape):
@@ -44,6 +74,10 @@ def test_served_results_equal_alone(serve, precision):
     for s in SHAPES:
         assert overlapped(served, s), s
     for r in served:
+        ref = oracle_outputs(r)
+        assert set(ref) == set(r.outputs)
+        for k in ref:
+            assert_close(r.outputs[k], ref[k], TOL_CONV, (r.rid, r.kind, r.shape, k))
         alone = serve.run_alone(r, params=dict(precision=precision))
         assert set(alone) == set(r.outputs)
         for k in alone:
