@@ -45,18 +45,23 @@ UNIT = "fwd+VJP solves/s"
 N_SIDE = 257
 RTOL = 1e-10
 # Roofline unit: one RB-GS half-sweep launch on the finest level (one colour).
-# FP32 (vertex coefficients, split rows): per interior vertex of the grid it
-# reads f and mu of its own colour (2 + 2 B), D of every vertex (4 B), u of the
-# other colour (2 B) and writes u of its own colour (2 B): 12 B.
+# Algorithmic bytes (the survey's unit): a full FP32 red-black sweep must read
+# u, f, D and mu once and write u once, 20 B per interior vertex, so one
+# half-sweep is charged 10 B per interior vertex of the grid. The kernel as
+# built moves 12 B per vertex per half-sweep (f and mu of its own colour,
+# D of every vertex, u of the other colour, u written on its own colour); the
+# line reports the fraction in both units.
 # FP64 (precomputed faces): 6 FMA + 1 MUL per updated vertex = 3.5 FP64-pipe
-# operations per interior vertex of the grid, against the measured FP64 rate.
-HALF_SWEEP_BYTES_FP32 = 12.0
+# operations per interior vertex of the grid, against the FP64 FMA rate that
+# dmg_probe_fma measures on the device at the start of the run.
+HALF_SWEEP_BYTES_FP32 = 10.0
+HALF_SWEEP_BYTES_FP32_KERNEL = 12.0
 HALF_SWEEP_FP64_OPS = 3.5
 # DRAM bytes (read + write) of one finest-level half-sweep launch at 257^3,
-# from an ncu capture of the current kernel (profiles/rbgs_half_sweep_257.md)
+# from an ncu capture of the current kernel
 HALF_SWEEP_TRAFFIC = {"fp32": 200145920, "fp64": 664092672}
-# DRAM bytes per sample of one batched finest-level FP32 half-sweep at 129^3, from an ncu capture of 8 samples
-# (profiles/rbgs_half_sweep_257.md), scaled by the sample count
+# DRAM bytes per sample of one batched finest-level FP32 half-sweep at 129^3,
+# from an ncu capture of 8 samples, scaled by the sample count
 VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = 25872500
 
 
@@ -131,10 +136,28 @@ def load_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-# FP64 pipe rate measured on a B300 with a dependent-chain-free DFMA
-# loop (0.565e12 DFMA/s at 1.93 GHz, i.e. 2 DFMA/clk/SM x 148 SMs); used as the
-# ALU roofline of the FP64 kernels (ops = DFMA/DMUL instructions).
-FP64_OPS_PEAK = 0.565e12
+# FP64 FMA rate (FMA instructions per second) of the device, measured by
+# dmg_probe_fma at the start of every run (main()); the denominator of the FP64
+# kernels' roofline
+FP64_OPS_PEAK = [None]
+
+
+def host_info():
+    """The host's core count (all, and usable by this process) and CPU model."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count()
+    return dict(nproc=os.cpu_count(), usable=usable, cpu_model=model)
 
 
 def make_inputs(n, seed=0):
@@ -232,52 +255,76 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
 
 
 def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
-    """Same pairs through the C ABI with pinned HOST buffers: every step is one
-    dmg_solve_vjp call that copies q, w host->device and u, qbar, Dbar, mubar
-    device->host inside the call."""
+    """Same pairs through the C ABI with pinned HOST buffers. Streamed: one
+    dmg_solve_vjp_many call for all `steps` pairs, each pair's q, w copied
+    host->device and u, qbar, Dbar, mubar device->host inside the call (two
+    distinct pinned input and output sets, alternating between pairs, so every
+    pair moves its own bytes), with the transfers overlapped with the
+    neighbouring pairs' solves. Single: one dmg_solve_vjp call per pair."""
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, rtol=RTOL, inner_cycles=inner)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    qh, wh = pin(w["q"]), pin(w["w"])
-    uh, qbh, Dbh, mbh = (torch.empty(w["shape"], dtype=torch.float64).pin_memory() for _ in range(4))
+    qh = [pin(w["q"]), pin(w["q"] * 1.5)]
+    wh = [pin(w["w"]), pin(-w["w"])]
+    outs = [[torch.empty(w["shape"], dtype=torch.float64).pin_memory() for _ in range(2)] for _ in range(4)]
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        st = dmg.dmg_solve_vjp(S.ctx, qh, wh, uh, qbh, Dbh, mbh, None, None, stream, n=S.n)
+    def many(k):
+        st = dmg.dmg_solve_vjp_many(S.ctx, [qh[i % 2] for i in range(k)], [wh[i % 2] for i in range(k)],
+                                    *[[o[i % 2] for i in range(k)] for o in outs], stream=stream, n=S.n)
         assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
 
+    def single():
+        st = dmg.dmg_solve_vjp(S.ctx, qh[0], wh[0], outs[0][0], outs[1][0], outs[2][0], outs[3][0], None, None,
+                               stream, n=S.n)
+        assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+
+    many(2)   # allocates the staging buffers, warms up
     for _ in range(warmup):
-        step()
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        step()
-    torch.cuda.synchronize(dev)
-    el = time.perf_counter() - t0
-    barrier(world)
-    el = max_over_ranks(world, el)
+        single()
+    res = {}
+    for name, fn in (("streamed", lambda: many(steps)), ("single", lambda: [single() for _ in range(steps)])):
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        barrier(world)
+        res[name] = max_over_ranks(world, el)
     nbytes = 8 * int(np.prod(w["shape"]))
     S.close()
-    return dict(seconds=el, h2d=2 * nbytes, d2h=4 * nbytes)
+    return dict(seconds=res["streamed"], seconds_single=res["single"], h2d=2 * nbytes, d2h=4 * nbytes)
 
 
-def time_autograd_steps(dmg, torch, w, steps, warmup, world, local, inner, profile=False):
+def time_autograd_steps(dmg, torch, w, steps, warmup, world, local, inner, profile=False, w2=None):
     """Times `steps` VI steps through the torch.autograd.Function: u = solve(q; D, mu)
     for every sample, loss = sum <w, u>, loss.backward() -> gradients w.r.t. q,
-    D and mu (the transposed V-cycle plus the gradient kernel)."""
+    D and mu (the transposed V-cycle plus the gradient kernel). With w2: the
+    coefficients change every step (alternating between w's and w2's D, mu, as
+    a sampler's iterates do), and each step first rebuilds the hierarchy in place
+    (dmg_set_coefficients), inside the timed region."""
     from paper_2608_00760_b300 import autograd
     dev = torch.device("cuda", local)
     T = lambda a, g=False: torch.from_numpy(np.ascontiguousarray(a)).to(dev).requires_grad_(g)
     D, mu, q, wv = T(w["D"], True), T(w["mu"], True), T(w["q"], True), T(w["w"])
     S = dmg.Solver(D.detach(), mu.detach(), w["h"], precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=inner)
     stream = torch.cuda.current_stream(dev)
+    coeffs = None
+    if w2 is not None:
+        coeffs = [(D, mu), (T(w2["D"], True), T(w2["mu"], True))]
+    count = [0]
 
     def step():
-        for x in (D, mu, q):
+        Dk, muk = D, mu
+        if coeffs is not None:
+            Dk, muk = coeffs[count[0] % 2]
+            count[0] += 1
+            S.set_coefficients(Dk.detach(), muk.detach(), stream=stream)
+        for x in (Dk, muk, q):
             x.grad = None
-        u = autograd.DMGSolve.apply(q, D, mu, S, False)
+        u = autograd.DMGSolve.apply(q, Dk, muk, S, False)
         (u * wv).sum().backward()
 
     for _ in range(warmup):
@@ -320,6 +367,9 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
     one = {k: (w[k][0] if k in ("D", "mu", "q", "w") else w[k]) for k in w}
     one["shape"] = w["shape"][1:]
     r1 = time_autograd_steps(dmg, torch, one, 3 * steps, 3, world, local, args.inner)
+    w2 = inputs.vi_batch(n, B, seed=1, keys=("D", "mu"))
+    rr = time_autograd_steps(dmg, torch, w, steps, 3, world, local, args.inner, w2=w2)
+    del w2
     ms = res["total_ms"] / steps
     nint = B * (n - 2) ** 3
     out = dict(workload="VI step: %d tissue samples x %d^3 in one context; forward solve + backward through the "
@@ -332,7 +382,12 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
                                               rel_max=max(res["adj_rel"])),
                one_at_a_time=dict(value=world * 3 * steps / (r1["total_ms"] / 1e3), unit="samples/s",
                                   ms_per_sample=r1["total_ms"] / (3 * steps),
-                                  gpu_launches_per_sample=r1["launches"] / (3 * steps)))
+                                  gpu_launches_per_sample=r1["launches"] / (3 * steps)),
+               new_coefficients_every_step=dict(
+                   value=world * B * steps / (rr["total_ms"] / 1e3), unit="samples/s",
+                   ms_per_step=rr["total_ms"] / steps,
+                   note="each step first rebuilds every sample's coefficient hierarchy in place "
+                        "(dmg_set_coefficients, inside the timed region), alternating between two coefficient draws"))
     pr = res["prof"]
     if pr and pr["launches"]:
         dur = pr["total_ms"] / pr["launches"] / 1e3
@@ -341,9 +396,10 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
         pk = peaks.get("hbm_gbs", 6400.0)
         out["roofline"] = dict(kernel="rbgs_half_sweep_fp32_level0 (all samples)", bound="hbm", achieved=ach,
                                peak=pk, unit="GB/s", frac=ach / pk,
+                               frac_kernel_bytes=HALF_SWEEP_BYTES_FP32_KERNEL * nint / dur / 1e9 / pk,
                                traffic=VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 * B if n == 129 else None,
                                peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
-                               algorithmic_bytes=byt)
+                               algorithmic_bytes=byt, bytes_per_vertex=HALF_SWEEP_BYTES_FP32)
     return out
 
 
@@ -473,23 +529,73 @@ def run_2d(dmg, torch, args, world, local, peaks, peak_src):
             else:
                 ops = 2.5 * (n - 2) ** 2   # 4 FMA + 1 MUL per updated vertex
                 r["roofline"] = dict(kernel="rbgs_half_sweep_2d_fp64_level0", bound="alu",
-                                     achieved=ops / dur / 1e12, peak=FP64_OPS_PEAK / 1e12, unit="TFP64-op/s",
-                                     frac=ops / dur / FP64_OPS_PEAK, traffic=None, avg_us=dur * 1e6)
+                                     achieved=ops / dur / 1e12, peak=FP64_OPS_PEAK[0] / 1e12, unit="TFP64-op/s",
+                                     frac=ops / dur / FP64_OPS_PEAK[0], traffic=None, avg_us=dur * 1e6,
+                                     peak_source="dmg_probe_fma, measured in this run")
         out[prec] = r
+    return out
+
+
+def run_setup(dmg, torch, args, world, local):
+    """The cost of row a1 (the coefficient hierarchy): dmg_setup (allocation, hierarchy, coarsest inverse, no
+    autotuning), dmg_set_coefficients (the hierarchy rebuilt in place for new coefficients) and dmg_slot_load (one
+    slot of a serving pool), wall-clock around each synchronous call, median of 3 (setup) or 5 (rebuilds)."""
+    from paper_2608_00760_b300 import inputs
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    out = dict(note="milliseconds per call; setup includes every cudaMalloc of the context")
+
+    def med(fn, reps):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return float(np.median(ts))
+
+    sizes = [(257, "mixed"), (257, "fp64")] + ([(args.size_513, "mixed")] if args.size_513 > 0 else [])
+    for n, prec in sizes:
+        w = inputs.tissue_torch((n, n, n), 21, device=dev, keys=("D", "mu"))
+        p = dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64
+        holder = []
+
+        def setup():
+            holder.append(dmg.Solver(w["D"], w["mu"], 0.5, precision=p, autotune=0))
+
+        t_setup = med(setup, 3)
+        S = holder[-1]
+        for x in holder[:-1]:
+            x.close()
+        t_set = med(lambda: S.set_coefficients(w["D"], w["mu"], stream=stream), 5)
+        out["%d^3_%s" % (n, prec)] = dict(dmg_setup_ms=t_setup, dmg_set_coefficients_ms=t_set,
+                                          context_gb=dmg.dmg_device_bytes(S.ctx) / 1e9)
+        S.close()
+        del w
+    for n in (129, 257):
+        w = inputs.tissue_torch((n, n, n), 22, device=dev, keys=("D", "mu"))
+        prm = dmg.dmg_default_params(nx=n, ny=n, nz=n, h=0.5, batch=4, precision=dmg.DMG_MIXED)
+        ones = torch.ones((4, n, n, n), dtype=torch.float64, device=dev)
+        st, ctx = dmg.dmg_setup(prm, ones, ones, stream=stream)
+        del ones
+        assert st == dmg.DMG_OK, dmg.dmg_last_error(None)
+        nn = n ** 3
+        t_load = med(lambda: dmg.dmg_slot_load(ctx, 1, w["D"], w["mu"], stream, n=nn), 5)
+        out["slot_load_%d^3_mixed_ms" % n] = t_load
+        dmg.dmg_destroy(ctx)
+        del w
     return out
 
 
 SERVE_SHAPES = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
 
 
-def run_serving(dmg, torch, args, world, rank, local):
-    """The request stream: Poisson arrivals of forward, JVP and VJP requests
-    (1:1:2) on grids drawn uniformly from SERVE_SHAPES, tissue coefficients with
-    per-request seeds, served with continuous batching under the memory budget
-    (mixed precision, rtol 1e-10); then the same requests one at a time in FP64."""
+def serve_stream(dmg, torch, args, world, rank, local, rate, nreq):
+    """One served stream of nreq Poisson arrivals at `rate` per second (mixed precision, rtol 1e-10)."""
     from paper_2608_00760_b300 import serve
     dev = torch.device("cuda", local)
-    reqs = serve.poisson_stream(args.serve_requests, args.serve_rate, SERVE_SHAPES, seed=1000 + rank)
+    reqs = serve.poisson_stream(nreq, rate, SERVE_SHAPES, seed=1000 + rank)
     server = serve.Server(SERVE_SHAPES, budget_bytes=args.serve_budget_gb * 1e9, device=dev,
                           params=dict(precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=args.inner))
     try:
@@ -501,7 +607,27 @@ def run_serving(dmg, torch, args, world, rank, local):
         pool_gb = server.pool_bytes / 1e9
     finally:
         server.close()
+    return reqs, served, st, slots, pool_gb
+
+
+def run_serving(dmg, torch, args, world, rank, local):
+    """The request stream: Poisson arrivals of forward, JVP and VJP requests
+    (1:1:2) on grids drawn uniformly from SERVE_SHAPES, tissue coefficients with
+    per-request seeds, served with continuous batching under the memory budget
+    (mixed precision, rtol 1e-10); then the same requests one at a time in FP64."""
+    from paper_2608_00760_b300 import serve
+    dev = torch.device("cuda", local)
+    reqs, served, st, slots, pool_gb = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate,
+                                                     args.serve_requests)
     secs = max_over_ranks(world, st["seconds"])
+    low = None
+    if args.serve_rate_low > 0:
+        lreqs, lserved, lst, _, _ = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate_low,
+                                                 args.serve_requests)
+        lsecs = max_over_ranks(world, lst["seconds"])
+        low = dict(rate=args.serve_rate_low, value=world * sum(r.solves for r in lreqs) / lsecs
+                   if lst["ok"] == len(lreqs) else None, unit="solves/s", requests_per_s=world * lst["ok"] / lsecs,
+                   ok=lst["ok"], requests=len(lreqs), p50_ms=lst["p50_ms"], p99_ms=lst["p99_ms"], seconds=lsecs)
     t_alone = serve.run_one_at_a_time(reqs, params=dict(precision=dmg.DMG_FP64, rtol=RTOL), device=dev)
     t_alone = max_over_ranks(world, t_alone)
     nsolves = sum(r.solves for r in reqs)
@@ -514,20 +640,19 @@ def run_serving(dmg, torch, args, world, rank, local):
                 requests_per_s=world * st["ok"] / secs, ok=st["ok"], requests=len(reqs),
                 p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], seconds=secs,
                 slots=slots, pools_gb=pool_gb, cycles_mean=float(np.mean(cyc)) if cyc else None,
+                lower_rate=low,
                 one_at_a_time_fp64=dict(value=world * nsolves / t_alone, unit="solves/s",
                                         requests_per_s=world * len(reqs) / t_alone, seconds=t_alone,
                                         api="dmg_setup + dmg_solve/dmg_jvp/dmg_vjp per request, batch 1"))
 
 
-def cpu_baseline_sample(w, m_fwd, m_adj):
-    """Times the FP64 CPU oracle (single-threaded C) on a bounded sample of the
-    workload -- one forward V-cycle, one transposed V-cycle, the residual norm
-    and the coefficient gradients at the full grid -- and scales it to one
-    fwd+VJP pair of m_fwd + m_adj cycles."""
+def _oracle_sample_times(w):
+    """Times of the FP64 CPU oracle (single-threaded C) on one bounded sample of
+    a workload: one forward V-cycle, one residual norm, one transposed V-cycle
+    and one coefficient-gradient evaluation, at the full grid."""
     import oracle
     H = oracle.Hierarchy(w["D"], w["mu"], w["h"])
-    shape = w["shape"]
-    z = np.zeros(shape)
+    z = np.zeros(w["shape"])
     t0 = time.perf_counter()
     u1 = H.vcycle(w["q"], z)
     t1 = time.perf_counter()
@@ -537,12 +662,110 @@ def cpu_baseline_sample(w, m_fwd, m_adj):
     t3 = time.perf_counter()
     oracle.grad(w["D"], w["h"], u1, l1)
     t4 = time.perf_counter()
-    t_pair = m_fwd * (t1 - t0 + t2 - t1) + m_adj * (t3 - t2 + t2 - t1) + (t4 - t3)
-    sample = ("1 forward + 1 transposed V(2,2) cycle, 1 residual norm and 1 gradient evaluation of the FP64 "
-              "oracle at %s (%.1f s), scaled to %d + %d cycles per fwd+VJP pair" %
-              ("x".join(map(str, shape)), t4 - t0, m_fwd, m_adj))
-    return dict(value=1.0 / t_pair, unit=UNIT, cores=1, kind="oracle", sample=sample,
-                seconds_per_pair=t_pair)
+    return dict(fwd=t1 - t0, res=t2 - t1, adj=t3 - t2, grad=t4 - t3, total=t4 - t0)
+
+
+def _pair_seconds(t, m_fwd, m_adj):
+    """One fwd+VJP pair: m_fwd forward cycles and m_adj transposed cycles, each
+    followed by a residual norm, plus one gradient evaluation."""
+    return m_fwd * (t["fwd"] + t["res"]) + m_adj * (t["adj"] + t["res"]) + t["grad"]
+
+
+def _oracle_worker(path, h):
+    """One process of the all-core run: the bounded sample on the arrays saved at path."""
+    w = {k: np.load(os.path.join(path, k + ".npy"), mmap_mode="r") for k in ("D", "mu", "q", "w")}
+    w = {k: np.ascontiguousarray(v) for k, v in w.items()}
+    w["h"], w["shape"] = h, w["D"].shape
+    return _oracle_sample_times(w)
+
+
+def _all_core_processes(shape):
+    """Concurrent oracle processes for the all-core run: one per usable core,
+    as many as host memory holds (about 1.6 GB per process at 257^3)."""
+    cores = host_info()["usable"] or 1
+    per = 1.6e9 * float(np.prod(shape)) / 257 ** 3
+    avail = 8e9
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    avail = 1024.0 * float(line.split()[1])
+                    break
+    except Exception:
+        pass
+    return max(1, min(cores, int(0.6 * avail // per), 128))
+
+
+def cpu_baseline_leg(dmg, torch, w, m_fwd, m_adj, local, inner):
+    """The FP64 CPU oracle as it stands, on this host's cores (the reported CPU
+    baseline), plus the oracle's own check of the GPU path at 65^3.
+
+    * single thread: the bounded sample (one forward and one transposed
+      V-cycle, one residual norm, one gradient evaluation) at the full grid,
+      scaled to a fwd+VJP pair with the GPU run's cycle counts;
+    * all cores: the same sample in one process per usable core at once (the
+      oracle is single-threaded C; independent pairs are how a sampler would
+      use the host), throughput = sum of the processes' pair rates;
+    * the scaling is checked against a measured full pair of the oracle at
+      65^3 (predicted from the same per-cycle sample there);
+    * 65^3 parity (the tissue recipe's errors the configuration asks for):
+      the GPU's mixed and FP64 fwd+VJP results against the oracle's, relative
+      L2 and max-entry errors of u, qbar, Dbar, mubar."""
+    import multiprocessing as mp
+
+    import oracle
+    from paper_2608_00760_b300 import inputs
+    oracle.build()
+    host = host_info()
+    # single thread, full grid
+    t = _oracle_sample_times(w)
+    pair1 = _pair_seconds(t, m_fwd, m_adj)
+    # all cores, full grid
+    nproc = _all_core_processes(w["shape"])
+    with tempfile.TemporaryDirectory() as d:
+        for k in ("D", "mu", "q", "w"):
+            np.save(os.path.join(d, k + ".npy"), w[k])
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(nproc) as pool:
+            ts = pool.starmap(_oracle_worker, [(d, w["h"])] * nproc)
+        wall = time.perf_counter() - t0
+    rate_all = sum(1.0 / _pair_seconds(x, m_fwd, m_adj) for x in ts)
+    # 65^3: measured oracle pair, predicted pair, and the GPU's errors against it
+    s = inputs.tissue(65, seed=3)
+    H = oracle.Hierarchy(s["D"], s["mu"], s["h"])
+    t0 = time.perf_counter()
+    ur, mf, _ = H.solve(s["q"], rtol=RTOL)
+    qr, Dr, mr, ma = H.vjp(ur, s["w"], rtol=RTOL)
+    meas65 = time.perf_counter() - t0
+    pred65 = _pair_seconds(_oracle_sample_times(s), mf, ma)
+    dev = torch.device("cuda", local)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    errs = {}
+    for prec in ("mixed", "fp64"):
+        S = dmg.Solver(T(s["D"]), T(s["mu"]), s["h"], rtol=RTOL, inner_cycles=inner,
+                       precision=dmg.DMG_MIXED if prec == "mixed" else dmg.DMG_FP64)
+        u = S.solve(T(s["q"]))
+        qb, Db, mb = S.vjp(u, T(s["w"]))
+        S.close()
+        e = {}
+        for k, a, b in (("u", u, ur), ("qbar", qb, qr), ("Dbar", Db, Dr), ("mubar", mb, mr)):
+            a = a.cpu().numpy()
+            e[k] = dict(rel_l2=float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                        rel_max=float(np.max(np.abs(a - b)) / np.max(np.abs(b))))
+        errs[prec] = e
+    shape = "x".join(map(str, w["shape"]))
+    return dict(value=1.0 / pair1, unit=UNIT, cores=1, kind="oracle",
+                sample="1 forward + 1 transposed V(2,2) cycle, 1 residual norm and 1 gradient evaluation of the FP64 "
+                       "oracle at %s (%.1f s), scaled to %d + %d cycles per fwd+VJP pair" %
+                       (shape, t["total"], m_fwd, m_adj),
+                host=host,
+                all_cores=dict(value=rate_all, unit=UNIT, cores=nproc, processes=nproc, wall_s=wall,
+                               sample="the same sample in %d concurrent single-threaded oracle processes; value = "
+                                      "sum of their pair rates" % nproc),
+                scaling_check_65=dict(measured_pair_s=meas65, predicted_pair_s=pred65, cycles=[mf, ma],
+                                      ratio=pred65 / meas65),
+                oracle_parity_65=dict(workload="tissue-like 65^3 (seed 3), fwd+VJP(q,D,mu), rtol 1e-10 on both "
+                                               "sides", **errs))
 
 
 def reference_arm(args, rank):
@@ -597,7 +820,7 @@ def reference_arm(args, rank):
                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(workload="tissue-like %d^3 fwd+VJP(q,D,mu), rtol 1e-10" % args.size,
                            grid=[args.size] * 3, h_mm=0.5, rtol=RTOL, precision="fp64 (CPU oracle, single thread)"),
-               cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample),
+               cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample, host=host_info()),
                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out))
 
@@ -623,6 +846,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=1, help="tile autotuner at setup (dmg_params.autotune)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
+    ap.add_argument("--serve-rate-low", type=float, default=100.0,
+                    help="arrival rate of a second stream below capacity (0: skip it)")
+    ap.add_argument("--no-setup", action="store_true", help="skip the setup-cost timings")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args, int(os.environ.get("RANK", "0")))
@@ -635,6 +861,10 @@ def main():
     from paper_2608_00760_b300 import dmg
     dmg.lib()
     torch.cuda.set_device(local)
+    st, FP64_OPS_PEAK[0] = dmg.dmg_probe_fma(True)
+    st32, fp32_rate = dmg.dmg_probe_fma(False)
+    if st != dmg.DMG_OK or not FP64_OPS_PEAK[0] > 0:
+        raise RuntimeError("dmg_probe_fma failed: %s" % dmg.dmg_strerror(st))
     if args.vi_only:
         peaks, peak_src = load_peaks()
         vi = run_vi(dmg, torch, args, world, local, peaks, peak_src)
@@ -671,14 +901,20 @@ def main():
             ach = byt / dur / 1e9
             pk = peaks.get("hbm_gbs", 6400.0)
             return dict(kernel="rbgs_half_sweep_fp32_level0", bound="hbm", achieved=ach, peak=pk, unit="GB/s",
-                        frac=ach / pk, traffic=HALF_SWEEP_TRAFFIC["fp32"] if args.size == 257 else None, peak_source=peak_src + " hbm_gbs",
-                        launches=pr["launches"], avg_us=dur * 1e6, algorithmic_bytes=byt)
+                        frac=ach / pk, frac_kernel_bytes=HALF_SWEEP_BYTES_FP32_KERNEL * nint / dur / 1e9 / pk,
+                        traffic=HALF_SWEEP_TRAFFIC["fp32"] if args.size == 257 else None,
+                        peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
+                        algorithmic_bytes=byt, bytes_per_vertex=HALF_SWEEP_BYTES_FP32,
+                        note="algorithmic bytes: 20 B per interior vertex per full FP32 sweep (read u, f, D, mu; "
+                             "write u), 10 B per half-sweep; frac_kernel_bytes charges the 12 B the colour kernel "
+                             "moves")
         ops = HALF_SWEEP_FP64_OPS * nint
         ach = ops / dur / 1e12
-        return dict(kernel="rbgs_half_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK / 1e12,
-                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK / 1e12), traffic=HALF_SWEEP_TRAFFIC["fp64"] if args.size == 257 else None,
-                    peak_source="measured FP64 FMA rate (probe)", launches=pr["launches"], avg_us=dur * 1e6,
-                    algorithmic_fp64_ops=ops)
+        return dict(kernel="rbgs_half_sweep_fp64_level0", bound="alu", achieved=ach, peak=FP64_OPS_PEAK[0] / 1e12,
+                    unit="TFP64-op/s", frac=ach / (FP64_OPS_PEAK[0] / 1e12),
+                    traffic=HALF_SWEEP_TRAFFIC["fp64"] if args.size == 257 else None,
+                    peak_source="dmg_probe_fma FP64 FMA rate, measured in this run", launches=pr["launches"],
+                    avg_us=dur * 1e6, algorithmic_fp64_ops=ops)
 
     def gbs(res, prec):
         # algorithmic HBM bytes of one pair divided by its time (see the design notes for the per-cycle bytes)
@@ -706,7 +942,9 @@ def main():
                device_memory_gb=dict(context=dmg.dmg_device_bytes(S.ctx) / 1e9,
                                      note="everything the fwd+VJP pair uses is allocated at setup: the pull-back "
                                           "adds no device memory to the forward"),
-               roofline=roofline(head, precisions[0]), clocks=head["clocks"])
+               roofline=roofline(head, precisions[0]), clocks=head["clocks"],
+               measured_rates=dict(fp64_fma_per_s=FP64_OPS_PEAK[0], fp32_fma_per_s=fp32_rate,
+                                   source="dmg_probe_fma (independent FMA chains on every SM, CUDA events)"))
     for prec in precisions[1:]:
         r = results[prec]
         out[prec] = dict(value=job_throughput(world, args.steps, r["total_ms"]), unit=UNIT,
@@ -728,19 +966,22 @@ def main():
                     ns, 1, world, local, inner=args.inner)
         out["e2e"] = dict(value=world * ns / e["seconds"], unit=UNIT, h2d_bytes_per_step=e["h2d"],
                           d2h_bytes_per_step=e["d2h"], steps=ns,
-                          api="dmg_solve_vjp with pinned host buffers (q, w in; u, qbar, Dbar, mubar out)")
+                          api="dmg_solve_vjp_many over %d pairs with pinned host buffers (q, w in; u, qbar, Dbar, "
+                              "mubar out per pair; transfers overlapped with the neighbouring pairs' solves)" % ns,
+                          single_call=dict(value=world * ns / e["seconds_single"], unit=UNIT,
+                                           api="dmg_solve_vjp, one call per pair"))
     else:
         out["e2e"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         m_f = results.get("fp64", head)["fwd_cycles"]
         m_a = results.get("fp64", head)["adj_cycles"]
-        out["cpu_baseline"] = cpu_baseline_sample(w, m_f, m_a)
-        out["cpu_baseline"].pop("seconds_per_pair", None)
+        out["cpu_baseline"] = cpu_baseline_leg(dmg, torch, w, m_f, m_a, local, args.inner)
     else:
         out["cpu_baseline"] = None
     out["vi_batch"] = run_vi(dmg, torch, args, world, local, peaks, peak_src) if args.vi_batch > 0 else None
     out["serving"] = (run_serving(dmg, torch, args, world, rank, local) if args.serve_requests > 0 else None)
     out["unrolled"] = run_unrolled(dmg, torch, args, world, local) if args.unrolled_size > 0 else None
+    out["setup"] = run_setup(dmg, torch, args, world, local) if not args.no_setup else None
     out["two_d"] = run_2d(dmg, torch, args, world, local, peaks, peak_src) if args.size_2d > 0 else None
     out["c3_large"] = run_513(dmg, torch, args, world, local) if args.size_513 > 0 else None
     if rank == 0:

@@ -166,6 +166,22 @@ dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, voi
                      dmg_ctx **out);
 
 /*
+ * dmg_set_coefficients -- new coefficient fields for an existing context: the
+ * hierarchy of Sec. 2.2 (D and mu coarsened level by level, the operator
+ * rediscretised on every level, the coarsest matrix inverted) is rebuilt in
+ * place for every sample, with the same kernels as dmg_setup and no
+ * allocation; the context's buffers and captured graphs stay valid. This is
+ * the per-iteration setup of a variational-inference loop, whose coefficients
+ * are the quantities being inferred (Sec. 2.5).
+ *   D, mu   as in dmg_setup ([batch][nz][ny][nx], device or host memory).
+ * Synchronises the stream (to check the coarsest matrices). Returns
+ * DMG_EINVAL for NULL arrays, while slots are running phases, or when a
+ * coarsest matrix is not positive definite (the context then holds the new,
+ * unusable coefficients until the next successful call).
+ */
+dmg_status dmg_set_coefficients(dmg_ctx *ctx, const double *D, const double *mu, void *stream);
+
+/*
  * dmg_solve -- u = S(q) (Eq. 2): V-cycles from u = 0 until the relative
  * residual reaches rtol, or exactly fixed_cycles cycles. info may be NULL.
  * Returns DMG_ENOCONV (u still written) when max_cycles is reached first
@@ -267,6 +283,31 @@ dmg_status dmg_response_vjp(dmg_ctx *ctx, const double *u, const double *rbar, d
 dmg_status dmg_solve_vjp(dmg_ctx *ctx, const double *q, const double *w, double *u, double *qbar,
                          double *Dbar, double *mubar, dmg_info *info_fwd, dmg_info *info_adj,
                          void *stream);
+
+/*
+ * dmg_solve_vjp_many -- npairs fwd+VJP pairs in one call: for every i,
+ * u[i] = S(q[i]) and the converged pull-back of w[i] (qbar[i], Dbar[i],
+ * mubar[i]), as dmg_solve_vjp computes them (Sec. 2.3 forward, Sec. 2.4 /
+ * Eq. 18 adjoint; streaming several pairs has no counterpart in the paper).
+ * It exists for callers whose arrays live in host memory: pair i+1's q and w
+ * are copied to the device while pair i iterates, and pair i's outputs are
+ * copied back while pair i+1 iterates (an upload and a download stream, two
+ * staging buffers each way), so the host transfers hide under the solves.
+ *   q, w                 arrays of npairs pointers (none NULL), each a field as
+ *                        in dmg_solve ([batch][nz][ny][nx], device or host).
+ *   u, qbar, Dbar, mubar arrays of npairs output pointers, or NULL (that output
+ *                        is skipped for every pair); an entry may be NULL.
+ *   info_fwd, info_adj   arrays of npairs reports, or NULL.
+ * Host outputs are complete when the call returns (it synchronises). Results
+ * are bit for bit those of dmg_solve_vjp on each pair. The first call
+ * allocates the staging buffers (12 fields of the level-0 size) and two
+ * streams, kept until dmg_destroy. Returns the first error (DMG_EINVAL,
+ * DMG_ENAN, ...) and stops there, or DMG_ENOCONV if some pair reached
+ * max_cycles (every output still written).
+ */
+dmg_status dmg_solve_vjp_many(dmg_ctx *ctx, int npairs, const double *const *q, const double *const *w,
+                              double *const *u, double *const *qbar, double *const *Dbar,
+                              double *const *mubar, dmg_info *info_fwd, dmg_info *info_adj, void *stream);
 
 /*
  * dmg_residual -- out[2b] = ||q_b - A_b u_b||_2 and out[2b+1] = ||q_b||_2 over
@@ -439,6 +480,16 @@ enum {
     DMG_KERNEL_GRAD = 4        /* coefficient gradients */
 };
 unsigned long long dmg_launch_count(const dmg_ctx *ctx);
+
+/*
+ * dmg_probe_fma -- measured FMA rate of the current device (instrumentation
+ * for the roofline of the FP64 kernels; no counterpart in the paper): runs a
+ * kernel of independent FMA chains on every SM (FP64 when fp64 != 0, else FP32)
+ * on `stream`, times the third of three launches with CUDA events and writes
+ * FMA instructions per second (one FMA = 2 flops) to *fma_per_s. Synchronises
+ * the stream. DMG_EINVAL for a NULL output, DMG_ECUDA on a CUDA failure.
+ */
+dmg_status dmg_probe_fma(int fp64, double *fma_per_s, void *stream);
 dmg_status dmg_profile_begin(dmg_ctx *ctx, int kernel, int level, int precision_fp32,
                              int max_launches);
 dmg_status dmg_profile_end(dmg_ctx *ctx, long long *launches, double *total_ms);

@@ -133,11 +133,20 @@ struct dmg_ctx {
     double *stage2 = nullptr;         // a second one, for transfers on the side stream
     cudaStream_t side = nullptr;      // overlaps host transfers with the iteration on the caller's stream
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_aux = nullptr;
+    // dmg_solve_vjp_many (allocated on first use): two input staging buffers
+    // (q then w, caller layout), two output staging buffers (u, qbar, Dbar,
+    // mubar), an upload and a download stream, and their events
+    double *mi_stage[2] = {nullptr, nullptr}, *mo_stage[2] = {nullptr, nullptr};
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_ready_u[2] = {}, ev_ready[2] = {}, ev_out[2] = {};
+    bool many_ready = false;
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
     double *red = nullptr;            // reduction results (device, kRedSlots doubles per sample)
-    double *hred = nullptr;           // pinned host copy of red
+    double *hred = nullptr;           // pinned host copy of red (mapped: hred_d is its device address)
+    double *hred_d = nullptr;
+    int *hact_d = nullptr, *hact_a_d = nullptr;   // device addresses of the mapped hact, hact_a
     int *act = nullptr;               // device mask: sample still iterating
     const int *mask = nullptr;        // mask argument of the launches being issued: act, or NULL
                                       // while every sample iterates (no per-block mask load)
@@ -302,6 +311,20 @@ void graphs_reset(dmg_ctx *c) {
         for (int idx : G.prof) c->prof_free.push_back(idx);
         G = Graph();
     }
+}
+
+// dst = src, n elements, by a kernel on stream s (double2 when both are 16-byte
+// aligned and n is even)
+template <class T>
+dmg_status dcopy(dmg_ctx *c, T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n == 0) return DMG_OK;
+    const int blocks = 148 * 8;
+    if (sizeof(T) == 8 && n % 2 == 0 && ((uintptr_t)dst % 16) == 0 && ((uintptr_t)src % 16) == 0)
+        dmgk::k_copy<double2><<<blocks, 256, 0, s>>>(reinterpret_cast<const double2 *>(src),
+                                                     reinterpret_cast<double2 *>(dst), (long long)(n / 2));
+    else
+        dmgk::k_copy<T><<<blocks, 256, 0, s>>>(src, dst, (long long)n);
+    return check_launch(c, "copy");
 }
 
 // --- staging between the caller's contiguous arrays and the split layout -------
@@ -604,11 +627,11 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
 // --- reductions ------------------------------------------------------------------
 constexpr int kSlots = dmgk::kRedSlots;
 
-// copy the reduction slots of every sample to pinned host memory
+// copy the reduction slots of every sample to pinned host memory (a kernel
+// writing through the mapping: no copy engine, so a step's read-back never
+// queues behind bulk host transfers on other streams)
 dmg_status enqueue_readback(dmg_ctx *c, cudaStream_t s) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, (size_t)kSlots * c->nb * sizeof(double), cudaMemcpyDeviceToHost,
-                                s));
-    return DMG_OK;
+    return dcopy(c, c->hred_d, c->red, (size_t)kSlots * c->nb, s);
 }
 
 // wait for the stream; the results are in hred[sample * kSlots + slot]
@@ -623,8 +646,7 @@ inline double hred(const dmg_ctx *c, int smp, int slot) { return c->hred[smp * k
 // the host mask to the device (the next launches see it; a replayed graph
 // reads it at run time)
 dmg_status push_act(dmg_ctx *c, cudaStream_t s) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->act, c->hact, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
-    return DMG_OK;
+    return dcopy(c, c->act, (const int *)c->hact_d, (size_t)c->nb, s);
 }
 
 // end of an API call: wait for the stream, harvest direct profiling pairs
@@ -1232,9 +1254,12 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
     CUDA_TRY(c, cudaMemsetAsync(c->red, 0, (size_t)kSlots * nb * sizeof(double), s));
     {
-        cudaError_t e = cudaMallocHost(&c->hred, (size_t)kSlots * nb * sizeof(double));
-        if (e == cudaSuccess) e = cudaMallocHost(&c->hact, nb * sizeof(int));
-        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+        // mapped pinned memory: kernels write the read-back and read the mask through the mapping
+        cudaError_t e = cudaHostAlloc(&c->hred, (size_t)kSlots * nb * sizeof(double), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc(&c->hact, nb * sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->hred_d, c->hred, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->hact_d, c->hact, 0);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaHostAlloc failed"); }
         memset(c->hred, 0, (size_t)kSlots * nb * sizeof(double));
         for (int b = 0; b < nb; b++) c->hact[b] = 1;
     }
@@ -1242,8 +1267,9 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     TRY(dalloc(c, &c->act_a, nb));
     CUDA_TRY(c, cudaMemsetAsync(c->act_a, 0, nb * sizeof(int), s));
     {
-        cudaError_t e = cudaMallocHost(&c->hact_a, nb * sizeof(int));
-        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+        cudaError_t e = cudaHostAlloc(&c->hact_a, nb * sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->hact_a_d, c->hact_a, 0);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaHostAlloc failed"); }
         memset(c->hact_a, 0, nb * sizeof(int));
     }
     c->slots.assign(nb, Slot());
@@ -1316,6 +1342,134 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     return DMG_OK;
 }
 
+// --- a stream of fwd+VJP pairs with overlapped host transfers --------------------
+dmg_status many_alloc(dmg_ctx *c) {
+    if (c->many_ready) return DMG_OK;
+    const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz * c->nb;
+    for (int b = 0; b < 2; b++) {
+        TRY(dalloc(c, &c->mi_stage[b], 2 * n));
+        TRY(dalloc(c, &c->mo_stage[b], 4 * n));
+    }
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; b++)
+        for (cudaEvent_t *e : {&c->ev_in[b], &c->ev_used[b], &c->ev_ready_u[b], &c->ev_ready[b], &c->ev_out[b]})
+            CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    c->many_ready = true;
+    return DMG_OK;
+}
+
+// Pairs i = 0 .. npairs-1, each dmg_solve(q[i]) then the converged pull-back
+// of w[i]. Host inputs are copied on the upload stream into one of two staging
+// buffers one pair ahead; host outputs are laid out on the caller's stream into
+// one of two staging buffers and copied out on the download stream while the
+// next pair iterates. Device arrays are read and written in place.
+dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, const double *const *w,
+                               double *const *u, double *const *qbar, double *const *Dbar, double *const *mubar,
+                               dmg_info *info_fwd, dmg_info *info_adj, cudaStream_t s) {
+    if (npairs < 1 || !q || !w) return fail(c, DMG_EINVAL, "npairs must be >= 1 and q, w not NULL");
+    for (int i = 0; i < npairs; i++)
+        if (!q[i] || !w[i]) return fail(c, DMG_EINVAL, "q[%d] and w[%d] must not be NULL", i, i);
+    TRY(many_alloc(c));
+    Level &l = c->L[0];
+    const Geom g = geom0(c, -1);
+    const size_t n = (size_t)g.nx * g.ny * g.nz * g.nb;
+    const size_t bytes = n * sizeof(double);
+    auto out_at = [](double *const *a, int i) { return a ? a[i] : nullptr; };
+    // H2D copies of pair i's host inputs into mi_stage[i % 2], once pair i-2 has gathered from it
+    auto upload = [&](int i) -> dmg_status {
+        const int b = i % 2;
+        CUDA_TRY(c, cudaStreamWaitEvent(c->up, c->ev_used[b], 0));
+        if (!is_device_ptr(q[i]))
+            CUDA_TRY(c, cudaMemcpyAsync(c->mi_stage[b], q[i], bytes, cudaMemcpyHostToDevice, c->up));
+        if (!is_device_ptr(w[i]))
+            CUDA_TRY(c, cudaMemcpyAsync(c->mi_stage[b] + n, w[i], bytes, cudaMemcpyHostToDevice, c->up));
+        CUDA_TRY(c, cudaEventRecord(c->ev_in[b], c->up));
+        return DMG_OK;
+    };
+    // lay src out into dst (device) or into the output staging slot, whose copy to
+    // the host follows on the download stream
+    auto put = [&](const double *src, double *dst, double *stage_slot) -> dmg_status {
+        if (is_device_ptr(dst)) {
+            dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
+            return check_launch(c, "scatter");
+        }
+        dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, stage_slot);
+        return check_launch(c, "scatter");
+    };
+    auto fetch = [&](const double *stage_slot, double *dst) -> dmg_status {
+        if (dst && !is_device_ptr(dst))
+            CUDA_TRY(c, cudaMemcpyAsync(dst, stage_slot, bytes, cudaMemcpyDeviceToHost, c->down));
+        return DMG_OK;
+    };
+    auto abort_all = [&](dmg_status st) {
+        cudaStreamSynchronize(c->up);
+        cudaStreamSynchronize(c->down);
+        return st;
+    };
+    dmg_status worst = DMG_OK;
+    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));   // the uploads start after the caller's earlier work
+    CUDA_TRY(c, cudaStreamWaitEvent(c->up, c->ev_fork, 0));
+    TRY(upload(0));
+    for (int i = 0; i < npairs; i++) {
+        const int b = i % 2;
+        double *mo = c->mo_stage[b];
+        // inputs of pair i
+        CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
+        const double *qs = is_device_ptr(q[i]) ? q[i] : c->mi_stage[b];
+        const double *ws = is_device_ptr(w[i]) ? w[i] : c->mi_stage[b] + n;
+        dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, qs, l.f, 0);
+        TRY(check_launch(c, "gather"));
+        dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, ws, c->T3, 0);
+        TRY(check_launch(c, "gather"));
+        CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
+        if (i + 1 < npairs) TRY(upload(i + 1));   // overlaps this pair's iterations
+        dmg_status st = iterate(c, false, c->p.fixed_cycles, info_fwd ? info_fwd + i : nullptr, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) return abort_all(st);
+        if (st != DMG_OK) worst = st;
+        TRY(dcopy(c, c->U0, l.u, l.n, s));
+        TRY(dcopy(c, l.f, c->T3, l.n, s));
+        // the staging slot of pair i-2 must have reached the host
+        CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_out[b], 0));
+        if (double *dst = out_at(u, i)) {
+            TRY(put(c->U0, dst, mo));
+            CUDA_TRY(c, cudaEventRecord(c->ev_ready_u[b], s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready_u[b], 0));
+            TRY(fetch(mo, dst));   // overlaps the adjoint iteration
+        }
+        st = iterate(c, true, 0, info_adj ? info_adj + i : nullptr, s);
+        if (st != DMG_OK && st != DMG_ENOCONV) return abort_all(st);
+        if (st != DMG_OK) worst = st;
+        double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *qb = out_at(qbar, i);
+        if (Db || mb) {
+            const double ih2 = 1.0 / (l.h * l.h);
+            ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+            if (c->dim == 2)
+                dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                               c->p.face_mean == DMG_FACE_HARMONIC,
+                                                               Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+            else
+                dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                                                             c->p.face_mean == DMG_FACE_HARMONIC,
+                                                             Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+            TRY(check_launch(c, "grad"));
+        }
+        if (qb) TRY(put(l.u, qb, mo + n));
+        if (Db) TRY(put(c->T1, Db, mo + 2 * n));
+        if (mb) TRY(put(c->T2, mb, mo + 3 * n));
+        CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], s));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready[b], 0));
+        if (qb) TRY(fetch(mo + n, qb));   // overlap the next pair's iterations
+        if (Db) TRY(fetch(mo + 2 * n, Db));
+        if (mb) TRY(fetch(mo + 3 * n, mb));
+        CUDA_TRY(c, cudaEventRecord(c->ev_out[b], c->down));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->up));
+    CUDA_TRY(c, cudaStreamSynchronize(c->down));
+    TRY(end_call(c, s));
+    return worst;
+}
+
 // --- slot-level (serving) interface ---------------------------------------------
 // A batched context doubles as a pool of slots. Each slot holds one request's
 // coefficient hierarchy and runs one phase at a time (forward solve, tangent
@@ -1348,6 +1502,29 @@ dmg_status slot_load_impl(dmg_ctx *c, int slot, const double *D, const double *m
     TRY(build_coefficients(c, slot, D, mu, s));
     sl = Slot();
     sl.load_pending = true;
+    return DMG_OK;
+}
+
+// New coefficients for every sample of an existing context: the hierarchy is
+// rebuilt in place (the same kernels as setup, no allocation), so the
+// context's graphs and buffers stay valid. Waits for the stream to check that
+// every coarsest matrix is positive definite.
+dmg_status set_coefficients_impl(dmg_ctx *c, const double *D, const double *mu, cudaStream_t s) {
+    if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
+    if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+    TRY(build_coefficients(c, -1, D, mu, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    for (Slot &sl : c->slots) {
+        sl = Slot();
+        sl.loaded = true;
+    }
+    for (int b = 0; b < c->nb; b++)
+        if (c->hstatus[b] != 0) {
+            if (c->nb == 1)
+                return fail(c, DMG_EINVAL, "coarsest-level matrix is not positive definite (need D > 0, mu >= 0)");
+            return fail(c, DMG_EINVAL,
+                        "coarsest-level matrix of sample %d is not positive definite (need D > 0, mu >= 0)", b);
+        }
     return DMG_OK;
 }
 
@@ -1436,8 +1613,8 @@ dmg_status step_launch_impl(dmg_ctx *c, cudaStream_t s) {
         c->hact_a[b] = sl.in_step && t == 1;
         if (sl.in_step) run[t] = true;
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->act, c->hact, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->act_a, c->hact_a, c->nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(dcopy(c, c->act, (const int *)c->hact_d, (size_t)c->nb, s));
+    TRY(dcopy(c, c->act_a, (const int *)c->hact_a_d, (size_t)c->nb, s));
     for (int t = 0; t < 2; t++) {
         if (!run[t]) continue;
         TRY(capture_step(c, t));
@@ -1505,8 +1682,7 @@ dmg_status step_finish_impl(dmg_ctx *c, cudaStream_t s, int *ended_out, int *nen
         Slot &sl = c->slots[b];
         if (sl.phase == DMG_PHASE_FORWARD && (sl.status == DMG_OK || sl.status == DMG_ENOCONV)) {
             const Level l = level_view(c, 0, b);
-            CUDA_TRY(c, cudaMemcpyAsync(c->U0 + (long long)b * l.g.sb, l.u, l.n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, s));
+            TRY(dcopy(c, c->U0 + (long long)b * l.g.sb, (const double *)l.u, l.n, s));
             sl.have_fwd = true;
         }
         c->bcyc[b] = sl.steps * per_step;
@@ -1584,8 +1760,7 @@ dmg_status unrolled_alloc(dmg_ctx *c, int nck) {
 }
 
 dmg_status copy_level(dmg_ctx *c, double *dst, const double *src, int l, cudaStream_t s) {
-    CUDA_TRY(c, cudaMemcpyAsync(dst, src, c->L[l].n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return DMG_OK;
+    return dcopy(c, dst, src, c->L[l].n, s);
 }
 
 dmg_status half64(dmg_ctx *c, int l, int color, cudaStream_t s) {
@@ -1781,6 +1956,10 @@ dmg_status guarded(dmg_ctx *c, F fn, const char *name = "dmg") {
 
 }  // namespace
 
+// results of the arithmetic-rate probe land here only if they are impossible
+__device__ double g_fma_sink64;
+__device__ float g_fma_sink32;
+
 // Sets the message dmg_last_error(NULL) returns on this thread; used by the
 // context-free entry point in noalloc.cu.
 void dmg_detail_set_noctx_error(const char *msg) { snprintf(g_setup_err, sizeof(g_setup_err), "%s", msg); }
@@ -1896,9 +2075,9 @@ dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u
         }
         // the forward solution stays on the device for the gradient; its read-out
         // (side stream) overlaps the adjoint iteration
-        CUDA_TRY(c, cudaMemcpyAsync(c->U0, l.u, l.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TRY(dcopy(c, c->U0, l.u, l.n, s));
         CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_aux, 0));
-        CUDA_TRY(c, cudaMemcpyAsync(l.f, c->T3, l.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TRY(dcopy(c, l.f, c->T3, l.n, s));
         if (u) {
             CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
             CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -1934,6 +2113,17 @@ dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u
         TRY(end_call(c, s));
         return st != DMG_OK ? st : st2;
     }, "dmg_solve_vjp");
+}
+
+dmg_status dmg_solve_vjp_many(dmg_ctx *c, int npairs, const double *const *q, const double *const *w,
+                              double *const *u, double *const *qbar, double *const *Dbar, double *const *mubar,
+                              dmg_info *info_fwd, dmg_info *info_adj, void *stream) {
+    return guarded(c, [&]() -> dmg_status {
+        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        if (info_fwd) for (int i = 0; i < npairs; i++) info_reset(info_fwd + i);
+        if (info_adj) for (int i = 0; i < npairs; i++) info_reset(info_adj + i);
+        return solve_vjp_many_impl(c, npairs, q, w, u, qbar, Dbar, mubar, info_fwd, info_adj, S(stream));
+    }, "dmg_solve_vjp_many");
 }
 
 dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, double *qbar, double *Dbar,
@@ -2139,6 +2329,14 @@ dmg_status dmg_destroy(dmg_ctx *c) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
     }
+    for (cudaStream_t st : {c->up, c->down})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (int b = 0; b < 2; b++)
+        for (cudaEvent_t e : {c->ev_in[b], c->ev_used[b], c->ev_ready_u[b], c->ev_ready[b], c->ev_out[b]})
+            if (e) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_aux) cudaEventDestroy(c->ev_aux);
@@ -2177,6 +2375,47 @@ dmg_status dmg_vjp_unrolled(dmg_ctx *c, const double *q, const double *w, int m,
 
 dmg_status dmg_slot_load(dmg_ctx *c, int slot, const double *D, const double *mu, void *stream) {
     return guarded(c, [&]() { return slot_load_impl(c, slot, D, mu, S(stream)); }, "dmg_slot_load");
+}
+
+dmg_status dmg_set_coefficients(dmg_ctx *c, const double *D, const double *mu, void *stream) {
+    return guarded(c, [&]() { return set_coefficients_impl(c, D, mu, S(stream)); }, "dmg_set_coefficients");
+}
+
+dmg_status dmg_probe_fma(int fp64, double *fma_per_s, void *stream) {
+    Range r("dmg_probe_fma");
+    if (!fma_per_s) return DMG_EINVAL;
+    *fma_per_s = 0.0;
+    cudaStream_t s = S(stream);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return DMG_ECUDA;
+    void *sink = nullptr;
+    if ((fp64 ? cudaGetSymbolAddress(&sink, g_fma_sink64) : cudaGetSymbolAddress(&sink, g_fma_sink32)) !=
+        cudaSuccess)
+        return DMG_ECUDA;
+    // 8 blocks of 256 threads per SM (one full wave); about 20 ms of work at the expected rate
+    const int blocks = 8 * sms, threads = 256;
+    const int iters = fp64 ? 2048 : 65536;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    dmg_status st = DMG_OK;
+    float ms = 0.0f;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = DMG_ECUDA;
+    for (int rep = 0; rep < 3 && st == DMG_OK; rep++) {   // the first launch warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = DMG_ECUDA;
+        if (fp64)
+            dmgk::k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, (double *)sink);
+        else
+            dmgk::k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, (float *)sink);
+        if (st == DMG_OK && (cudaPeekAtLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = DMG_ECUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != DMG_OK || ms <= 0.0f) return DMG_ECUDA;
+    *fma_per_s = (double)blocks * threads * dmgk::kFmaChains * iters / (ms * 1e-3);
+    return DMG_OK;
 }
 
 dmg_status dmg_slot_begin(dmg_ctx *c, int slot, int phase, const double *a, const double *b, const double *d,

@@ -1373,6 +1373,42 @@ __global__ void __launch_bounds__(256) k_response_mubar(Geom g, Margins m, const
     if (m.kept(g, i, j, k)) mubar[p] = fma(u[p], rbar[p], mubar[p]);
 }
 
+// ---------------------------------------------------------------------------
+// dst[0..n) = src[0..n) on the SMs (copies between device arrays, and between
+// device arrays and mapped pinned host memory, stay off the copy engines, which
+// the bulk host transfers of dmg_solve_vjp_many keep busy)
+template <class T>
+__global__ void __launch_bounds__(256) k_copy(const T *__restrict__ src, T *__restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic-rate probe (instrumentation): every thread runs kChains
+// independent FMA chains of `iters` steps, so the FMA pipe of every SM is kept
+// busy. The chains stay bounded (|a| < 2) and the result is written only if it
+// equals an impossible value, which keeps the work from being removed.
+constexpr int kFmaChains = 16;
+constexpr int kFmaUnroll = 4;   // iterations per loop trip (iters must be a multiple)
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T *sink) {
+    T a[kFmaChains];
+#pragma unroll
+    for (int q = 0; q < kFmaChains; q++) a[q] = T(0.25) + T(0.001) * T(threadIdx.x + q);
+    const T b = T(0.999), c = T(0.0005);
+    for (int it = 0; it < iters; it += kFmaUnroll) {
+#pragma unroll
+        for (int u = 0; u < kFmaUnroll; u++)
+#pragma unroll
+            for (int q = 0; q < kFmaChains; q++) a[q] = fma(a[q], b, c);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < kFmaChains; q++) s += a[q];
+    if (s == T(-12345.0)) *sink = s;
+}
+
 // x = 0 on the interior vertices of the active samples
 template <class T>
 __global__ void __launch_bounds__(256) k_zero_interior(Geom g, T *__restrict__ x, const int *act) {

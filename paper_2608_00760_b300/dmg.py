@@ -64,7 +64,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
            "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp",
-           "dmg_debug_oob_count")
+           "dmg_debug_oob_count", "dmg_set_coefficients", "dmg_probe_fma", "dmg_solve_vjp_many")
 
 _lib = None
 
@@ -117,6 +117,9 @@ def lib():
             "dmg_debug_oob_count": (ctypes.c_longlong, []),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
+            "dmg_set_coefficients": (i, [vp, vp, vp, vp]),
+            "dmg_probe_fma": (i, [i, P(d), vp]),
+            "dmg_solve_vjp_many": (i, [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -201,6 +204,28 @@ def dmg_solve_vjp(ctx, q, w, u, qbar, Dbar, mubar, info_fwd=None, info_adj=None,
                                ctypes.byref(info_adj) if info_adj is not None else None, _stream(stream))
 
 
+def dmg_solve_vjp_many(ctx, q, w, u=None, qbar=None, Dbar=None, mubar=None, info_fwd=None, info_adj=None,
+                       stream=None, n=None):
+    """npairs fwd+VJP pairs with overlapped host transfers. q, w: sequences of
+    arrays (one per pair); u, qbar, Dbar, mubar: sequences of output arrays or
+    None; info_fwd / info_adj: ctypes arrays of dmg_info (e.g. (dmg_info * n)())
+    or None."""
+    m = len(q)
+    if len(w) != m:
+        raise ValueError("q and w need one array per pair")
+
+    def ptrs(seq):
+        if seq is None:
+            return None
+        if len(seq) != m:
+            raise ValueError("expected %d arrays" % m)
+        arr = (ctypes.c_void_p * m)(*[_ptr(x, n) for x in seq])
+        return arr
+
+    keep = [ptrs(x) for x in (q, w, u, qbar, Dbar, mubar)]
+    return lib().dmg_solve_vjp_many(ctx, m, *keep, info_fwd, info_adj, _stream(stream))
+
+
 def dmg_vjp(ctx, u, w, cycles, qbar, Dbar, mubar, info=None, stream=None, n=None):
     return lib().dmg_vjp(ctx, _ptr(u, n), _ptr(w, n), int(cycles), _ptr(qbar, n), _ptr(Dbar, n),
                          _ptr(mubar, n), ctypes.byref(info) if info is not None else None, _stream(stream))
@@ -250,6 +275,17 @@ def dmg_response_vjp(ctx, u, rbar, edge, qbar, Dbar, mubar, info=None, stream=No
     return lib().dmg_response_vjp(ctx, _ptr(u, n), _ptr(rbar, n), float(edge), _ptr(qbar, n), _ptr(Dbar, n),
                                   _ptr(mubar, n), ctypes.byref(info) if info is not None else None,
                                   _stream(stream))
+
+
+def dmg_set_coefficients(ctx, D, mu, stream=None, n=None):
+    return lib().dmg_set_coefficients(ctx, _ptr(D, n), _ptr(mu, n), _stream(stream))
+
+
+def dmg_probe_fma(fp64=True, stream=None):
+    """(status, FMA instructions per second) of the current device."""
+    out = ctypes.c_double()
+    st = lib().dmg_probe_fma(int(bool(fp64)), ctypes.byref(out), _stream(stream))
+    return st, out.value
 
 
 def dmg_slot_load(ctx, slot, D, mu, stream=None, n=None):
@@ -399,6 +435,10 @@ class Solver:
 
     def levels(self):
         return [dmg_level_shape(self.ctx, l)[1] for l in range(dmg_levels(self.ctx))]
+
+    def set_coefficients(self, D, mu, stream=None):
+        """Rebuild the coefficient hierarchy in place from new D, mu (same shape)."""
+        self._check(dmg_set_coefficients(self.ctx, D, mu, stream, n=self.n))
 
     def tiles(self, fp32=False):
         """Block shape (threads along the half-row, rows) of the colour kernels per level."""

@@ -57,3 +57,30 @@ def test_percentile_of_empty_and_small_samples():
     assert bench.percentile([], 50) is None
     assert bench.percentile([3.0], 99) == 3.0
     assert bench.percentile([1.0, 2.0, 3.0, 4.0], 50) == 2.5
+
+
+def test_host_info_reports_cores_and_model():
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and 1 <= h["usable"] <= h["nproc"]
+    assert h["cpu_model"] is None or isinstance(h["cpu_model"], str)
+
+
+def test_all_core_oracle_workers_run_the_sample(tmp_path):
+    # the all-core CPU baseline: spawned processes load the saved arrays and
+    # time the oracle's bounded sample; the pair time combines the pieces
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from paper_2608_00760_b300 import inputs
+    w = inputs.tissue(17, seed=1)
+    for k in ("D", "mu", "q", "w"):
+        np.save(str(tmp_path / (k + ".npy")), w[k])
+    with mp.get_context("spawn").Pool(2) as pool:
+        ts = pool.starmap(bench._oracle_worker, [(str(tmp_path), w["h"])] * 2)
+    for t in ts:
+        assert all(t[k] > 0 for k in ("fwd", "res", "adj", "grad"))
+        assert abs(t["total"] - (t["fwd"] + t["res"] + t["adj"] + t["grad"])) < 1e-6
+    t = ts[0]
+    assert bench._pair_seconds(t, 3, 2) == (3 * (t["fwd"] + t["res"]) + 2 * (t["adj"] + t["res"]) + t["grad"])
+    assert 1 <= bench._all_core_processes((257, 257, 257)) <= bench.host_info()["usable"]

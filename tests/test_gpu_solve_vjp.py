@@ -55,3 +55,55 @@ def test_solve_vjp_is_bitwise_solve_then_vjp(dmg, case, precision, host):
     for a, b in zip(got, ref):
         assert torch.equal(a, b)
     S.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("where", ["host", "device", "mixed"])
+def test_many_pairs_are_bitwise_single_pairs(dmg, case, precision, where):
+    # dmg_solve_vjp_many over four pairs (different sources and cotangents, as a
+    # sampler streams them): each pair's outputs equal dmg_solve_vjp on that
+    # pair, with host arrays (transfers overlapped), device arrays, or both kinds
+    _, make, dim = case
+    w = make()
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, dim=dim)
+    rng = np.random.default_rng(7)
+    pairs = [(w["q"] * (1.0 + 0.5 * p), w["w"] * rng.standard_normal(w["q"].shape)) for p in range(4)]
+    ref = []
+    for qa, wa in pairs:
+        outs = [torch.empty(w["q"].shape, dtype=torch.float64, device="cuda") for _ in range(4)]
+        assert dmg.dmg_solve_vjp(S.ctx, T(qa), T(wa), *outs, n=S.n) == dmg.DMG_OK
+        ref.append(outs)
+
+    def arr(a, i):
+        dev = where == "device" or (where == "mixed" and i % 2 == 1)
+        return T(a) if dev else np.ascontiguousarray(a)
+
+    qs = [arr(qa, i) for i, (qa, _) in enumerate(pairs)]
+    ws = [arr(wa, i) for i, (_, wa) in enumerate(pairs)]
+    outs = [[arr(np.zeros(w["q"].shape), i) for i in range(4)] for _ in range(4)]
+    fi, ai = (dmg.dmg_info * 4)(), (dmg.dmg_info * 4)()
+    st = dmg.dmg_solve_vjp_many(S.ctx, qs, ws, *outs, info_fwd=fi, info_adj=ai, n=S.n)
+    assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+    for i in range(4):
+        assert fi[i].rel_residual <= 1e-10 and ai[i].rel_residual <= 1e-10
+        for k in range(4):
+            got = outs[k][i]
+            got = got if torch.is_tensor(got) else torch.from_numpy(got).cuda()
+            assert torch.equal(got, ref[i][k]), (i, k)
+    # outputs may be skipped
+    assert dmg.dmg_solve_vjp_many(S.ctx, qs[:2], ws[:2], None, None, outs[2][:2], None, n=S.n) == dmg.DMG_OK
+    for i in range(2):
+        got = outs[2][i]
+        got = got if torch.is_tensor(got) else torch.from_numpy(got).cuda()
+        assert torch.equal(got, ref[i][2])
+    S.close()
+
+
+def test_many_pairs_argument_errors(dmg):
+    w = inputs.tissue(17, seed=114)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"])
+    assert dmg.dmg_solve_vjp_many(S.ctx, [T(w["q"])], [None], n=S.n) == dmg.DMG_EINVAL
+    assert dmg.lib().dmg_solve_vjp_many(S.ctx, 0, None, None, None, None, None, None, None, None, None) == \
+        dmg.DMG_EINVAL
+    S.close()
