@@ -591,23 +591,26 @@ def run_setup(dmg, torch, args, world, local):
 SERVE_SHAPES = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
 
 
-def serve_stream(dmg, torch, args, world, rank, local, rate, nreq):
+def serve_stream(dmg, torch, args, world, rank, local, rate, nreq, pyramid=False):
     """One served stream of nreq Poisson arrivals at `rate` per second (mixed precision, rtol 1e-10)."""
     from paper_2608_00760_b300 import serve
     dev = torch.device("cuda", local)
     reqs = serve.poisson_stream(nreq, rate, SERVE_SHAPES, seed=1000 + rank)
     server = serve.Server(SERVE_SHAPES, budget_bytes=args.serve_budget_gb * 1e9, device=dev,
-                          params=dict(precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=args.inner))
+                          params=dict(precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=args.inner),
+                          pyramid=pyramid)
     try:
         warm = serve.poisson_stream(3 * len(SERVE_SHAPES), 1e4, SERVE_SHAPES, seed=99)
         server.run(warm, realtime=False, keep_outputs=False)      # graph capture, outside the measurement
         barrier(world)
         served, st = server.run(reqs, keep_outputs=False)
-        slots = {"x".join(map(str, s[::-1])): p.slots for s, p in server.pools.items()}
+        slots = {"x".join(map(str, s[::-1])): server.slots[s] for s in server.pools}
+        pyramids = ["+".join("x".join(map(str, s[::-1])) for s in p.chain) for p in server.unique_pools()
+                    if len(p.chain) > 1]
         pool_gb = server.pool_bytes / 1e9
     finally:
         server.close()
-    return reqs, served, st, slots, pool_gb
+    return reqs, served, st, dict(slots=slots, pyramid_pools=pyramids), pool_gb
 
 
 def run_serving(dmg, torch, args, world, rank, local):
@@ -617,9 +620,19 @@ def run_serving(dmg, torch, args, world, rank, local):
     (mixed precision, rtol 1e-10); then the same requests one at a time in FP64."""
     from paper_2608_00760_b300 import serve
     dev = torch.device("cuda", local)
-    reqs, served, st, slots, pool_gb = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate,
-                                                     args.serve_requests)
+    reqs, served, st, layout, pool_gb = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate,
+                                                      args.serve_requests)
     secs = max_over_ranks(world, st["seconds"])
+    pyr = None
+    if args.serve_pyramid:
+        preqs, _, pst, playout, _ = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate,
+                                                 args.serve_requests, pyramid=True)
+        psecs = max_over_ranks(world, pst["seconds"])
+        pyr = dict(rate=args.serve_rate, value=world * sum(r.solves for r in preqs) / psecs
+                   if pst["ok"] == len(preqs) else None, unit="solves/s", requests_per_s=world * pst["ok"] / psecs,
+                   p50_ms=pst["p50_ms"], p99_ms=pst["p99_ms"], seconds=psecs, pyramid_pools=playout["pyramid_pools"],
+                   note="the cube shapes in one pyramid pool: one launch per kernel and level for every slot of "
+                        "every shape holding that level")
     low = None
     if args.serve_rate_low > 0:
         lreqs, lserved, lst, _, _ = serve_stream(dmg, torch, args, world, rank, local, args.serve_rate_low,
@@ -639,8 +652,9 @@ def run_serving(dmg, torch, args, world, rank, local):
                 value=world * nsolves / secs if st["ok"] == len(reqs) else None, unit="solves/s",
                 requests_per_s=world * st["ok"] / secs, ok=st["ok"], requests=len(reqs),
                 p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], seconds=secs,
-                slots=slots, pools_gb=pool_gb, cycles_mean=float(np.mean(cyc)) if cyc else None,
-                lower_rate=low,
+                slots=layout["slots"], pyramid_pools=layout["pyramid_pools"], pools_gb=pool_gb,
+                cycles_mean=float(np.mean(cyc)) if cyc else None,
+                lower_rate=low, pyramid_variant=pyr,
                 one_at_a_time_fp64=dict(value=world * nsolves / t_alone, unit="solves/s",
                                         requests_per_s=world * len(reqs) / t_alone, seconds=t_alone,
                                         api="dmg_setup + dmg_solve/dmg_jvp/dmg_vjp per request, batch 1"))
@@ -849,6 +863,8 @@ def main():
     ap.add_argument("--serve-rate-low", type=float, default=100.0,
                     help="arrival rate of a second stream below capacity (0: skip it)")
     ap.add_argument("--no-setup", action="store_true", help="skip the setup-cost timings")
+    ap.add_argument("--serve-pyramid", type=int, default=1,
+                    help="also serve the stream with the cube shapes in one pyramid pool (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args, int(os.environ.get("RANK", "0")))

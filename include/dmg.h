@@ -357,6 +357,33 @@ dmg_status dmg_batch_info(const dmg_ctx *ctx, int *cycles, double *rel);
  */
 enum { DMG_PHASE_FORWARD = 0, DMG_PHASE_TANGENT = 1, DMG_PHASE_ADJOINT = 2 };
 
+/*
+ * dmg_setup_pyramid -- a pool of slots for requests on a chain of grid sizes
+ * that share their coarse levels (no counterpart in the paper). The grid
+ * hierarchy of Sec. 2.2 for p's grid (nx, ny, nz) is the chain: level k has
+ * (n - 1) / 2^k + 1 vertices per axis. slots_per_level[k] slots (k < nlevels)
+ * take requests whose grid is level k, so a 257^3 pyramid serves 257^3,
+ * 129^3, 65^3, ... requests together: slots are numbered level by level
+ * (slots_per_level[0] slots of level 0 first), and every step launch runs one
+ * V-cycle of all slots in which each level's kernels take every slot that
+ * holds that level -- a 257^3 request's 65^3 level and a 65^3 request's finest
+ * level in the same launch. Each slot's refinement (update, residual, norms)
+ * runs on its own finest level, and its arithmetic is that of its request on a
+ * context of its own grid: results are bit for bit those of
+ * dmg_solve / dmg_jvp / dmg_vjp there.
+ *   p          the chain's finest grid (nx, ny, nz), the vertex spacing h of
+ *              every slot's own finest grid (requests of all sizes share h;
+ *              a slot's coarser levels have 2h, 4h, ...), and the solver
+ *              parameters (batch is ignored; fixed_cycles must be 0; 3D only).
+ * Slots have no coefficients until dmg_slot_load; the slot calls take arrays
+ * of the slot's own grid. Only the slot-level calls (and dmg_destroy,
+ * dmg_device_bytes, dmg_levels, ...) accept a pyramid. Returns DMG_EINVAL for
+ * bad counts, or when a level with slots would lie inside the single-block tail
+ * of the small levels (its grid is too small; e.g. 17^3 in mixed precision).
+ */
+dmg_status dmg_setup_pyramid(const dmg_params *p, const int *slots_per_level, int nlevels, void *stream,
+                             dmg_ctx **out);
+
 /* dmg_slot_load -- rebuild the coefficient hierarchy of one slot from D, mu
    (asynchronous; a matrix that is not positive definite makes the slot's next
    phase end with DMG_EINVAL). The slot must not be running a phase. */

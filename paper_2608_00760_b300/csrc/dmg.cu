@@ -140,6 +140,16 @@ struct dmg_ctx {
     cudaStream_t up = nullptr, down = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_ready_u[2] = {}, ev_ready[2] = {}, ev_out[2] = {};
     bool many_ready = false;
+    // pyramid pool (dmg_setup_pyramid): slot b's finest level is top_of[b]; level l
+    // holds samples [0, L[l].g.nb), of which [top_first[l], top_first[l] + top_count[l])
+    // have it as their finest level. Every other context is the case of one top
+    // level (level 0, all samples).
+    bool pyramid = false;
+    int top_count[kMaxLevels] = {}, top_first[kMaxLevels] = {};
+    std::vector<int> top_of;
+    std::vector<long long> stage_off;   // per slot: its part of the contiguous staging buffers
+    // per level: outputs of the slots whose finest level it is (U0l[0] = U0, ...)
+    double *U0l[kMaxLevels] = {}, *T1l[kMaxLevels] = {}, *T2l[kMaxLevels] = {};
     double *U0 = nullptr;             // level-0 staging: user's u
     double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;  // level-0 staging: tangents / outputs
     double *partial = nullptr;        // reduction partials
@@ -344,10 +354,12 @@ inline dim3 vertex_grid(const Geom &g) {
     return dim3((unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256), g.nb);
 }
 
-// level-0 geometry of one slot (a single sample; slot < 0: every sample)
+// level-0 geometry of every sample (slot < 0), or the geometry of one slot's
+// finest level (a single sample)
 inline Geom geom0(const dmg_ctx *c, int slot) {
-    Geom g = c->L[0].g;
-    if (slot >= 0) g.nb = 1;
+    if (slot < 0) return c->L[0].g;
+    Geom g = c->L[c->top_of[slot]].g;
+    g.nb = 1;
     return g;
 }
 
@@ -360,7 +372,7 @@ dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_bounda
     const size_t bytes = n * g.nb * sizeof(double);
     const double *from = src;
     if (!is_device_ptr(src)) {
-        double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : n * slot);
+        double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : c->stage_off[slot]);
         CUDA_TRY(c, cudaMemcpyAsync(st, src, bytes, cudaMemcpyHostToDevice, s));
         from = st;
     }
@@ -377,7 +389,7 @@ dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s,
         dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
         return check_launch(c, "scatter");
     }
-    double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : n * slot);
+    double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : c->stage_off[slot]);
     dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, st);
     TRY(check_launch(c, "scatter"));
     CUDA_TRY(c, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyDeviceToHost, s));
@@ -459,9 +471,19 @@ dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
 // both). zero_colour >= 0: the defect
 // vanishes on that colour (the last half-sweep updated it), so it is formed on
 // the other colour only and the restriction reads only that colour.
+// the coarse level lev+1 seen with the samples of level lev only (a pyramid's
+// coarse levels also hold the samples whose finest level they are; transfers
+// between lev and lev+1 touch the samples of lev)
+inline Level coarse_of(const dmg_ctx *c, int lev) {
+    Level v = c->L[lev + 1];
+    v.g.nb = c->L[lev].g.nb;
+    return v;
+}
+
 template <class T>
 dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s) {
-    Level &l = c->L[lev], &cl = c->L[lev + 1];
+    Level &l = c->L[lev];
+    Level cl = coarse_of(c, lev);
     ProfScope ps(c, DMG_KERNEL_RESTRICT, lev, sizeof(T) == 4, s);
     if (c->dim == 2) {   // full defect and 9-point full weighting
         TRY(dispatch<T>(c, l, [&](auto cf) {
@@ -514,7 +536,8 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
 // FP32 launch that stores only the colour's new values (k_prolong_smooth32);
 // the half-sweep of the other colour must follow.
 dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
-    Level &l = c->L[lev], &cl = c->L[lev + 1];
+    Level &l = c->L[lev];
+    Level cl = coarse_of(c, lev);
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
     return with_coef32(c, l, [&](auto cf) {
         constexpr bool H = decltype(cf)::harmonic;
@@ -531,14 +554,15 @@ dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
 
 template <class T>
 dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
-    Level &l = c->L[lev], &cl = c->L[lev + 1];
+    Level &l = c->L[lev];
+    Level cl = coarse_of(c, lev);
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
     if (c->dim == 2) {
-        dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, c->nb);   // coarse cells
+        dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, l.g.nb);   // coarse cells
         dmgk::k_prolong_add2<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
         return check_launch(c, "prolong");
     }
-    dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, c->nb * (cl.g.nz - 1));   // coarse cells
+    dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, l.g.nb * (cl.g.nz - 1));   // coarse cells
     dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
     return check_launch(c, "prolong");
 }
@@ -1126,19 +1150,43 @@ dmg_status autotune(dmg_ctx *c, cudaStream_t s) {
     return DMG_OK;
 }
 
-// Level l of one slot (a single sample, pointers at its part; slot < 0: the
-// level itself with every sample).
-Level level_view(const dmg_ctx *c, int l, int slot) {
+// Samples [first, first + count) of level l (pointers at the first one's part)
+Level level_range(const dmg_ctx *c, int l, int first, int count) {
     Level v = c->L[l];
-    if (slot < 0) return v;
-    const long long o = (long long)slot * v.g.sb;
-    v.g.nb = 1;
-    v.n = (size_t)v.g.sb;
+    const long long o = (long long)first * v.g.sb;
+    v.g.nb = count;
+    v.n = (size_t)v.g.sb * count;
     for (double **q : {&v.u, &v.f, &v.r, &v.cx, &v.cy, &v.cz, &v.diag, &v.invd, &v.D, &v.mu})
         if (*q) *q += o;
     for (float **q : {&v.u32, &v.f32, &v.r32, &v.Dh32, &v.mu32})
         if (*q) *q += o;
     return v;
+}
+
+// Level l of one slot (a single sample, pointers at its part; slot < 0: the
+// level itself with every sample).
+Level level_view(const dmg_ctx *c, int l, int slot) {
+    if (slot < 0) return c->L[l];
+    return level_range(c, l, slot, 1);
+}
+
+// a slot's finest level and its outputs there (U0: forward solution, T1, T2:
+// tangent coefficients or gradients)
+struct SlotTop {
+    int lev;
+    Level v;
+    double *U0, *T1, *T2;
+};
+SlotTop slot_top(const dmg_ctx *c, int slot) {
+    SlotTop t;
+    t.lev = c->top_of[slot];
+    t.v = level_view(c, t.lev, slot);
+    t.v.h = c->p.h;   // every slot's finest grid has the spacing h
+    const long long o = (long long)(slot - c->top_first[t.lev]) * t.v.g.sb;
+    t.U0 = c->U0l[t.lev] + o;
+    t.T1 = c->T1l[t.lev] + o;
+    t.T2 = c->T2l[t.lev] + o;
+    return t;
 }
 
 // The coefficient hierarchy of every sample (slot < 0) or of one slot
@@ -1149,10 +1197,12 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     const dmg_params *p = &c->p;
     const bool mixed = p->precision == DMG_MIXED;
     Level V[kMaxLevels];
-    for (int l = 0; l < c->nlev; l++) V[l] = level_view(c, l, slot);
-    TRY(stage_in(c, D, V[0].D, false, s, slot));
-    TRY(stage_in(c, mu, V[0].mu, false, s, slot));
-    for (int l = 1; l < c->nlev; l++) {
+    // a slot's hierarchy starts at its finest level (0 unless the context is a pyramid)
+    const int l0 = slot < 0 ? 0 : c->top_of[slot];
+    for (int l = l0; l < c->nlev; l++) V[l] = level_view(c, l, slot);
+    TRY(stage_in(c, D, V[l0].D, false, s, slot));
+    TRY(stage_in(c, mu, V[l0].mu, false, s, slot));
+    for (int l = l0 + 1; l < c->nlev; l++) {
         Level &F = V[l - 1], &C = V[l];
         if (c->dim == 2) {
             dmgk::k_coarsen2<<<grid_all2(C.g), blk(), 0, s>>>(F.g, F.D, C.g, C.D, p->coarsen);
@@ -1167,9 +1217,12 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
         TRY(check_launch(c, "coarsen"));
     }
     const int harm = p->face_mean == DMG_FACE_HARMONIC;
-    for (int l = 0; l < c->nlev; l++) {
+    for (int l = l0; l < c->nlev; l++) {
         Level &L = V[l];
-        const double ih2 = 1.0 / (L.h * L.h);
+        // spacing of level l for these samples: h on the slot's finest level,
+        // doubling per level below it (a pyramid's levels serve grids of one h)
+        const double hl = std::ldexp(c->p.h, l - l0);
+        const double ih2 = 1.0 / (hl * hl);
         if (c->dim == 2)
             dmgk::k_build_faces2<<<grid_all2(L.g), blk(), 0, s>>>(L.g, L.D, L.mu, ih2, harm, L.cx, L.cy, L.diag,
                                                                   L.invd);
@@ -1200,9 +1253,28 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     return DMG_OK;
 }
 
-dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const double *mu, cudaStream_t s) {
+// per_level (pyramid pools only): per_level[k] slots have level k as their
+// finest level, k < nper; D and mu are then not read (slots are loaded one by one)
+dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const double *mu, cudaStream_t s,
+                      const int *per_level = nullptr, int nper = 0) {
+    dmg_params pp;
+    if (per_level) {
+        if (!p) return fail(c, DMG_EINVAL, "params is NULL");
+        const int nl = count_levels(p->nx, p->ny, p->nz);
+        if (p->nz == 1) return fail(c, DMG_EINVAL, "pyramid pools are 3D only");
+        if (nper < 1 || nper > nl) return fail(c, DMG_EINVAL, "nlevels must be in [1, %d]", nl);
+        long long total = 0;
+        for (int k = 0; k < nper; k++) {
+            if (per_level[k] < 0) return fail(c, DMG_EINVAL, "slots_per_level[%d] < 0", k);
+            total += per_level[k];
+        }
+        if (total < 1 || total > 65535) return fail(c, DMG_EINVAL, "a pyramid needs 1 to 65535 slots");
+        pp = *p;
+        pp.batch = (int)total;
+        p = &pp;
+    }
     TRY(validate(c, p));
-    if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
+    if (!per_level && (!D || !mu)) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
     c->p = *p;
     c->nb = p->batch;
     const int nb = c->nb;
@@ -1210,18 +1282,37 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         for (dim3 &b : row) b = dim3(32, 8, 1);
     c->nlev = count_levels(p->nx, p->ny, p->nz);
     c->dim = p->nz == 1 ? 2 : 3;
+    c->pyramid = per_level != nullptr;
+    // samples per level and the slots whose finest level each level is
+    int nb_at[kMaxLevels];
+    {
+        int acc = 0;
+        for (int l = 0; l < c->nlev; l++) {
+            c->top_first[l] = acc;
+            c->top_count[l] = per_level ? (l < nper ? per_level[l] : 0) : (l == 0 ? nb : 0);
+            acc += c->top_count[l];
+            nb_at[l] = acc;
+        }
+        c->top_of.assign(nb, 0);
+        for (int l = 0; l < c->nlev; l++)
+            for (int b = c->top_first[l]; b < c->top_first[l] + c->top_count[l]; b++) c->top_of[b] = l;
+    }
     bool mixed = p->precision == DMG_MIXED;
     for (int l = 0; l < c->nlev; l++) {
         Level &L = c->L[l];
         if (l == 0) {
-            L.g = make_geom(p->nx, p->ny, p->nz, nb);
+            L.g = make_geom(p->nx, p->ny, p->nz, nb_at[l]);
             L.h = p->h;
         } else {
             const Level &F = c->L[l - 1];
-            L.g = make_geom((F.g.nx - 1) / 2 + 1, (F.g.ny - 1) / 2 + 1, (F.g.nz - 1) / 2 + 1, nb);
+            L.g = make_geom((F.g.nx - 1) / 2 + 1, (F.g.ny - 1) / 2 + 1, (F.g.nz - 1) / 2 + 1, nb_at[l]);
             L.h = 2.0 * F.h;
         }
-        L.n = (size_t)L.g.sb * nb;
+        if ((long long)nb_at[l] * L.g.nz > 65535)
+            return fail(c, DMG_EINVAL, "level %d: samples * nz = %lld exceeds 65535", l,
+                        (long long)nb_at[l] * L.g.nz);
+        L.n = (size_t)L.g.sb * nb_at[l];
+        if (L.n == 0) continue;   // a pyramid level above every slot
         double **f64[] = {&L.u, &L.f, &L.r, &L.cx, &L.cy, &L.cz, &L.diag, &L.invd, &L.D, &L.mu};
         for (double **q : f64) {
             TRY(dalloc(c, q, L.n));
@@ -1236,11 +1327,36 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         }
     }
     Level &L0 = c->L[0];
-    TRY(dalloc(c, &c->stage, (size_t)p->nx * p->ny * p->nz * nb));
-    TRY(dalloc(c, &c->stage2, (size_t)p->nx * p->ny * p->nz * nb));
-    for (double **q : {&c->U0, &c->T1, &c->T2, &c->T3}) {
-        TRY(dalloc(c, q, L0.n));
-        CUDA_TRY(c, cudaMemsetAsync(*q, 0, L0.n * sizeof(double), s));
+    // contiguous staging: every slot's field at its finest level, back to back
+    {
+        c->stage_off.assign(nb, 0);
+        long long acc = 0;
+        for (int b = 0; b < nb; b++) {
+            c->stage_off[b] = acc;
+            const Geom &g = c->L[c->top_of[b]].g;
+            acc += (long long)g.nx * g.ny * g.nz;
+        }
+        TRY(dalloc(c, &c->stage, (size_t)acc));
+        TRY(dalloc(c, &c->stage2, (size_t)acc));
+    }
+    if (!c->pyramid) {
+        for (double **q : {&c->U0, &c->T1, &c->T2, &c->T3}) {
+            TRY(dalloc(c, q, L0.n));
+            CUDA_TRY(c, cudaMemsetAsync(*q, 0, L0.n * sizeof(double), s));
+        }
+        c->U0l[0] = c->U0;
+        c->T1l[0] = c->T1;
+        c->T2l[0] = c->T2;
+    } else {
+        for (int l = 0; l < c->nlev; l++) {
+            const size_t n = (size_t)c->L[l].g.sb * c->top_count[l];
+            if (n == 0) continue;
+            for (double **q : {&c->U0l[l], &c->T1l[l], &c->T2l[l]}) {
+                TRY(dalloc(c, q, n));
+                CUDA_TRY(c, cudaMemsetAsync(*q, 0, n * sizeof(double), s));
+            }
+        }
+        c->U0 = c->U0l[0];
     }
     TRY(dalloc(c, &c->partial, (size_t)kNormBlocks * nb));
     TRY(dalloc(c, &c->red, (size_t)kSlots * nb));
@@ -1273,7 +1389,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         memset(c->hact_a, 0, nb * sizeof(int));
     }
     c->slots.assign(nb, Slot());
-    for (Slot &sl : c->slots) sl.loaded = true;   // setup builds every sample's hierarchy
+    for (Slot &sl : c->slots) sl.loaded = !c->pyramid;   // setup builds every sample's hierarchy (pyramid: none)
     c->bcyc.assign(nb, 0);
     c->brel.assign(nb, 0.0);
     Level &LC0 = c->L[c->nlev - 1];
@@ -1303,6 +1419,16 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         c->tail_first[t] = first;
         c->tail_smem[t] = first < c->nlev ? bytes(first) : 0;
     }
+    if (c->pyramid) {
+        // every slot's finest level lies above the single-CTA tail (which stages
+        // the levels below from the coarse defects) and the coarsest level
+        const int t = mixed ? 1 : 0;
+        for (int l = 0; l < c->nlev; l++)
+            if (c->top_count[l] > 0 && (l >= c->tail_first[t] || l >= c->nlev - 1))
+                return fail(c, DMG_EINVAL,
+                            "slots whose finest level is level %d (%dx%dx%d) would start inside the small-level "
+                            "tail: use larger grids", l, c->L[l].g.nx, c->L[l].g.ny, c->L[l].g.nz);
+    }
     {
         // the attribute belongs to the device's context: set it once per device
         static std::mutex mu;
@@ -1328,6 +1454,10 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     {
         cudaError_t e = cudaMallocHost(&c->hstatus, nb * sizeof(int));
         if (e != cudaSuccess) { cudaGetLastError(); return fail(c, DMG_ENOMEM, "cudaMallocHost failed"); }
+    }
+    if (c->pyramid) {   // slots get their coefficients from dmg_slot_load
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        return DMG_OK;
     }
     TRY(build_coefficients(c, -1, D, mu, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1487,6 +1617,14 @@ bool any_busy(const dmg_ctx *c) {
     return false;
 }
 
+// calls on the whole context (every sample at level 0): not while slots run
+// phases, and not on a pyramid pool, whose slots live on different levels
+dmg_status need_whole(dmg_ctx *c) {
+    if (c->pyramid) return fail(c, DMG_EINVAL, "a pyramid pool serves its slots only (dmg_slot_* calls)");
+    if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+    return DMG_OK;
+}
+
 dmg_status check_slot(dmg_ctx *c, int slot) {
     if (c->dim == 2) return fail(c, DMG_EINVAL, "the slot interface is 3D only");
     if (slot < 0 || slot >= c->nb) return fail(c, DMG_EINVAL, "slot %d out of range [0, %d)", slot, c->nb);
@@ -1511,7 +1649,7 @@ dmg_status slot_load_impl(dmg_ctx *c, int slot, const double *D, const double *m
 // every coarsest matrix is positive definite.
 dmg_status set_coefficients_impl(dmg_ctx *c, const double *D, const double *mu, cudaStream_t s) {
     if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
-    if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+    TRY(need_whole(c));
     TRY(build_coefficients(c, -1, D, mu, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     for (Slot &sl : c->slots) {
@@ -1540,8 +1678,8 @@ dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, con
         return fail(c, DMG_EINVAL, "the right-hand side must not be NULL");
     if (phase == DMG_PHASE_TANGENT && (b || d) && !sl.have_fwd)
         return fail(c, DMG_EINVAL, "slot %d has no forward solution for a D or mu tangent", slot);
-    Level l = level_view(c, 0, slot);
-    const long long o = (long long)slot * l.g.sb;
+    const SlotTop top = slot_top(c, slot);   // the slot's finest level
+    const Level &l = top.v;
     CUDA_TRY(c, cudaMemsetAsync(l.u, 0, l.n * sizeof(double), s));
     if (a) {
         TRY(stage_in(c, a, l.f, false, s, slot));
@@ -1549,10 +1687,10 @@ dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, con
         CUDA_TRY(c, cudaMemsetAsync(l.f, 0, l.n * sizeof(double), s));
     }
     if (phase == DMG_PHASE_TANGENT && (b || d)) {
-        if (b) TRY(stage_in(c, b, c->T1 + o, false, s, slot));
-        if (d) TRY(stage_in(c, d, c->T2 + o, false, s, slot));
+        if (b) TRY(stage_in(c, b, top.T1, false, s, slot));
+        if (d) TRY(stage_in(c, d, top.T2, false, s, slot));
         const double ih2 = 1.0 / (l.h * l.h);
-        dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, c->U0 + o, b ? c->T1 + o : nullptr, d ? c->T2 + o : nullptr,
+        dmgk::k_dA<<<grid_int(l.g), blk(), 0, s>>>(l.g, top.U0, b ? top.T1 : nullptr, d ? top.T2 : nullptr,
                                                    l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC, l.f);
         TRY(check_launch(c, "dA"));
     }
@@ -1580,24 +1718,60 @@ dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, con
     return DMG_OK;
 }
 
-// the step graph of one direction: t = 0 forward and tangent phases, 1 adjoint
+// ||f - A u||^2 (FP64) of the slots whose finest level is lev -> red[slot][0];
+// with r32: their FP32 right-hand sides r * 2^-e_prev
+dmg_status top_resid_norm(dmg_ctx *c, int lev, bool r32, cudaStream_t s) {
+    const int first = c->top_first[lev], cnt = c->top_count[lev];
+    const Level v = level_range(c, lev, first, cnt);
+    const int *act = c->mask ? c->mask + first : nullptr;
+    {
+        ProfScope ps(c, DMG_KERNEL_RESIDUAL, lev, 0, s);
+        dmgk::k_resid_norm<double><<<dim3(kNormBlocks, cnt), 256, 0, s>>>(
+            v.g, v.u, v.f, coef64(v), (double *)nullptr, r32 ? v.f32 : nullptr, c->ms + first,
+            c->partial + (size_t)kNormBlocks * first, act);
+        TRY(check_launch(c, "resid_norm"));
+    }
+    dmgk::k_reduce_final<<<cnt, 256, 0, s>>>(c->partial + (size_t)kNormBlocks * first, kNormBlocks,
+                                             c->red + (size_t)kSlots * first, 0, act);
+    return check_launch(c, "reduce");
+}
+
+// the step graph of one direction: t = 0 forward and tangent phases, 1 adjoint.
+// In a pyramid the V-cycle starts at the finest level that holds slots and
+// every level takes the samples it holds; each slot's refinement (update,
+// residual, norm) runs on its own finest level.
 dmg_status capture_step(dmg_ctx *c, int t) {
-    Level &l = c->L[0];
     const bool transposed = t == 1;
     c->mask = t ? c->act_a : c->act;
+    int lev0 = 0;
+    while (c->top_count[lev0] == 0) lev0++;
     return capture(c, c->g_srv[t], [&](cudaStream_t cs) -> dmg_status {
         if (c->p.precision == DMG_MIXED) {
-            dmgk::k_zero_interior<float><<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u32, c->mask);
-            TRY(check_launch(c, "zero"));
-            for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
-            dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
-            TRY(check_launch(c, "update"));
-            TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
+            for (int lev = 0; lev < c->nlev; lev++) {
+                if (c->top_count[lev] == 0) continue;
+                const int first = c->top_first[lev];
+                const Level v = level_range(c, lev, first, c->top_count[lev]);
+                dmgk::k_zero_interior<float><<<grid_int(v.g), blk(), 0, cs>>>(v.g, v.u32,
+                                                                              c->mask ? c->mask + first : nullptr);
+                TRY(check_launch(c, "zero"));
+            }
+            for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, lev0, transposed, cs));
+            for (int lev = 0; lev < c->nlev; lev++) {
+                if (c->top_count[lev] == 0) continue;
+                const int first = c->top_first[lev];
+                const Level v = level_range(c, lev, first, c->top_count[lev]);
+                dmgk::k_update<<<grid_int(v.g), blk(), 0, cs>>>(v.g, v.u, v.u32, c->ms + first,
+                                                                c->mask ? c->mask + first : nullptr);
+                TRY(check_launch(c, "update"));
+                TRY(top_resid_norm(c, lev, true, cs));
+            }
             dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);
             return check_launch(c, "mix_next");
         }
-        TRY(vcycle<double>(c, 0, transposed, cs));
-        return resid_norm_async(c, l.u, l.f, nullptr, 0, c->mask, cs);
+        TRY(vcycle<double>(c, lev0, transposed, cs));
+        for (int lev = 0; lev < c->nlev; lev++)
+            if (c->top_count[lev] > 0) TRY(top_resid_norm(c, lev, false, cs));
+        return DMG_OK;
     });
 }
 
@@ -1681,8 +1855,8 @@ dmg_status step_finish_impl(dmg_ctx *c, cudaStream_t s, int *ended_out, int *nen
     for (int b : ended) {
         Slot &sl = c->slots[b];
         if (sl.phase == DMG_PHASE_FORWARD && (sl.status == DMG_OK || sl.status == DMG_ENOCONV)) {
-            const Level l = level_view(c, 0, b);
-            TRY(dcopy(c, c->U0 + (long long)b * l.g.sb, (const double *)l.u, l.n, s));
+            const SlotTop top = slot_top(c, b);
+            TRY(dcopy(c, top.U0, (const double *)top.v.u, top.v.n, s));
             sl.have_fwd = true;
         }
         c->bcyc[b] = sl.steps * per_step;
@@ -1703,19 +1877,19 @@ dmg_status slot_read_impl(dmg_ctx *c, int slot, double *u, double *x, double *Db
     if ((u || Dbar || mubar) && !sl.have_fwd) return fail(c, DMG_EINVAL, "slot %d has no forward solution", slot);
     if ((Dbar || mubar) && sl.phase != DMG_PHASE_ADJOINT)
         return fail(c, DMG_EINVAL, "Dbar and mubar need a finished adjoint phase");
-    const Level l = level_view(c, 0, slot);
-    const long long o = (long long)slot * l.g.sb;
-    if (u) TRY(stage_out(c, c->U0 + o, u, s, slot));
+    const SlotTop top = slot_top(c, slot);
+    const Level &l = top.v;
+    if (u) TRY(stage_out(c, top.U0, u, s, slot));
     if (x) TRY(stage_out(c, l.u, x, s, slot));
     if (Dbar || mubar) {
         const double ih2 = 1.0 / (l.h * l.h);
-        ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
-        dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0 + o, l.u, l.D, ih2,
+        ProfScope ps(c, DMG_KERNEL_GRAD, top.lev, 0, s);
+        dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, top.U0, l.u, l.D, ih2,
                                                      c->p.face_mean == DMG_FACE_HARMONIC,
-                                                     Dbar ? c->T1 + o : nullptr, mubar ? c->T2 + o : nullptr);
+                                                     Dbar ? top.T1 : nullptr, mubar ? top.T2 : nullptr);
         TRY(check_launch(c, "grad"));
-        if (Dbar) TRY(stage_out(c, c->T1 + o, Dbar, s, slot));
-        if (mubar) TRY(stage_out(c, c->T2 + o, mubar, s, slot));
+        if (Dbar) TRY(stage_out(c, top.T1, Dbar, s, slot));
+        if (mubar) TRY(stage_out(c, top.T2, mubar, s, slot));
     }
     return DMG_OK;
 }
@@ -1865,7 +2039,7 @@ dmg_status rev_plain(dmg_ctx *c, int l, cudaStream_t s) {
 dmg_status vjp_unrolled_impl(dmg_ctx *c, const double *q, const double *w, int m, int stride, double *u,
                              double *qbar, double *Dbar, double *mubar, cudaStream_t s) {
     if (c->dim == 2) return fail(c, DMG_EINVAL, "dmg_vjp_unrolled is 3D only");
-    if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+    TRY(need_whole(c));
     if (!q || !w) return fail(c, DMG_EINVAL, "q and w must not be NULL");
     if (m < 1 || m > 100000) return fail(c, DMG_EINVAL, "m must be in [1, 100000]");
     if (stride < 0) return fail(c, DMG_EINVAL, "stride must be >= 0");
@@ -2002,9 +2176,31 @@ dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, voi
     return DMG_OK;
 }
 
+dmg_status dmg_setup_pyramid(const dmg_params *p, const int *slots_per_level, int nlevels, void *stream,
+                             dmg_ctx **out) {
+    if (!out) return DMG_EINVAL;
+    Range r("dmg_setup_pyramid");
+    *out = nullptr;
+    if (!slots_per_level) {
+        snprintf(g_setup_err, sizeof(g_setup_err), "slots_per_level must not be NULL");
+        return DMG_EINVAL;
+    }
+    dmg_ctx *c = new (std::nothrow) dmg_ctx();
+    if (!c) return DMG_ENOMEM;
+    dmg_status st = setup_impl(c, p, nullptr, nullptr, S(stream), slots_per_level, nlevels);
+    if (st != DMG_OK) {
+        memcpy(g_setup_err, c->err, sizeof(g_setup_err));
+        dmg_destroy(c);
+        return st;
+    }
+    g_setup_err[0] = 0;
+    *out = c;
+    return DMG_OK;
+}
+
 dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!q || !u) return fail(c, DMG_EINVAL, "q and u must not be NULL");
         info_reset(info);
         cudaStream_t s = S(stream);
@@ -2021,7 +2217,7 @@ dmg_status dmg_solve(dmg_ctx *c, const double *q, double *u, dmg_info *info, voi
 dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
                    double *du, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!du) return fail(c, DMG_EINVAL, "du must not be NULL");
         if ((dD || dmu) && !u) return fail(c, DMG_EINVAL, "u is needed for a D or mu tangent");
         info_reset(info);
@@ -2056,7 +2252,7 @@ dmg_status dmg_jvp(dmg_ctx *c, const double *u, const double *dq, const double *
 dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u, double *qbar, double *Dbar,
                          double *mubar, dmg_info *info_fwd, dmg_info *info_adj, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!q || !w) return fail(c, DMG_EINVAL, "q and w must not be NULL");
         info_reset(info_fwd);
         info_reset(info_adj);
@@ -2119,7 +2315,7 @@ dmg_status dmg_solve_vjp_many(dmg_ctx *c, int npairs, const double *const *q, co
                               double *const *u, double *const *qbar, double *const *Dbar, double *const *mubar,
                               dmg_info *info_fwd, dmg_info *info_adj, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (info_fwd) for (int i = 0; i < npairs; i++) info_reset(info_fwd + i);
         if (info_adj) for (int i = 0; i < npairs; i++) info_reset(info_adj + i);
         return solve_vjp_many_impl(c, npairs, q, w, u, qbar, Dbar, mubar, info_fwd, info_adj, S(stream));
@@ -2129,7 +2325,7 @@ dmg_status dmg_solve_vjp_many(dmg_ctx *c, int npairs, const double *const *q, co
 dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, double *qbar, double *Dbar,
                    double *mubar, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!w) return fail(c, DMG_EINVAL, "w must not be NULL");
         if ((Dbar || mubar) && !u) return fail(c, DMG_EINVAL, "u is needed for Dbar / mubar");
         if (cycles < 0) return fail(c, DMG_EINVAL, "cycles must be >= 0");
@@ -2211,7 +2407,7 @@ extern "C" {
 dmg_status dmg_response(dmg_ctx *c, const double *q, double edge, double *Le, double *u, dmg_info *info,
                         void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!q || !Le) return fail(c, DMG_EINVAL, "q and Le must not be NULL");
         dmgk::Margins m;
         TRY(margins(c, edge, &m));
@@ -2233,7 +2429,7 @@ dmg_status dmg_response(dmg_ctx *c, const double *q, double edge, double *Le, do
 dmg_status dmg_response_jvp(dmg_ctx *c, const double *u, const double *dq, const double *dD, const double *dmu,
                             double edge, double *dLe, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!u || !dLe) return fail(c, DMG_EINVAL, "u and dLe must not be NULL");
         dmgk::Margins m;
         TRY(margins(c, edge, &m));
@@ -2268,7 +2464,7 @@ dmg_status dmg_response_jvp(dmg_ctx *c, const double *u, const double *dq, const
 dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, double edge, double *qbar,
                             double *Dbar, double *mubar, dmg_info *info, void *stream) {
     return guarded(c, [&]() -> dmg_status {
-        if (any_busy(c)) return fail(c, DMG_EINVAL, "slots are running phases");
+        TRY(need_whole(c));
         if (!rbar) return fail(c, DMG_EINVAL, "rbar must not be NULL");
         if ((Dbar || mubar) && !u) return fail(c, DMG_EINVAL, "u is needed for Dbar / mubar");
         dmgk::Margins m;
@@ -2304,6 +2500,7 @@ dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, dou
 dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *out, void *stream) {
     return guarded(c, [&]() -> dmg_status {
         if (!q || !u || !out) return fail(c, DMG_EINVAL, "q, u and out must not be NULL");
+        if (c->pyramid) return fail(c, DMG_EINVAL, "a pyramid pool serves its slots only (dmg_slot_* calls)");
         cudaStream_t s = S(stream);
         Level &l = c->L[0];
         TRY(stage_in(c, q, c->T3, false, s));

@@ -64,7 +64,8 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
            "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp",
-           "dmg_debug_oob_count", "dmg_set_coefficients", "dmg_probe_fma", "dmg_solve_vjp_many")
+           "dmg_debug_oob_count", "dmg_set_coefficients", "dmg_probe_fma", "dmg_solve_vjp_many",
+           "dmg_setup_pyramid")
 
 _lib = None
 
@@ -120,6 +121,7 @@ def lib():
             "dmg_set_coefficients": (i, [vp, vp, vp, vp]),
             "dmg_probe_fma": (i, [i, P(d), vp]),
             "dmg_solve_vjp_many": (i, [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "dmg_setup_pyramid": (i, [P(dmg_params), P(i), i, vp, P(vp)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -185,6 +187,15 @@ def dmg_setup(params: dmg_params, D, mu, stream=None):
     n = params.nx * params.ny * params.nz * max(params.batch, 1)
     out = ctypes.c_void_p()
     st = lib().dmg_setup(ctypes.byref(params), _ptr(D, n), _ptr(mu, n), _stream(stream), ctypes.byref(out))
+    return st, (out if st == DMG_OK else None)
+
+
+def dmg_setup_pyramid(params: dmg_params, slots_per_level, stream=None):
+    """Returns (status, ctx): a pool whose slots_per_level[k] slots serve grids of level k of params' grid."""
+    k = len(slots_per_level)
+    arr = (ctypes.c_int * max(k, 1))(*[int(x) for x in slots_per_level])
+    out = ctypes.c_void_p()
+    st = lib().dmg_setup_pyramid(ctypes.byref(params), arr, k, _stream(stream), ctypes.byref(out))
     return st, (out if st == DMG_OK else None)
 
 

@@ -96,27 +96,64 @@ class Request:
         return 8 * n * (len(INPUT_KEYS[self.kind]) + len(OUTPUT_KEYS[self.kind]))
 
 
-class Pool:
-    """The slots of one grid shape: a context with batch = slots."""
+def coarse_shape(shape):
+    """The next level of the grid hierarchy (Sec. 2.2): (n - 1) / 2 + 1 per axis."""
+    return tuple((n - 1) // 2 + 1 for n in shape)
 
-    def __init__(self, shape, h, slots, params, device):
+
+def chains(shapes):
+    """Group grid shapes into chains of the hierarchy: each next shape is the
+    coarse level of the previous one (257^3, 129^3, 65^3, ...). A chain of more
+    than one shape is served by one pyramid pool."""
+    left = sorted({tuple(s) for s in shapes}, key=lambda s: -int(np.prod(s)))
+    out = []
+    while left:
+        chain = [left.pop(0)]
+        while True:
+            nxt = coarse_shape(chain[-1])
+            if nxt in left:
+                left.remove(nxt)
+                chain.append(nxt)
+            else:
+                break
+        out.append(chain)
+    return out
+
+
+class Pool:
+    """Slots for one grid shape (a context with batch = slots), or for a chain
+    of shapes that share their coarse levels (a pyramid context: each level's
+    kernels run for the slots of every shape that holds the level)."""
+
+    def __init__(self, shape, h, slots, params, device, chain=None, chain_slots=None):
         import torch
         self.torch = torch
-        self.shape, self.slots = tuple(shape), int(slots)
+        self.chain = [tuple(s) for s in (chain or [shape])]
+        per = [int(x) for x in (chain_slots or [slots])]
+        self.shape, self.slots = self.chain[0], sum(per)
         self.n = int(np.prod(self.shape))
         self.device = device
         self.stream = _dev.stream(device)
         nz, ny, nx = self.shape
-        p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.slots, **params)
-        with _dev.use(self.stream):
-            ones = torch.ones((self.slots,) + self.shape, dtype=torch.float64, device=device)
-            st, self.ctx = dmg.dmg_setup(p, ones, torch.zeros_like(ones), stream=self.stream)
+        if len(self.chain) == 1:
+            p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), batch=self.slots, **params)
+            with _dev.use(self.stream):
+                ones = torch.ones((self.slots,) + self.shape, dtype=torch.float64, device=device)
+                st, self.ctx = dmg.dmg_setup(p, ones, torch.zeros_like(ones), stream=self.stream)
+            del ones
+        else:
+            p = dmg.dmg_default_params(nx=nx, ny=ny, nz=nz, h=float(h), **params)
+            st, self.ctx = dmg.dmg_setup_pyramid(p, per, stream=self.stream)
         _dev.sync(self.stream)
-        del ones
         if st != dmg.DMG_OK:
             raise dmg.DMGError(st, dmg.dmg_last_error(None))
         self.bytes = dmg.dmg_device_bytes(self.ctx)
-        self.free = list(range(self.slots - 1, -1, -1))
+        # slots of each shape: the pyramid numbers them level by level
+        self.free_by = {}
+        first = 0
+        for s_, k in zip(self.chain, per):
+            self.free_by[s_] = list(range(first + k - 1, first - 1, -1))
+            first += k
         self.busy = {}        # slot -> [request, phase index, inputs]
         self.steps = 0
         self.step_event = None      # recorded after the launched step's read-back
@@ -131,19 +168,29 @@ class Pool:
         if st != dmg.DMG_OK:
             raise dmg.DMGError(st, dmg.dmg_last_error(self.ctx))
 
+    @property
+    def free(self):
+        """Free slots of every shape (the pool can admit when this is not empty)."""
+        return [s for v in self.free_by.values() for s in v]
+
+    def has_free(self, shape):
+        return bool(self.free_by.get(tuple(shape)))
+
     def admit(self, req, now):
-        """Load the request into a free slot and stage its forward phase. If its
-        inputs cannot be made or the library refuses them, the slot goes back
-        to the free list and the exception propagates."""
-        slot = self.free.pop()
+        """Load the request into a free slot of its shape and stage its forward
+        phase. If its inputs cannot be made or the library refuses them, the
+        slot goes back to the free list and the exception propagates."""
+        free = self.free_by[tuple(req.shape)]
+        slot = free.pop()
+        n = int(np.prod(req.shape))
         try:
             with _dev.use(self.stream):
                 x = req.make_inputs(self.device)
-            self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=self.n))
+            self._check(dmg.dmg_slot_load(self.ctx, slot, x["D"], x["mu"], self.stream, n=n))
             self._check(dmg.dmg_slot_begin(self.ctx, slot, dmg.DMG_PHASE_FORWARD, x["q"], None, None, self.stream,
-                                           n=self.n))
+                                           n=n))
         except Exception:
-            self.free.append(slot)
+            free.append(slot)
             raise
         self.busy[slot] = [req, 0, x]
         req.t_admit = now
@@ -172,6 +219,7 @@ class Pool:
         for slot in ended:
             entry = self.busy[slot]
             req, ph, x = entry
+            n = int(np.prod(req.shape))
             _, status, cyc, rel = dmg.dmg_slot_result(self.ctx, slot)
             req.cycles.append(cyc)
             req.rel.append(rel)
@@ -184,22 +232,21 @@ class Pool:
                     args = (x["dq"], x["dD"], x["dmu"])
                 else:
                     args = (x["w"], None, None)
-                self._check(dmg.dmg_slot_begin(self.ctx, slot, nxt, *args, self.stream, n=self.n))
+                self._check(dmg.dmg_slot_begin(self.ctx, slot, nxt, *args, self.stream, n=n))
                 continue
             req.status = status
             if ok:
                 with _dev.use(self.stream):
-                    out = {k: torch.empty(self.shape, dtype=torch.float64, device=self.device)
+                    out = {k: torch.empty(tuple(req.shape), dtype=torch.float64, device=self.device)
                            for k in OUTPUT_KEYS[req.kind]}
                 if req.kind == "fwd":
-                    self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], None, None, None, self.stream,
-                                                  n=self.n))
+                    self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], None, None, None, self.stream, n=n))
                 elif req.kind == "jvp":
                     self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], out["du"], None, None, self.stream,
-                                                  n=self.n))
+                                                  n=n))
                 else:
                     self._check(dmg.dmg_slot_read(self.ctx, slot, out["u"], out["qbar"], out["Dbar"],
-                                                  out["mubar"], self.stream, n=self.n))
+                                                  out["mubar"], self.stream, n=n))
                 req.outputs = out
             done.append((slot, req))
         if done:
@@ -208,7 +255,7 @@ class Pool:
                 req.pool_steps = (req.pool_steps[0], self.steps)
                 self.busy[slot][2] = None
                 del self.busy[slot]
-                self.free.append(slot)
+                self.free_by[tuple(req.shape)].append(slot)
             self.completing.append((ev, [r for _, r in done]))
 
     def completed(self, clock):
@@ -246,11 +293,18 @@ class Server:
     budget_bytes: device memory for the pools and the requests' own tensors;
     pool_fraction of it goes to the pools (slots are fixed at start), the rest
     bounds the inputs and outputs of admitted requests. slots: an explicit
-    {shape: slots} plan instead of the budget split.
+    {shape: slots} plan instead of the budget split. pyramid: shapes that form a
+    chain of the grid hierarchy (257^3, 129^3, 65^3, ...) share one pyramid
+    pool, whose launches batch the same level across shapes; a chain the
+    library refuses (a shape too small to start above the small-level tail)
+    falls back to one pool per shape. Off by default: a pyramid steps all its
+    slots together, so small requests advance at the rate of the largest grid's
+    step, and on the benchmark's mix separate pools (each on its own stream)
+    serve more requests per second.
     """
 
     def __init__(self, shapes, h=0.5, budget_bytes=80e9, params=None, device="cuda", max_slots=64,
-                 slots=None, pool_fraction=0.75):
+                 slots=None, pool_fraction=0.75, pyramid=False):
         params = dict(params or {})
         self.h, self.device = h, device
         self.budget = float(budget_bytes)
@@ -262,15 +316,36 @@ class Server:
                 probe[s] = p.bytes
                 p.close()
             slots = plan_slots(shapes, probe, pool_fraction * self.budget, max_slots)
-        self.pools = {s: Pool(s, h, slots[s], params, device) for s in shapes}
-        self.pool_bytes = sum(p.bytes for p in self.pools.values())
+        self.slots = {s: slots[s] for s in shapes}
+        self.pools = {}
+        for chain in (chains(shapes) if pyramid else [[s] for s in shapes]):
+            pool = None
+            if len(chain) > 1:
+                try:
+                    pool = Pool(chain[0], h, None, params, device, chain=chain, chain_slots=[slots[s] for s in chain])
+                except dmg.DMGError:
+                    pool = None
+            if pool is not None:
+                for s in chain:
+                    self.pools[s] = pool
+            else:
+                for s in chain:
+                    self.pools[s] = Pool(s, h, slots[s], params, device)
+        self.pool_bytes = sum(p.bytes for p in self.unique_pools())
         if self.pool_bytes > self.budget:
             raise ValueError("pools need %.1f GB, above the budget of %.1f GB" % (self.pool_bytes / 1e9,
                                                                                    self.budget / 1e9))
         self.io_bytes = 0
 
-    def close(self):
+    def unique_pools(self):
+        out = []
         for p in self.pools.values():
+            if all(p is not q for q in out):
+                out.append(p)
+        return out
+
+    def close(self):
+        for p in self.unique_pools():
             p.close()
 
     def _admit(self, queue, now):
@@ -287,7 +362,7 @@ class Server:
             req = queue.popleft()
             pool = self.pools[tuple(req.shape)]
             need = req.io_bytes()
-            if (req.shape in blocked or not pool.free or
+            if (req.shape in blocked or not pool.has_free(req.shape) or
                     self.pool_bytes + self.io_bytes + need > self.budget):
                 blocked.add(req.shape)
                 kept.append(req)
@@ -314,7 +389,7 @@ class Server:
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
         served = []
-        pools = list(self.pools.values())
+        pools = self.unique_pools()
         while pending or queue or not all(p.idle() for p in pools):
             now = clock()
             while pending and (not realtime or pending[0].arrival <= now):

@@ -88,6 +88,29 @@ def serving():
     finally:
         server.close()
 run("serving", serving)
+
+def pyramid(prec):
+    shapes = [(65, 65, 65), (33, 33, 33)]
+    server = serve.Server(shapes, slots={s: 2 for s in shapes}, params=dict(precision=prec), budget_bytes=8e9,
+                          pyramid=True)
+    try:
+        assert len(server.unique_pools()) == 1
+        served, st = server.run(serve.poisson_stream(6, 2000.0, shapes, seed=6))
+        assert st["ok"] == 6
+    finally:
+        server.close()
+run("pyramid p0", lambda: pyramid(0))
+run("pyramid p1", lambda: pyramid(1))
+
+def many():
+    w = inputs.vi_batch(17, 2, seed=7)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=1)
+    hq, hw = np.ascontiguousarray(w["q"]), np.ascontiguousarray(w["w"])
+    outs = [[np.zeros(w["q"].shape) for _ in range(2)] for _ in range(4)]
+    assert dmg.dmg_solve_vjp_many(S.ctx, [hq, hq], [hw, hw], *outs, n=S.n) == dmg.DMG_OK
+    S.set_coefficients(T(w["D"]), T(w["mu"]))
+    S.close()
+run("solve_vjp_many, set_coefficients", many)
 torch.cuda.synchronize()
 print(json.dumps(dict(runs=runs, oob=dmg.dmg_debug_oob_count())))
 '''

@@ -129,3 +129,54 @@ def test_budget_limits_admission(serve):
     assert stats["ok"] == 4
     iv = sorted(r.pool_steps for r in served)
     assert all(a2 >= b1 for (_, b1), (a2, _) in zip(iv, iv[1:]))
+
+
+PYRAMID = [(65, 65, 65), (33, 33, 33)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pyramid_pool_batches_levels_across_shapes(serve, precision):
+    # 65^3 and 33^3 requests share one pyramid pool: the 65^3 requests' second
+    # level and the 33^3 requests' finest level run in the same launches. Every
+    # result matches the oracle and is bit for bit the request alone.
+    from paper_2608_00760_b300 import dmg
+    reqs = serve.poisson_stream(12, rate=2000.0, shapes=PYRAMID, seed=21)
+    server = serve.Server(PYRAMID, slots={s: 3 for s in PYRAMID}, params=dict(precision=precision),
+                          budget_bytes=16e9, pyramid=True)
+    try:
+        pools = server.unique_pools()
+        assert len(pools) == 1 and pools[0].chain == PYRAMID and pools[0].slots == 6
+        served, stats = server.run(reqs)
+    finally:
+        server.close()
+    assert stats["ok"] == 12 and {r.shape for r in served} == set(PYRAMID)
+    for r in served:
+        ref = oracle_outputs(r)
+        for k in ref:
+            assert_close(r.outputs[k], ref[k], TOL_CONV, (r.rid, r.kind, r.shape, k))
+        alone = serve.run_alone(r, params=dict(precision=precision))
+        for k in alone:
+            assert torch.equal(r.outputs[k], alone[k]), (r.rid, r.kind, r.shape, k)
+        assert r.status == dmg.DMG_OK
+
+
+def test_pyramid_refusals(serve):
+    from paper_2608_00760_b300 import dmg
+    # a 17^3 level lies inside the FP32 small-level tail: refused, the server
+    # falls back to one pool per shape
+    p = dmg.dmg_default_params(nx=33, ny=33, nz=33, h=0.5, precision=dmg.DMG_MIXED)
+    st, ctx = dmg.dmg_setup_pyramid(p, [2, 2])
+    assert st == dmg.DMG_EINVAL and ctx is None and "tail" in dmg.dmg_last_error(None)
+    shapes = [(33, 33, 33), (17, 17, 17)]
+    server = serve.Server(shapes, slots={s: 1 for s in shapes}, params=dict(precision=1), budget_bytes=8e9,
+                          pyramid=True)
+    assert len(server.unique_pools()) == 2
+    server.close()
+    # whole-context calls are refused on a pyramid
+    p = dmg.dmg_default_params(nx=65, ny=65, nz=65, h=0.5)
+    st, ctx = dmg.dmg_setup_pyramid(p, [1, 1])
+    assert st == dmg.DMG_OK
+    q = torch.zeros((65, 65, 65), dtype=torch.float64, device="cuda")
+    assert dmg.dmg_solve(ctx, q, torch.empty_like(q), n=q.numel()) == dmg.DMG_EINVAL
+    assert "pyramid" in dmg.dmg_last_error(ctx)
+    dmg.dmg_destroy(ctx)

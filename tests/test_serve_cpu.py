@@ -356,3 +356,12 @@ def test_a_refused_slot_load_ends_that_request_with_the_library_status(fake, mon
     assert by[7].status == real_dmg.DMG_ENOMEM and by[7].error.startswith("DMGError")
     assert by[8].status == real_dmg.DMG_OK and by[8].pool_steps == (0, 2)
     assert summ["ok"] == 1 and summ["p50_ms"] is not None
+
+
+def test_chains_group_shapes_of_one_hierarchy():
+    from paper_2608_00760_b300 import serve
+    shapes = [(33, 33, 33), (65, 65, 65), (129, 129, 129), (257, 257, 257), (129, 257, 257)]
+    assert serve.chains(shapes) == [[(257, 257, 257), (129, 129, 129), (65, 65, 65), (33, 33, 33)],
+                                    [(129, 257, 257)]]
+    assert serve.chains([(17, 17, 17), (9, 17, 33)]) == [[(9, 17, 33)], [(17, 17, 17)]]
+    assert serve.coarse_shape((257, 257, 129)) == (129, 129, 65)
