@@ -97,10 +97,11 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 each step then gains ~3 decades, far above the FP32 floor).
  *   batch         independent problems in the context (default 1); needs
  *                 batch * nz <= 65535.
- *   autotune      0 (default): colour kernels use 32 x 8 thread blocks; 1: dmg_setup
+ *   autotune      0 (default): colour kernels use 32 x 8 thread blocks (FP64)
+ *                 and 32 x 4 (FP32, two vertices per thread); 1: dmg_setup
  *                 times the candidate block shapes of the half-sweep on every
  *                 grid level (FP64, and FP32 in mixed mode) and keeps the
- *                 fastest (one at least 3% faster than 32 x 8). Results are
+ *                 fastest (one at least 3% faster than the default). Results are
  *                 reused within the process for the same device, precision,
  *                 grid, batch and face mean, and, if the environment variable
  *                 DMG_TUNE_CACHE names a file, read from and appended to it.
@@ -484,7 +485,8 @@ int dmg_levels(const dmg_ctx *ctx);
 dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int *nz);
 
 /* Thread-block shape (threads along the half-row, rows) of the colour kernels
-   on a level, FP32 (fp32 != 0) or FP64: 32 x 8 unless autotuned (no counterpart
+   on a level, FP32 (fp32 != 0; threads take two vertices) or FP64: 32 x 4 and
+   32 x 8 unless autotuned (no counterpart
    in the paper). DMG_EINVAL for NULL or a level out of range. */
 dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 

@@ -117,7 +117,8 @@ struct dmg_ctx {
     int dim = 3;                      // 3, or 2 for an (ny, nx) grid (nz == 1)
     int nb = 1;                       // samples in the batch
     // thread-block shape of the colour kernels (half-sweep, colour defect) per
-    // level: [0] FP64, [1] FP32; 32 x 8 unless the autotuner chose another
+    // level: [0] FP64, [1] FP32; 32 x 8 (FP64) and 32 x 4 (FP32, two vertices per
+    // thread) unless the autotuner chose another
     dim3 tb[2][kMaxLevels];
     int nlev = 0;
     Level L[kMaxLevels];
@@ -239,6 +240,12 @@ inline dim3 grid_all2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), 
 // the same with a tuned block shape b (b.x threads along the half-row, b.y rows)
 inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
+}
+// the FP32 pair kernels (k_smooth_half32, k_residual_colour32): one thread per
+// two elements of a half-row
+inline dim3 grid_pair(const Geom &g, dim3 b) {
+    const int pairs = (g.nhalf() + 1) / 2;
+    return dim3((pairs + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
 }
 
 dmg_status check_launch(dmg_ctx *c, const char *what) {
@@ -443,10 +450,10 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
             constexpr bool H = decltype(cf)::harmonic;
             const dim3 b = c->tb[1][lev];
             if (c->nb == 1)
-                dmgk::k_smooth_half32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                dmgk::k_smooth_half32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
                                                                                  nullptr);
             else
-                dmgk::k_smooth_half32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
+                dmgk::k_smooth_half32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
                                                                                 c->mask);
             return check_launch(c, "smooth");
         });
@@ -500,10 +507,10 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
                 constexpr bool H = decltype(cf)::harmonic;
                 const dim3 b = c->tb[1][lev];
                 if (c->nb == 1)
-                    dmgk::k_residual_colour32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
+                    dmgk::k_residual_colour32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
                                                                                          l.r32, nz, nullptr);
                 else
-                    dmgk::k_residual_colour32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
+                    dmgk::k_residual_colour32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
                                                                                         l.r32, nz, c->mask);
                 return check_launch(c, "residual_colour");
             }));
@@ -1032,10 +1039,14 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
 // on the level's own arrays during setup. Results are kept for the process
 // (keyed by device, precision, grid, batch and face mean) and, when the
 // environment variable DMG_TUNE_CACHE names a file, read from and appended to
-// it. A candidate replaces the default 32 x 8 only when it is at least 3% faster.
+// it. A candidate replaces the default (32 x 8 for FP64, 32 x 4 for the FP32 pair
+// kernels) only when it is at least 3% faster.
 
-const dim3 kTiles[] = {dim3(32, 8), dim3(32, 4), dim3(32, 2), dim3(64, 4), dim3(64, 2),
-                       dim3(128, 2), dim3(128, 1), dim3(16, 16), dim3(16, 8)};
+// candidates per precision; the first is the default the others must beat
+const dim3 kTiles[2][9] = {{dim3(32, 8), dim3(32, 4), dim3(32, 2), dim3(64, 4), dim3(64, 2), dim3(128, 2),
+                            dim3(128, 1), dim3(16, 16), dim3(16, 8)},
+                           {dim3(32, 4), dim3(32, 8), dim3(32, 2), dim3(64, 4), dim3(64, 2), dim3(128, 2),
+                            dim3(128, 1), dim3(16, 16), dim3(16, 8)}};
 
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune;
@@ -1089,9 +1100,9 @@ dmg_status tune_launch(dmg_ctx *c, int l, int prec, dim3 b, int color, cudaStrea
         return with_coef32(c, L, [&](auto cf) {
             constexpr bool H = decltype(cf)::harmonic;
             if (c->nb == 1)
-                dmgk::k_smooth_half32<H, false><<<grid_half(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
+                dmgk::k_smooth_half32<H, false><<<grid_pair(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
             else
-                dmgk::k_smooth_half32<H, true><<<grid_half(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
+                dmgk::k_smooth_half32<H, true><<<grid_pair(L.g, b), b, 0, s>>>(L.g, L.u32, L.f32, cf, color, nullptr);
             return check_launch(c, "tune");
         });
     }
@@ -1114,11 +1125,11 @@ dmg_status tune_level(dmg_ctx *c, int l, int prec, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
-    dim3 best = kTiles[0];
+    dim3 best = kTiles[prec][0];
     float best_ms = 0.f;
     dmg_status st = DMG_OK;
-    for (size_t q = 0; q < sizeof(kTiles) / sizeof(kTiles[0]) && st == DMG_OK; q++) {
-        const dim3 b = kTiles[q];
+    for (size_t q = 0; q < sizeof(kTiles[0]) / sizeof(kTiles[0][0]) && st == DMG_OK; q++) {
+        const dim3 b = kTiles[prec][q];
         for (int w = 0; w < 2 && st == DMG_OK; w++) st = tune_launch(c, l, prec, b, w, s);
         if (st != DMG_OK) break;
         cudaEventRecord(e0, s);
@@ -1278,8 +1289,8 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     c->p = *p;
     c->nb = p->batch;
     const int nb = c->nb;
-    for (auto &row : c->tb)
-        for (dim3 &b : row) b = dim3(32, 8, 1);
+    for (int t = 0; t < 2; t++)
+        for (dim3 &b : c->tb[t]) b = t ? dim3(32, 4, 1) : dim3(32, 8, 1);   // FP32: the pair kernels' default
     c->nlev = count_levels(p->nx, p->ny, p->nz);
     c->dim = p->nz == 1 ? 2 : 3;
     c->pyramid = per_level != nullptr;

@@ -410,21 +410,125 @@ __device__ __forceinline__ float coupled_sum32(float s, const float *u, int p, i
     return (s0 + s1) + s2;
 }
 
+// The two FP32 colour kernels below update (or take the defect of) two
+// vertices per thread: elements m and m+1 (m even) of the colour's half-row in
+// row (j, k), i.e. vertices i = 2m + par and 2m + 2 + par. Every operand then
+// comes in as one 8-byte load per pair (own values, y and z neighbours, and two
+// of the three x neighbours in the other half), which halves the memory
+// instructions of the one-vertex form and lets the DRAM stream the half-rows
+// at a higher rate. The arithmetic of each vertex is that of couplings32 /
+// coupled_sum32 and the diagonal sum above, in the same order, so results are
+// bit for bit those of the one-vertex form.
+
+// the pair of colour `color` handled by this thread: in-sample positions of
+// element m of its own half (p) and of the other half (q), the parity of i, and
+// which of the two vertices are interior
+template <bool BATCH>
+__device__ __forceinline__ bool colour_pair32(const Geom &g, int color, const int *act, long long &base, int &p,
+                                              int &q, int &par, bool &v0, bool &v1) {
+    int k, smp = 0;
+    if (BATCH) {
+        smp = zsplit(g, kInterior, k);
+        if (inactive(act, smp)) return false;
+    } else {
+        k = blockIdx.z;
+    }
+    k += 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (j > g.ny - 2) return false;
+    par = (color + j + k) & 1;                      // parity of i for this colour in row (j, k)
+    const int m = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int i0 = 2 * m + par;
+    v0 = i0 >= 1 && i0 <= g.nx - 2;
+    v1 = i0 + 2 <= g.nx - 2;
+    if (!v0 && !v1) return false;
+    base = BATCH ? (long long)smp * g.sb : 0;
+    const int row = k * (int)g.sz + j * g.sy;
+    p = row + par * g.hx + m;
+    q = row + (1 - par) * g.hx + m;
+    g.check(p - g.sz);
+    g.check(p + g.sz + 1);
+    g.check(q - 1 + 2 * par);   // the third x neighbour: q - 1 (par 0) or q + 2 (par 1)
+    g.check(q + 1);
+    return true;
+}
+
+// operands of a pair: the six couplings of each vertex and its six neighbour
+// values, in the neighbour order of couplings32 (-x, +x, -y, +y, -z, +z)
+struct Pair32 {
+    float a0[6], a1[6], n0[6], n1[6], f0, f1, mu0, mu1;
+};
+
+template <bool HARM>
+__device__ __forceinline__ void pair_load32(const float *u, const float *f, const float *Dh, const float *mu, int p,
+                                            int q, int par, int sy, int sz, Pair32 &P) {
+    using C = VertCoef<float, HARM>;
+    auto ld = [](const float *x) { return __ldg(reinterpret_cast<const float2 *>(x)); };
+    auto lu = [](const float *x) { return *reinterpret_cast<const float2 *>(x); };
+    const float2 d = ld(Dh + p), dq = ld(Dh + q), uq = lu(u + q);
+    // x neighbours: par 0 (i = 2m): other half m-1, m | m, m+1; par 1 (i = 2m+1): m, m+1 | m+1, m+2
+    const int e = par ? q + 2 : q - 1;
+    const float de = __ldg(Dh + e), ue = u[e];
+    const float dxm0 = par ? dq.x : de, dxp0 = par ? dq.y : dq.x, dxm1 = par ? dq.y : dq.x, dxp1 = par ? de : dq.y;
+    P.n0[0] = par ? uq.x : ue;
+    P.n0[1] = par ? uq.y : uq.x;
+    P.n1[0] = par ? uq.y : uq.x;
+    P.n1[1] = par ? ue : uq.y;
+    const float2 dym = ld(Dh + p - sy), dyp = ld(Dh + p + sy), dzm = ld(Dh + p - sz), dzp = ld(Dh + p + sz);
+    const float2 uym = lu(u + p - sy), uyp = lu(u + p + sy), uzm = lu(u + p - sz), uzp = lu(u + p + sz);
+    P.a0[0] = C::face(d.x, dxm0);
+    P.a0[1] = C::face(d.x, dxp0);
+    P.a0[2] = C::face(d.x, dym.x);
+    P.a0[3] = C::face(d.x, dyp.x);
+    P.a0[4] = C::face(d.x, dzm.x);
+    P.a0[5] = C::face(d.x, dzp.x);
+    P.a1[0] = C::face(d.y, dxm1);
+    P.a1[1] = C::face(d.y, dxp1);
+    P.a1[2] = C::face(d.y, dym.y);
+    P.a1[3] = C::face(d.y, dyp.y);
+    P.a1[4] = C::face(d.y, dzm.y);
+    P.a1[5] = C::face(d.y, dzp.y);
+    P.n0[2] = uym.x; P.n0[3] = uyp.x; P.n0[4] = uzm.x; P.n0[5] = uzp.x;
+    P.n1[2] = uym.y; P.n1[3] = uyp.y; P.n1[4] = uzm.y; P.n1[5] = uzp.y;
+    const float2 ff = lu(f + p), mm = ld(mu + p);
+    P.f0 = ff.x; P.f1 = ff.y; P.mu0 = mm.x; P.mu1 = mm.y;
+}
+
+// s + sum_q a_q n_q and the diagonal, in the pairing of coupled_sum32
+__device__ __forceinline__ float pair_sum32(float s, const float *a, const float *n) {
+    float s0 = fmaf(a[0], n[0], s);
+    float s1 = a[2] * n[2];
+    float s2 = a[4] * n[4];
+    s0 = fmaf(a[1], n[1], s0);
+    s1 = fmaf(a[3], n[3], s1);
+    s2 = fmaf(a[5], n[5], s2);
+    return (s0 + s1) + s2;
+}
+
+__device__ __forceinline__ float pair_diag32(const float *a, float mu) {
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + mu);
+}
+
+__device__ __forceinline__ void pair_store32(float *x, int p, bool v0, bool v1, float r0, float r1) {
+    if (v0 && v1) *reinterpret_cast<float2 *>(x + p) = make_float2(r0, r1);
+    else if (v0) x[p] = r0;
+    else x[p + 1] = r1;
+}
+
 template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_smooth_half32(Geom g, float *__restrict__ u, const float *__restrict__ f,
                                                        VertCoef<float, HARM> c, int color, const int *act) {
     long long base;
-    int p, xm;
-    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
+    int p, q, par;
+    bool v0, v1;
+    if (!colour_pair32<BATCH>(g, color, act, base, p, q, par, v0, v1)) return;
     u += base;
     f += base;
-    const float *Dh = c.Dh + base, *mu = c.mu + base;
-    const int sy = g.sy, sz = (int)g.sz;
-    float a[6];
-    couplings32<HARM>(Dh, p, xm, sy, sz, a);
-    const float s = coupled_sum32(f[p], u, p, xm, sy, sz, a);
-    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
-    u[p] = __fdividef(s, dg);
+    Pair32 P;
+    pair_load32<HARM>(u, f, c.Dh + base, c.mu + base, p, q, par, g.sy, (int)g.sz, P);
+    const float r0 = __fdividef(pair_sum32(P.f0, P.a0, P.n0), pair_diag32(P.a0, P.mu0));
+    const float r1 = __fdividef(pair_sum32(P.f1, P.a1, P.n1), pair_diag32(P.a1, P.mu1));
+    pair_store32(u, p, v0, v1, r0, r1);
 }
 
 template <bool HARM, bool BATCH>
@@ -432,17 +536,18 @@ __global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *
                                                            const float *__restrict__ f, VertCoef<float, HARM> c,
                                                            float *__restrict__ r, int color, const int *act) {
     long long base;
-    int p, xm;
-    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
+    int p, q, par;
+    bool v0, v1;
+    if (!colour_pair32<BATCH>(g, color, act, base, p, q, par, v0, v1)) return;
     u += base;
     f += base;
     r += base;
-    const float *Dh = c.Dh + base, *mu = c.mu + base;
-    const int sy = g.sy, sz = (int)g.sz;
-    float a[6];
-    couplings32<HARM>(Dh, p, xm, sy, sz, a);
-    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
-    r[p] = coupled_sum32(fmaf(-dg, u[p], f[p]), u, p, xm, sy, sz, a);
+    Pair32 P;
+    pair_load32<HARM>(u, f, c.Dh + base, c.mu + base, p, q, par, g.sy, (int)g.sz, P);
+    const float2 up = *reinterpret_cast<const float2 *>(u + p);
+    const float r0 = pair_sum32(fmaf(-pair_diag32(P.a0, P.mu0), up.x, P.f0), P.a0, P.n0);
+    const float r1 = pair_sum32(fmaf(-pair_diag32(P.a1, P.mu1), up.y, P.f1), P.a1, P.n1);
+    pair_store32(r, p, v0, v1, r0, r1);
 }
 
 // ---------------------------------------------------------------------------

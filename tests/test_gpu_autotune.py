@@ -38,8 +38,8 @@ def test_autotuned_results_are_bitwise_the_default(dmg, precision, tmp_path, mon
         out[tune] = (u,) + S.vjp(u, T(w["w"]))
         tiles = S.tiles(fp32=bool(precision))
         assert all(t in VALID for t in tiles)
-        if not tune:
-            assert all(t == (32, 8) for t in tiles)
+        if not tune:   # the defaults: 32 x 8 (FP64), 32 x 4 (FP32 pair kernels)
+            assert all(t == ((32, 4) if precision else (32, 8)) for t in tiles)
         S.close()
     for a, b in zip(out[0], out[1]):
         assert torch.equal(a, b)
