@@ -59,10 +59,11 @@ HALF_SWEEP_BYTES_FP32_KERNEL = 12.0
 HALF_SWEEP_FP64_OPS = 3.5
 # DRAM bytes (read + write) of one finest-level half-sweep launch at 257^3,
 # from an ncu capture of the current kernel
-HALF_SWEEP_TRAFFIC = {"fp32": 200145920, "fp64": 664092672}
+HALF_SWEEP_TRAFFIC = {"fp32": 208017152, "fp64": 664092672}
 # DRAM bytes per sample of one batched finest-level FP32 half-sweep at 129^3,
-# from an ncu capture of 8 samples, scaled by the sample count
-VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = 25872500
+# from an ncu capture of 8 samples, scaled by the sample count (None: the
+# kernel changed since the last capture)
+VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = None
 
 
 AUTOTUNE = [1]   # set from --autotune
@@ -309,7 +310,8 @@ def time_autograd_steps(dmg, torch, w, steps, warmup, world, local, inner, profi
     dev = torch.device("cuda", local)
     T = lambda a, g=False: torch.from_numpy(np.ascontiguousarray(a)).to(dev).requires_grad_(g)
     D, mu, q, wv = T(w["D"], True), T(w["mu"], True), T(w["q"], True), T(w["w"])
-    S = dmg.Solver(D.detach(), mu.detach(), w["h"], precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=inner)
+    S = dmg.Solver(D.detach(), mu.detach(), w["h"], precision=dmg.DMG_MIXED, rtol=RTOL, inner_cycles=inner,
+                   autotune=AUTOTUNE[0])
     stream = torch.cuda.current_stream(dev)
     coeffs = None
     if w2 is not None:
@@ -397,7 +399,8 @@ def run_vi(dmg, torch, args, world, local, peaks, peak_src):
         out["roofline"] = dict(kernel="rbgs_half_sweep_fp32_level0 (all samples)", bound="hbm", achieved=ach,
                                peak=pk, unit="GB/s", frac=ach / pk,
                                frac_kernel_bytes=HALF_SWEEP_BYTES_FP32_KERNEL * nint / dur / 1e9 / pk,
-                               traffic=VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 * B if n == 129 else None,
+                               traffic=VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 * B
+                               if n == 129 and VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 else None,
                                peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
                                algorithmic_bytes=byt, bytes_per_vertex=HALF_SWEEP_BYTES_FP32)
     return out

@@ -98,7 +98,8 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *   batch         independent problems in the context (default 1); needs
  *                 batch * nz <= 65535.
  *   autotune      0 (default): colour kernels use 32 x 8 thread blocks (FP64)
- *                 and 32 x 4 (FP32, two vertices per thread); 1: dmg_setup
+ *                 and, FP32 (two vertices per thread), 32 x 4 on wide levels,
+ *                 16 x 8 or 8 x 16 on narrow ones; 1: dmg_setup
  *                 times the candidate block shapes of the half-sweep on every
  *                 grid level (FP64, and FP32 in mixed mode) and keeps the
  *                 fastest (one at least 3% faster than the default). Results are
@@ -485,8 +486,9 @@ int dmg_levels(const dmg_ctx *ctx);
 dmg_status dmg_level_shape(const dmg_ctx *ctx, int level, int *nx, int *ny, int *nz);
 
 /* Thread-block shape (threads along the half-row, rows) of the colour kernels
-   on a level, FP32 (fp32 != 0; threads take two vertices) or FP64: 32 x 4 and
-   32 x 8 unless autotuned (no counterpart
+   on a level, FP32 (fp32 != 0; threads take two vertices) or FP64: by default
+   32 x 8 (FP64) and 32 x 4, 16 x 8 or 8 x 16 by the level's width (FP32), unless
+   autotuned (no counterpart
    in the paper). DMG_EINVAL for NULL or a level out of range. */
 dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 

@@ -117,8 +117,9 @@ struct dmg_ctx {
     int dim = 3;                      // 3, or 2 for an (ny, nx) grid (nz == 1)
     int nb = 1;                       // samples in the batch
     // thread-block shape of the colour kernels (half-sweep, colour defect) per
-    // level: [0] FP64, [1] FP32; 32 x 8 (FP64) and 32 x 4 (FP32, two vertices per
-    // thread) unless the autotuner chose another
+    // level: [0] FP64, [1] FP32; 32 x 8 (FP64) and, FP32 (two vertices per
+    // thread), 32 x 4 / 16 x 8 / 8 x 16 by the level's width, unless the
+    // autotuner chose another
     dim3 tb[2][kMaxLevels];
     int nlev = 0;
     Level L[kMaxLevels];
@@ -242,9 +243,10 @@ inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
 }
 // the FP32 pair kernels (k_smooth_half32, k_residual_colour32): one thread per
-// two elements of a half-row
+// two elements m, m+1 of a half-row; interior vertices i = 2m + parity <= nx - 2
+// have m <= (nx - 2) / 2, so pairs 0 .. (nx - 2) / 4 cover them
 inline dim3 grid_pair(const Geom &g, dim3 b) {
-    const int pairs = (g.nhalf() + 1) / 2;
+    const int pairs = (g.nx - 2) / 4 + 1;
     return dim3((pairs + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
 }
 
@@ -1039,14 +1041,15 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
 // on the level's own arrays during setup. Results are kept for the process
 // (keyed by device, precision, grid, batch and face mean) and, when the
 // environment variable DMG_TUNE_CACHE names a file, read from and appended to
-// it. A candidate replaces the default (32 x 8 for FP64, 32 x 4 for the FP32 pair
-// kernels) only when it is at least 3% faster.
+// it. A candidate replaces the level's default (32 x 8 for FP64; for the FP32
+// pair kernels 32 x 4, 16 x 8 or 8 x 16 by the level's width) only when it is at
+// least 3% faster.
 
-// candidates per precision; the first is the default the others must beat
+// candidates per precision (timed after the level's default shape)
 const dim3 kTiles[2][9] = {{dim3(32, 8), dim3(32, 4), dim3(32, 2), dim3(64, 4), dim3(64, 2), dim3(128, 2),
                             dim3(128, 1), dim3(16, 16), dim3(16, 8)},
-                           {dim3(32, 4), dim3(32, 8), dim3(32, 2), dim3(64, 4), dim3(64, 2), dim3(128, 2),
-                            dim3(128, 1), dim3(16, 16), dim3(16, 8)}};
+                           {dim3(32, 4), dim3(32, 8), dim3(32, 2), dim3(64, 4), dim3(64, 2), dim3(16, 16),
+                            dim3(16, 8), dim3(8, 16), dim3(8, 32)}};
 
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune;
@@ -1125,11 +1128,15 @@ dmg_status tune_level(dmg_ctx *c, int l, int prec, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
-    dim3 best = kTiles[prec][0];
+    // the level's default shape first; a candidate must beat it by 3%
+    const dim3 def = c->tb[prec][l];
+    dim3 best = def;
     float best_ms = 0.f;
     dmg_status st = DMG_OK;
-    for (size_t q = 0; q < sizeof(kTiles[0]) / sizeof(kTiles[0][0]) && st == DMG_OK; q++) {
-        const dim3 b = kTiles[prec][q];
+    const size_t ncand = sizeof(kTiles[0]) / sizeof(kTiles[0][0]);
+    for (size_t q = 0; q <= ncand && st == DMG_OK; q++) {
+        const dim3 b = q == 0 ? def : kTiles[prec][q - 1];
+        if (q > 0 && b.x == def.x && b.y == def.y) continue;
         for (int w = 0; w < 2 && st == DMG_OK; w++) st = tune_launch(c, l, prec, b, w, s);
         if (st != DMG_OK) break;
         cudaEventRecord(e0, s);
@@ -1289,8 +1296,7 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     c->p = *p;
     c->nb = p->batch;
     const int nb = c->nb;
-    for (int t = 0; t < 2; t++)
-        for (dim3 &b : c->tb[t]) b = t ? dim3(32, 4, 1) : dim3(32, 8, 1);   // FP32: the pair kernels' default
+    for (dim3 &b : c->tb[0]) b = dim3(32, 8, 1);
     c->nlev = count_levels(p->nx, p->ny, p->nz);
     c->dim = p->nz == 1 ? 2 : 3;
     c->pyramid = per_level != nullptr;
@@ -1336,6 +1342,14 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
                 CUDA_TRY(c, cudaMemsetAsync(*q, 0, L.n * sizeof(float), s));
             }
         }
+    }
+    // FP32 pair kernels: 128-thread blocks whose x extent covers a row's pairs
+    // ((nx - 2) / 4 + 1 of them) with few idle lanes: 32 x 4 on wide levels,
+    // 16 x 8 and 8 x 16 on narrow ones
+    for (int l = 0; l < c->nlev; l++) {
+        const int pairs = (c->L[l].g.nx - 2) / 4 + 1;
+        const unsigned bx = pairs > 16 ? 32u : (pairs > 8 ? 16u : 8u);
+        c->tb[1][l] = dim3(bx, 128 / bx, 1);
     }
     Level &L0 = c->L[0];
     // contiguous staging: every slot's field at its finest level, back to back

@@ -11,7 +11,7 @@ from paper_2608_00760_b300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-VALID = {(32, 8), (32, 4), (32, 2), (64, 4), (64, 2), (128, 2), (128, 1), (16, 16), (16, 8)}
+VALID = {(32, 8), (32, 4), (32, 2), (64, 4), (64, 2), (128, 2), (128, 1), (16, 16), (16, 8), (8, 16), (8, 32)}
 
 
 @pytest.fixture(scope="module")
@@ -38,8 +38,12 @@ def test_autotuned_results_are_bitwise_the_default(dmg, precision, tmp_path, mon
         out[tune] = (u,) + S.vjp(u, T(w["w"]))
         tiles = S.tiles(fp32=bool(precision))
         assert all(t in VALID for t in tiles)
-        if not tune:   # the defaults: 32 x 8 (FP64), 32 x 4 (FP32 pair kernels)
-            assert all(t == ((32, 4) if precision else (32, 8)) for t in tiles)
+        if not tune:   # the defaults: 32 x 8 (FP64); FP32 pair kernels by the level's width
+            if precision:
+                widths = [(s[2] - 2) // 4 + 1 for s in S.levels()]
+                assert tiles == [(32, 4) if p > 16 else ((16, 8) if p > 8 else (8, 16)) for p in widths]
+            else:
+                assert all(t == (32, 8) for t in tiles)
         S.close()
     for a, b in zip(out[0], out[1]):
         assert torch.equal(a, b)
