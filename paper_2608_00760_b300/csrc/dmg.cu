@@ -229,6 +229,11 @@ inline dim3 blk() { return dim3(32, 8, 1); }
 inline dim3 grid_int(const Geom &g) {
     return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
 }
+// k_update / k_to_f32: elements m, m+1 of one half-row per thread; pairs
+// 0 .. (nx - 2) / 4 cover the interior vertices of either parity
+inline dim3 grid_int_pair(const Geom &g) {
+    return dim3(2 * (((g.nx - 2) / 4 + 1 + 31) / 32), (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
+}
 inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb * g.nz); }
 // half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
 inline dim3 grid_half(const Geom &g) {
@@ -242,7 +247,8 @@ inline dim3 grid_all2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), 
 inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
 }
-// the FP32 pair kernels (k_smooth_half32, k_residual_colour32): one thread per
+// the FP32 pair kernels (k_smooth_half32, k_residual_colour32,
+// k_prolong_smooth32): one thread per
 // two elements m, m+1 of a half-row; interior vertices i = 2m + parity <= nx - 2
 // have m <= (nx - 2) / 2, so pairs 0 .. (nx - 2) / 4 cover them
 inline dim3 grid_pair(const Geom &g, dim3 b) {
@@ -359,8 +365,9 @@ bool is_device_ptr(const void *ptr) {
 }
 
 // gather/scatter grid: x over the vertices of one sample, y over samples
-inline dim3 vertex_grid(const Geom &g) {
-    return dim3((unsigned)(((long long)g.nx * g.ny * g.nz + 255) / 256), g.nb);
+// k_gather / k_scatter: four consecutive vertices of a row per thread, blk() blocks
+inline dim3 quad_grid(const Geom &g) {
+    return dim3(((g.nx + 3) / 4 + 31) / 32, (g.ny + 7) / 8, g.nb * g.nz);
 }
 
 // level-0 geometry of every sample (slot < 0), or the geometry of one slot's
@@ -385,7 +392,7 @@ dmg_status stage_in(dmg_ctx *c, const double *src, double *dst, bool zero_bounda
         CUDA_TRY(c, cudaMemcpyAsync(st, src, bytes, cudaMemcpyHostToDevice, s));
         from = st;
     }
-    dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
+    dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, from, dst, zero_boundary ? 1 : 0);
     return check_launch(c, "gather");
 }
 
@@ -395,11 +402,11 @@ dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s,
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     const size_t bytes = n * g.nb * sizeof(double);
     if (is_device_ptr(dst)) {
-        dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
+        dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, dst);
         return check_launch(c, "scatter");
     }
     double *st = (buf ? buf : c->stage) + (slot < 0 ? 0 : c->stage_off[slot]);
-    dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, st);
+    dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, st);
     TRY(check_launch(c, "scatter"));
     CUDA_TRY(c, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyDeviceToHost, s));
     return DMG_OK;
@@ -552,10 +559,10 @@ dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
         constexpr bool H = decltype(cf)::harmonic;
         const dim3 b = c->tb[1][lev];
         if (c->nb == 1)
-            dmgk::k_prolong_smooth32<H, false><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
+            dmgk::k_prolong_smooth32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
                                                                                 color, nullptr);
         else
-            dmgk::k_prolong_smooth32<H, true><<<grid_half(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
+            dmgk::k_prolong_smooth32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
                                                                                color, c->mask);
         return check_launch(c, "prolong_smooth");
     });
@@ -919,7 +926,7 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
     if (c->dim == 2)
         dmgk::k_to_f32_2<<<grid_int2(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
     else
-        dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
+        dmgk::k_to_f32<<<grid_int_pair(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
     TRY(check_launch(c, "to_f32"));
     TRY(finish_reduce(c, s));
     Progress P;
@@ -934,7 +941,7 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
             if (c->dim == 2)
                 dmgk::k_update2<<<grid_int2(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
             else
-                dmgk::k_update<<<grid_int(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+                dmgk::k_update<<<grid_int_pair(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
             TRY(check_launch(c, "update"));
             TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
             dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);
@@ -1546,10 +1553,10 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     // the host follows on the download stream
     auto put = [&](const double *src, double *dst, double *stage_slot) -> dmg_status {
         if (is_device_ptr(dst)) {
-            dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, dst);
+            dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, dst);
             return check_launch(c, "scatter");
         }
-        dmgk::k_scatter<<<vertex_grid(g), 256, 0, s>>>(g, src, stage_slot);
+        dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, stage_slot);
         return check_launch(c, "scatter");
     };
     auto fetch = [&](const double *stage_slot, double *dst) -> dmg_status {
@@ -1573,9 +1580,9 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
         CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
         const double *qs = is_device_ptr(q[i]) ? q[i] : c->mi_stage[b];
         const double *ws = is_device_ptr(w[i]) ? w[i] : c->mi_stage[b] + n;
-        dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, qs, l.f, 0);
+        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, qs, l.f, 0);
         TRY(check_launch(c, "gather"));
-        dmgk::k_gather<<<vertex_grid(g), 256, 0, s>>>(g, ws, c->T3, 0);
+        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, ws, c->T3, 0);
         TRY(check_launch(c, "gather"));
         CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
         if (i + 1 < npairs) TRY(upload(i + 1));   // overlaps this pair's iterations
@@ -1728,7 +1735,7 @@ dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, con
     if (c->p.precision == DMG_MIXED) {
         dmgk::k_mix_init<<<1, 32, 0, s>>>(c->red + (size_t)kSlots * slot, 0, c->ms + slot, 1);
         TRY(check_launch(c, "mix_init"));
-        dmgk::k_to_f32<<<grid_int(l.g), blk(), 0, s>>>(l.g, l.f, c->ms + slot, l.f32);
+        dmgk::k_to_f32<<<grid_int_pair(l.g), blk(), 0, s>>>(l.g, l.f, c->ms + slot, l.f32);
         TRY(check_launch(c, "to_f32"));
     }
     const bool keep_fwd = sl.have_fwd && phase != DMG_PHASE_FORWARD;
@@ -1785,7 +1792,7 @@ dmg_status capture_step(dmg_ctx *c, int t) {
                 if (c->top_count[lev] == 0) continue;
                 const int first = c->top_first[lev];
                 const Level v = level_range(c, lev, first, c->top_count[lev]);
-                dmgk::k_update<<<grid_int(v.g), blk(), 0, cs>>>(v.g, v.u, v.u32, c->ms + first,
+                dmgk::k_update<<<grid_int_pair(v.g), blk(), 0, cs>>>(v.g, v.u, v.u32, c->ms + first,
                                                                 c->mask ? c->mask + first : nullptr);
                 TRY(check_launch(c, "update"));
                 TRY(top_resid_norm(c, lev, true, cs));

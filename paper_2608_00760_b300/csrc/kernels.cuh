@@ -360,56 +360,6 @@ __global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__rest
 // sample decoding. These are the bandwidth-bound kernels of the mixed-precision
 // cycle, where the instruction issue rate is the co-limit.
 
-// vertex of colour `color` handled by this thread: its in-sample position p and
-// the offset of its -x neighbour (the +x neighbour is at p + xm + 1)
-template <bool BATCH>
-__device__ __forceinline__ bool colour_vertex32(const Geom &g, int color, const int *act, long long &base, int &p,
-                                                int &xm) {
-    int k, smp = 0;
-    if (BATCH) {
-        smp = zsplit(g, kInterior, k);
-        if (inactive(act, smp)) return false;
-    } else {
-        k = blockIdx.z;
-    }
-    k += 1;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int par = (color + j + k) & 1;            // parity of i for this colour in row (j, k)
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > g.ny - 2 || 2 * t + 2 - par > g.nx - 2) return false;
-    base = BATCH ? (long long)smp * g.sb : 0;
-    p = k * (int)g.sz + j * g.sy + par * g.hx + (t + 1 - par);   // i = 2t + 2 - par
-    xm = par ? -g.hx : g.hx - 1;
-    g.check(p - g.sz);
-    g.check(p + g.sz);
-    g.check(p + xm);
-    g.check(p + xm + 1);
-    return true;
-}
-
-template <bool HARM>
-__device__ __forceinline__ void couplings32(const float *Dh, int p, int xm, int sy, int sz, float a[6]) {
-    using C = VertCoef<float, HARM>;
-    const float d = __ldg(Dh + p);
-    a[0] = C::face(d, __ldg(Dh + p + xm));
-    a[1] = C::face(d, __ldg(Dh + p + xm + 1));
-    a[2] = C::face(d, __ldg(Dh + p - sy));
-    a[3] = C::face(d, __ldg(Dh + p + sy));
-    a[4] = C::face(d, __ldg(Dh + p - sz));
-    a[5] = C::face(d, __ldg(Dh + p + sz));
-}
-
-// s + sum_q a_q u_q in the pairing of coupled_sum<float>
-__device__ __forceinline__ float coupled_sum32(float s, const float *u, int p, int xm, int sy, int sz, const float *a) {
-    float s0 = fmaf(a[0], u[p + xm], s);
-    float s1 = a[2] * u[p - sy];
-    float s2 = a[4] * u[p - sz];
-    s0 = fmaf(a[1], u[p + xm + 1], s0);
-    s1 = fmaf(a[3], u[p + sy], s1);
-    s2 = fmaf(a[5], u[p + sz], s2);
-    return (s0 + s1) + s2;
-}
-
 // The two FP32 colour kernels below update (or take the defect of) two
 // vertices per thread: elements m and m+1 (m even) of the colour's half-row in
 // row (j, k), i.e. vertices i = 2m + par and 2m + 2 + par. Every operand then
@@ -423,9 +373,17 @@ __device__ __forceinline__ float coupled_sum32(float s, const float *u, int p, i
 // the pair of colour `color` handled by this thread: in-sample positions of
 // element m of its own half (p) and of the other half (q), the parity of i, and
 // which of the two vertices are interior
+struct PairAt {
+    long long base;    // offset of the sample
+    int smp;           // sample index (0 for single problems)
+    int p, q;          // in-sample positions of element m in the own and in the other half
+    int par;           // parity of i
+    int m, j, k;       // element of the half-row, row and plane
+    bool v0, v1;       // interior flags of vertices 2m + par and 2m + 2 + par
+};
+
 template <bool BATCH>
-__device__ __forceinline__ bool colour_pair32(const Geom &g, int color, const int *act, long long &base, int &p,
-                                              int &q, int &par, bool &v0, bool &v1) {
+__device__ __forceinline__ bool colour_pair32(const Geom &g, int color, const int *act, PairAt &P) {
     int k, smp = 0;
     if (BATCH) {
         smp = zsplit(g, kInterior, k);
@@ -436,20 +394,25 @@ __device__ __forceinline__ bool colour_pair32(const Geom &g, int color, const in
     k += 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     if (j > g.ny - 2) return false;
-    par = (color + j + k) & 1;                      // parity of i for this colour in row (j, k)
+    const int par = (color + j + k) & 1;            // parity of i for this colour in row (j, k)
     const int m = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int i0 = 2 * m + par;
-    v0 = i0 >= 1 && i0 <= g.nx - 2;
-    v1 = i0 + 2 <= g.nx - 2;
-    if (!v0 && !v1) return false;
-    base = BATCH ? (long long)smp * g.sb : 0;
+    P.v0 = i0 >= 1 && i0 <= g.nx - 2;
+    P.v1 = i0 + 2 <= g.nx - 2;
+    if (!P.v0 && !P.v1) return false;
+    P.smp = smp;
+    P.base = BATCH ? (long long)smp * g.sb : 0;
+    P.par = par;
+    P.m = m;
+    P.j = j;
+    P.k = k;
     const int row = k * (int)g.sz + j * g.sy;
-    p = row + par * g.hx + m;
-    q = row + (1 - par) * g.hx + m;
-    g.check(p - g.sz);
-    g.check(p + g.sz + 1);
-    g.check(q - 1 + 2 * par);   // the third x neighbour: q - 1 (par 0) or q + 2 (par 1)
-    g.check(q + 1);
+    P.p = row + par * g.hx + m;
+    P.q = row + (1 - par) * g.hx + m;
+    g.check(P.p - g.sz);
+    g.check(P.p + g.sz + 1);
+    g.check(P.q - 1 + 2 * par);   // the third x neighbour: q - 1 (par 0) or q + 2 (par 1)
+    g.check(P.q + 1);
     return true;
 }
 
@@ -518,36 +481,32 @@ __device__ __forceinline__ void pair_store32(float *x, int p, bool v0, bool v1, 
 template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_smooth_half32(Geom g, float *__restrict__ u, const float *__restrict__ f,
                                                        VertCoef<float, HARM> c, int color, const int *act) {
-    long long base;
-    int p, q, par;
-    bool v0, v1;
-    if (!colour_pair32<BATCH>(g, color, act, base, p, q, par, v0, v1)) return;
-    u += base;
-    f += base;
+    PairAt A;
+    if (!colour_pair32<BATCH>(g, color, act, A)) return;
+    u += A.base;
+    f += A.base;
     Pair32 P;
-    pair_load32<HARM>(u, f, c.Dh + base, c.mu + base, p, q, par, g.sy, (int)g.sz, P);
+    pair_load32<HARM>(u, f, c.Dh + A.base, c.mu + A.base, A.p, A.q, A.par, g.sy, (int)g.sz, P);
     const float r0 = __fdividef(pair_sum32(P.f0, P.a0, P.n0), pair_diag32(P.a0, P.mu0));
     const float r1 = __fdividef(pair_sum32(P.f1, P.a1, P.n1), pair_diag32(P.a1, P.mu1));
-    pair_store32(u, p, v0, v1, r0, r1);
+    pair_store32(u, A.p, A.v0, A.v1, r0, r1);
 }
 
 template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *__restrict__ u,
                                                            const float *__restrict__ f, VertCoef<float, HARM> c,
                                                            float *__restrict__ r, int color, const int *act) {
-    long long base;
-    int p, q, par;
-    bool v0, v1;
-    if (!colour_pair32<BATCH>(g, color, act, base, p, q, par, v0, v1)) return;
-    u += base;
-    f += base;
-    r += base;
+    PairAt A;
+    if (!colour_pair32<BATCH>(g, color, act, A)) return;
+    u += A.base;
+    f += A.base;
+    r += A.base;
     Pair32 P;
-    pair_load32<HARM>(u, f, c.Dh + base, c.mu + base, p, q, par, g.sy, (int)g.sz, P);
-    const float2 up = *reinterpret_cast<const float2 *>(u + p);
+    pair_load32<HARM>(u, f, c.Dh + A.base, c.mu + A.base, A.p, A.q, A.par, g.sy, (int)g.sz, P);
+    const float2 up = *reinterpret_cast<const float2 *>(u + A.p);
     const float r0 = pair_sum32(fmaf(-pair_diag32(P.a0, P.mu0), up.x, P.f0), P.a0, P.n0);
     const float r1 = pair_sum32(fmaf(-pair_diag32(P.a1, P.mu1), up.y, P.f1), P.a1, P.n1);
-    pair_store32(r, p, v0, v1, r0, r1);
+    pair_store32(r, A.p, A.v0, A.v1, r0, r1);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,19 +524,24 @@ __global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *
 // the separate correction costs.
 //
 // (P e) at a fine vertex repeats prolong_cell's operations in its order: along
-// y, then z, then x. In one row (j, k) of one colour every thread has the same
-// parities of i, j and k, so a warp runs one specialisation, PX/PY/PZ the
-// parities of the vertex it updates. The coarse values its six neighbours
-// interpolate from lie in a 3x3x3 box around (i>>1, j>>1, k>>1); box entry
-// (x, y, z) is loaded only when one of the six needs it (7 to 12 values).
+// y, then z, then x. k_prolong_smooth32 runs on the pairs of the colour
+// kernels above (vertices i0 = 2m + par and i0 + 2 of one row), so that its
+// fine operands come in as the same 8-byte loads. In one row (j, k) of one
+// colour every thread has the same parities of i, j and k, so a warp runs one
+// specialisation, PX/PY/PZ the parities of the vertices it updates. The coarse
+// values that the twelve neighbours of the pair interpolate from lie in a
+// 4x3x3 box whose x entries are X = m - 1 .. m + 2 (the first vertex uses
+// entries 0..2, the second 1..3); an entry is loaded only when a neighbour
+// needs it, and the entries of one vertex alone only when that vertex is
+// interior.
 
 // coarse offset (relative to fine index >> 1) and oddness of the fine index
 // whose parity is par, displaced by d in {-1, 0, 1}
 __host__ __device__ constexpr int fuse_lo(int par, int d) { return (par + d + 2) / 2 - 1; }
 __host__ __device__ constexpr int fuse_odd(int par, int d) { return (par + d + 2) & 1; }
 
-// does the neighbour at fine displacement (dx, dy, dz) interpolate from box
-// entry (x, y, z) (entries -1..1 per axis)?
+// does the neighbour at fine displacement (dx, dy, dz) of a vertex interpolate
+// from its box entry (x, y, z) (entries -1..1 per axis)?
 __host__ __device__ constexpr bool fuse_uses(int px, int py, int pz, int dx, int dy, int dz, int x, int y, int z) {
     return (x == fuse_lo(px, dx) || (fuse_odd(px, dx) && x == fuse_lo(px, dx) + 1)) &&
            (y == fuse_lo(py, dy) || (fuse_odd(py, dy) && y == fuse_lo(py, dy) + 1)) &&
@@ -590,10 +554,20 @@ __host__ __device__ constexpr bool fuse_needed(int px, int py, int pz, int x, in
            fuse_uses(px, py, pz, 0, 0, -1, x, y, z) || fuse_uses(px, py, pz, 0, 0, 1, x, y, z);
 }
 
-// (P e) at the fine neighbour (dx, dy, dz) from the box B[z + 1][y + 1][x + 1]
-template <int PX, int PY, int PZ, int DX, int DY, int DZ>
-__device__ __forceinline__ float fuse_interp(const float (&B)[3][3][3]) {
-    constexpr int lx = fuse_lo(PX, DX) + 1, ly = fuse_lo(PY, DY) + 1, lz = fuse_lo(PZ, DZ) + 1;
+// entry (x, y, z) of the pair's box (x 0..3, y and z 0..2): needed by the
+// first vertex (x 0..2), by the second (x 1..3)
+__host__ __device__ constexpr bool fuse_needed_first(int px, int py, int pz, int x, int y, int z) {
+    return x <= 2 && fuse_needed(px, py, pz, x - 1, y - 1, z - 1);
+}
+__host__ __device__ constexpr bool fuse_needed_second(int px, int py, int pz, int x, int y, int z) {
+    return x >= 1 && fuse_needed(px, py, pz, x - 2, y - 1, z - 1);
+}
+
+// (P e) at the fine neighbour (dx, dy, dz) of the pair's vertex V (0 or 1)
+// from the box B[z][y][x]
+template <int PX, int PY, int PZ, int DX, int DY, int DZ, int V>
+__device__ __forceinline__ float fuse_interp(const float (&B)[3][3][4]) {
+    constexpr int lx = fuse_lo(PX, DX) + 1 + V, ly = fuse_lo(PY, DY) + 1, lz = fuse_lo(PZ, DZ) + 1;
     constexpr bool ox = fuse_odd(PX, DX), oy = fuse_odd(PY, DY), oz = fuse_odd(PZ, DZ);
     float row[2];
 #pragma unroll
@@ -608,44 +582,52 @@ __device__ __forceinline__ float fuse_interp(const float (&B)[3][3][3]) {
     return ox ? 0.5f * (row[0] + row[1]) : row[0];
 }
 
+// the six corrected neighbour values of vertex V: n_q + (P e)_q
+template <int PX, int PY, int PZ, int V>
+__device__ __forceinline__ void fuse_correct(float *n, const float (&B)[3][3][4]) {
+    n[0] += fuse_interp<PX, PY, PZ, -1, 0, 0, V>(B);
+    n[1] += fuse_interp<PX, PY, PZ, 1, 0, 0, V>(B);
+    n[2] += fuse_interp<PX, PY, PZ, 0, -1, 0, V>(B);
+    n[3] += fuse_interp<PX, PY, PZ, 0, 1, 0, V>(B);
+    n[4] += fuse_interp<PX, PY, PZ, 0, 0, -1, V>(B);
+    n[5] += fuse_interp<PX, PY, PZ, 0, 0, 1, V>(B);
+}
+
 template <int PX, int PY, int PZ, bool HARM>
-__device__ __forceinline__ void prolong_smooth_point32(const Geom &g, float *u, const float *f, const float *Dh,
-                                                       const float *mu, const Geom &gc, const float *e, int p, int xm,
-                                                       int i, int j, int k) {
-    const int sy = g.sy, sz = (int)g.sz;
-    const int I = (i >> 1) - 1, J = (j >> 1) - 1, K = (k >> 1) - 1;
+__device__ __forceinline__ void prolong_smooth_pair32(const Geom &g, float *u, const float *f, const float *Dh,
+                                                      const float *mu, const Geom &gc, const float *e,
+                                                      const PairAt &A) {
+    const int I = A.m - 1, J = (A.j >> 1) - 1, K = (A.k >> 1) - 1;
     const int csy = gc.sy, csz = (int)gc.sz;
-    float B[3][3][3];
+    float B[3][3][4];
 #pragma unroll
     for (int z = 0; z < 3; z++)
 #pragma unroll
         for (int y = 0; y < 3; y++)
 #pragma unroll
-            for (int x = 0; x < 3; x++) {
-                if (!fuse_needed(PX, PY, PZ, x - 1, y - 1, z - 1)) continue;
+            for (int x = 0; x < 4; x++) {
+                const bool first = fuse_needed_first(PX, PY, PZ, x, y, z);
+                const bool second = fuse_needed_second(PX, PY, PZ, x, y, z);
+                if (!first && !second) continue;
+                // an entry that only a boundary (not updated) vertex needs may
+                // lie outside the coarse row: it is not loaded
+                const bool load = (first && A.v0) || (second && A.v1);
                 const int X = I + x;
                 const int q = (K + z) * csz + (J + y) * csy + (X & 1) * gc.hx + (X >> 1);
-                gc.check(q);
-                B[z][y][x] = __ldg(e + q);
+                float b = 0.f;
+                if (load) {
+                    gc.check(q);
+                    b = __ldg(e + q);
+                }
+                B[z][y][x] = b;
             }
-    float a[6];
-    couplings32<HARM>(Dh, p, xm, sy, sz, a);
-    const float v0 = u[p + xm] + fuse_interp<PX, PY, PZ, -1, 0, 0>(B);
-    const float v1 = u[p + xm + 1] + fuse_interp<PX, PY, PZ, 1, 0, 0>(B);
-    const float v2 = u[p - sy] + fuse_interp<PX, PY, PZ, 0, -1, 0>(B);
-    const float v3 = u[p + sy] + fuse_interp<PX, PY, PZ, 0, 1, 0>(B);
-    const float v4 = u[p - sz] + fuse_interp<PX, PY, PZ, 0, 0, -1>(B);
-    const float v5 = u[p + sz] + fuse_interp<PX, PY, PZ, 0, 0, 1>(B);
-    // the pairing of coupled_sum32
-    float s0 = fmaf(a[0], v0, f[p]);
-    float s1 = a[2] * v2;
-    float s2 = a[4] * v4;
-    s0 = fmaf(a[1], v1, s0);
-    s1 = fmaf(a[3], v3, s1);
-    s2 = fmaf(a[5], v5, s2);
-    const float s = (s0 + s1) + s2;
-    const float dg = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + __ldg(mu + p));
-    u[p] = __fdividef(s, dg);
+    Pair32 P;
+    pair_load32<HARM>(u, f, Dh, mu, A.p, A.q, PX, g.sy, (int)g.sz, P);
+    fuse_correct<PX, PY, PZ, 0>(P.n0, B);
+    fuse_correct<PX, PY, PZ, 1>(P.n1, B);
+    const float r0 = __fdividef(pair_sum32(P.f0, P.a0, P.n0), pair_diag32(P.a0, P.mu0));
+    const float r1 = __fdividef(pair_sum32(P.f1, P.a1, P.n1), pair_diag32(P.a1, P.mu1));
+    pair_store32(u, A.p, A.v0, A.v1, r0, r1);
 }
 
 // u: fine level (its colour-`color` vertices updated, the other colour left
@@ -655,28 +637,21 @@ template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_prolong_smooth32(Geom g, float *__restrict__ u, const float *__restrict__ f,
                                                           VertCoef<float, HARM> c, Geom gc,
                                                           const float *__restrict__ e, int color, const int *act) {
-    long long base;
-    int p, xm;
-    if (!colour_vertex32<BATCH>(g, color, act, base, p, xm)) return;
-    int k, smp = 0;
-    if (BATCH) smp = zsplit(g, kInterior, k);
-    else k = blockIdx.z;
-    k += 1;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - ((color + j + k) & 1);
-    u += base;
-    f += base;
-    e += BATCH ? (long long)smp * gc.sb : 0;
-    const float *Dh = c.Dh + base, *mu = c.mu + base;
-    switch ((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) {
-    case 0: prolong_smooth_point32<0, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 1: prolong_smooth_point32<1, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 2: prolong_smooth_point32<0, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 3: prolong_smooth_point32<1, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 4: prolong_smooth_point32<0, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 5: prolong_smooth_point32<1, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    case 6: prolong_smooth_point32<0, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
-    default: prolong_smooth_point32<1, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, p, xm, i, j, k); break;
+    PairAt A;
+    if (!colour_pair32<BATCH>(g, color, act, A)) return;
+    u += A.base;
+    f += A.base;
+    e += BATCH ? (long long)A.smp * gc.sb : 0;
+    const float *Dh = c.Dh + A.base, *mu = c.mu + A.base;
+    switch (A.par | ((A.j & 1) << 1) | ((A.k & 1) << 2)) {
+    case 0: prolong_smooth_pair32<0, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 1: prolong_smooth_pair32<1, 0, 0, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 2: prolong_smooth_pair32<0, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 3: prolong_smooth_pair32<1, 1, 0, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 4: prolong_smooth_pair32<0, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 5: prolong_smooth_pair32<1, 0, 1, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    case 6: prolong_smooth_pair32<0, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, A); break;
+    default: prolong_smooth_pair32<1, 1, 1, HARM>(g, u, f, Dh, mu, gc, e, A); break;
     }
 }
 
@@ -959,41 +934,78 @@ inline size_t tail_smem_elems(const Geom &gs, int ncoef) {
 
 // ---------------------------------------------------------------------------
 // layout conversion between the caller's contiguous [nz][ny][nx] arrays and the
-// split level-0 layout (one thread per vertex, coalesced on the contiguous side;
-// blockIdx.y = sample)
+// split level-0 layout. One thread takes four consecutive vertices i0 .. i0+3
+// (i0 = 4t) of one row: elements m, m+1 (m = i0 / 2) of the even and of the odd
+// half, each pair one 16-byte access on the split side, and four consecutive
+// elements on the contiguous side (blockIdx.z = sample * nz + plane). Four
+// independent loads per thread keep enough bytes in flight for the copy to
+// run near the memory rate.
+
+__device__ __forceinline__ bool row_quad(const Geom &g, int &i0, int &j, int &k, int &smp) {
+    i0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    smp = zsplit(g, kAll, k);
+    return i0 < g.nx && j < g.ny;
+}
 
 // dst = src on every vertex, or on interior vertices only with zeros on the
 // boundary (zero_boundary != 0)
 __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict__ src,
                                                 double *__restrict__ dst, int zero_boundary) {
-    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned n = (unsigned)g.nx * g.ny * g.nz;
-    if (t >= n) return;
-    src += (long long)blockIdx.y * n;
-    dst += blockIdx.y * g.sb;
-    const unsigned r = t / g.nx;
-    const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
-    g.check(g.pos(i, j, k));
-    DMG_CHECK(blockIdx.y < (unsigned)g.nb);
-    double v = src[t];
-    if (zero_boundary &&
-        (i == 0 || j == 0 || i == g.nx - 1 || j == g.ny - 1 || (g.nz > 1 && (k == 0 || k == g.nz - 1))))
-        v = 0.0;   // (a 2D grid, nz == 1, has no z boundary)
-    dst[g.pos(i, j, k)] = v;
+    int i0, j, k, smp;
+    if (!row_quad(g, i0, j, k, smp)) return;
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long ps = k * g.sz + (long long)j * g.sy + (i0 >> 1);   // in-sample position of vertex i0
+    src += smp * n + ((long long)k * g.ny + j) * g.nx + i0;
+    dst += smp * g.sb + ps;
+    const int nv = min(4, g.nx - i0);
+    g.check(ps);
+    g.check(ps + g.hx + (nv > 3 ? 1 : 0));
+    DMG_CHECK(smp < g.nb);
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = q < nv ? src[q] : 0.0;
+    if (zero_boundary) {
+        // (a 2D grid, nz == 1, has no z boundary)
+        const bool edge = j == 0 || j == g.ny - 1 || (g.nz > 1 && (k == 0 || k == g.nz - 1));
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (edge || i0 + q == 0 || i0 + q == g.nx - 1) v[q] = 0.0;
+    }
+    if (nv == 4) {
+        *reinterpret_cast<double2 *>(dst) = make_double2(v[0], v[2]);
+        *reinterpret_cast<double2 *>(dst + g.hx) = make_double2(v[1], v[3]);
+    } else {
+        dst[0] = v[0];
+        if (nv > 1) dst[g.hx] = v[1];
+        if (nv > 2) dst[1] = v[2];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_scatter(Geom g, const double *__restrict__ src,
                                                  double *__restrict__ dst) {
-    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned n = (unsigned)g.nx * g.ny * g.nz;
-    if (t >= n) return;
-    src += blockIdx.y * g.sb;
-    dst += (long long)blockIdx.y * n;
-    const unsigned r = t / g.nx;
-    const int i = (int)(t - r * g.nx), k = (int)(r / g.ny), j = (int)(r - (unsigned)k * g.ny);
-    g.check(g.pos(i, j, k));
-    DMG_CHECK(blockIdx.y < (unsigned)g.nb);
-    dst[t] = src[g.pos(i, j, k)];
+    int i0, j, k, smp;
+    if (!row_quad(g, i0, j, k, smp)) return;
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long ps = k * g.sz + (long long)j * g.sy + (i0 >> 1);   // in-sample position of vertex i0
+    src += smp * g.sb + ps;
+    dst += smp * n + ((long long)k * g.ny + j) * g.nx + i0;
+    const int nv = min(4, g.nx - i0);
+    g.check(ps);
+    g.check(ps + g.hx + (nv > 3 ? 1 : 0));
+    DMG_CHECK(smp < g.nb);
+    if (nv == 4) {
+        const double2 e = *reinterpret_cast<const double2 *>(src);
+        const double2 o = *reinterpret_cast<const double2 *>(src + g.hx);
+        dst[0] = e.x;
+        dst[1] = o.x;
+        dst[2] = e.y;
+        dst[3] = o.y;
+    } else {
+        dst[0] = src[0];
+        if (nv > 1) dst[1] = src[g.hx];
+        if (nv > 2) dst[2] = src[1];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1403,30 +1415,63 @@ __global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u
     f[p] -= v;
 }
 
+// Elementwise kernels on the interior of level 0: one thread takes elements m,
+// m+1 (m even) of one half-row, vertices i = 2m + par and 2m + 2 + par, as one
+// 16-byte (FP64) and one 8-byte (FP32) access; blockIdx.x = 2 * chunk + par.
+__device__ __forceinline__ bool interior_pair(const Geom &g, const int *act, long long &p, int &smp, bool &v0,
+                                              bool &v1) {
+    const int par = blockIdx.x & 1;
+    const int m = 2 * (int)((blockIdx.x >> 1) * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k;
+    smp = zsplit(g, kInterior, k);
+    k += 1;
+    const int i0 = 2 * m + par;
+    v0 = i0 >= 1 && i0 <= g.nx - 2;
+    v1 = i0 + 2 <= g.nx - 2;
+    if (j > g.ny - 2 || (!v0 && !v1) || inactive(act, smp)) return false;
+    p = smp * g.sb + k * g.sz + (long long)j * g.sy + par * g.hx + m;
+    g.check(p - smp * g.sb + 1);
+    return true;
+}
+
 // mixed precision: u64 += e32 * 2^ms->e_cur on interior vertices (1 FP64 add)
 __global__ void __launch_bounds__(256) k_update(Geom g, double *__restrict__ u, const float *__restrict__ e,
                                                 const MixScalars *ms, const int *act) {
-    int i = vertex_i();
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k;
-    const int smp = zsplit(g, kInterior, k);
-    k += 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2 || inactive(act, smp)) return;
-    long long p = g.pos(i, j, k) + smp * g.sb;
-    u[p] += f32_to_f64_shift(e[p], ms[smp].e_cur);
+    long long p;
+    int smp;
+    bool v0, v1;
+    if (!interior_pair(g, act, p, smp, v0, v1)) return;
+    const int sh = ms[smp].e_cur;
+    if (v0 && v1) {
+        double2 x = *reinterpret_cast<const double2 *>(u + p);
+        const float2 d = *reinterpret_cast<const float2 *>(e + p);
+        x.x += f32_to_f64_shift(d.x, sh);
+        x.y += f32_to_f64_shift(d.y, sh);
+        *reinterpret_cast<double2 *>(u + p) = x;
+    } else if (v0) {
+        u[p] += f32_to_f64_shift(e[p], sh);
+    } else {
+        u[p + 1] += f32_to_f64_shift(e[p + 1], sh);
+    }
 }
 
 // y = x * 2^-ms->e_cur in FP32 on interior vertices
 __global__ void __launch_bounds__(256) k_to_f32(Geom g, const double *__restrict__ x, const MixScalars *ms,
                                                 float *__restrict__ y) {
-    int i = vertex_i();
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k;
-    const int smp = zsplit(g, kInterior, k);
-    k += 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
-    long long p = g.pos(i, j, k) + smp * g.sb;
-    y[p] = f64_to_f32_shift(x[p], -ms[smp].e_cur);
+    long long p;
+    int smp;
+    bool v0, v1;
+    if (!interior_pair(g, nullptr, p, smp, v0, v1)) return;
+    const int sh = -ms[smp].e_cur;
+    if (v0 && v1) {
+        const double2 a = *reinterpret_cast<const double2 *>(x + p);
+        *reinterpret_cast<float2 *>(y + p) = make_float2(f64_to_f32_shift(a.x, sh), f64_to_f32_shift(a.y, sh));
+    } else if (v0) {
+        y[p] = f64_to_f32_shift(x[p], sh);
+    } else {
+        y[p + 1] = f64_to_f32_shift(x[p + 1], sh);
+    }
 }
 
 // ---------------------------------------------------------------------------
