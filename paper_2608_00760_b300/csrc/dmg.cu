@@ -548,12 +548,33 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
     return DMG_OK;
 }
 
-// u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev, in one
-// FP32 launch that stores only the colour's new values (k_prolong_smooth32);
-// the half-sweep of the other colour must follow.
+// levels of at least this many vertices (all samples) take the correction on
+// one colour and a plain half-sweep instead of the fused launch
+constexpr long long kSplitProlongVertices = 1LL << 22;
+
+// u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev. Only the
+// other colour's corrected values are ever read (by this half-sweep), so only
+// they are formed: on the fly in one FP32 launch that stores the colour's new
+// values (k_prolong_smooth32), or on the large levels stored by
+// k_prolong_colour32 ahead of a plain half-sweep. The half-sweep of the other
+// colour must follow.
 dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
     Level &l = c->L[lev];
     Level cl = coarse_of(c, lev);
+    if ((long long)l.g.sb * l.g.nb >= kSplitProlongVertices) {
+        {
+            ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
+            const dim3 b = c->tb[1][lev];
+            if (c->nb == 1)
+                dmgk::k_prolong_colour32<false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, 1 - color,
+                                                                                 nullptr);
+            else
+                dmgk::k_prolong_colour32<true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, 1 - color,
+                                                                                c->mask);
+            TRY(check_launch(c, "prolong_colour"));
+        }
+        return half_sweep<float>(c, lev, color, s);
+    }
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
     return with_coef32(c, l, [&](auto cf) {
         constexpr bool H = decltype(cf)::harmonic;

@@ -655,6 +655,69 @@ __global__ void __launch_bounds__(256) k_prolong_smooth32(Geom g, float *__restr
     }
 }
 
+// The correction alone on the vertices of one colour, u_n += (P e)_n: the
+// values the next half-sweep (of the other colour) reads. On the large levels
+// this and a plain half-sweep take less time than k_prolong_smooth32, whose
+// coarse-box loads for twelve neighbours per pair leave it latency-bound; the
+// stored values are the ones k_prolong_smooth32 forms on the fly, so the two
+// orders end bitwise alike.
+template <int PX, int PY, int PZ>
+__device__ __forceinline__ void prolong_colour_pair32(float *u, const Geom &gc, const float *e, const PairAt &A) {
+    const int I = A.m - 1, J = (A.j >> 1) - 1, K = (A.k >> 1) - 1;
+    const int csy = gc.sy, csz = (int)gc.sz;
+    float B[3][3][4];
+#pragma unroll
+    for (int z = 0; z < 3; z++)
+#pragma unroll
+        for (int y = 0; y < 3; y++)
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+                const bool first = x <= 2 && fuse_uses(PX, PY, PZ, 0, 0, 0, x - 1, y - 1, z - 1);
+                const bool second = x >= 1 && fuse_uses(PX, PY, PZ, 0, 0, 0, x - 2, y - 1, z - 1);
+                if (!first && !second) continue;
+                const bool load = (first && A.v0) || (second && A.v1);
+                const int X = I + x;
+                const int q = (K + z) * csz + (J + y) * csy + (X & 1) * gc.hx + (X >> 1);
+                float b = 0.f;
+                if (load) {
+                    gc.check(q);
+                    b = __ldg(e + q);
+                }
+                B[z][y][x] = b;
+            }
+    const float r0 = fuse_interp<PX, PY, PZ, 0, 0, 0, 0>(B);
+    const float r1 = fuse_interp<PX, PY, PZ, 0, 0, 0, 1>(B);
+    if (A.v0 && A.v1) {
+        float2 x = *reinterpret_cast<const float2 *>(u + A.p);
+        x.x += r0;
+        x.y += r1;
+        *reinterpret_cast<float2 *>(u + A.p) = x;
+    } else if (A.v0) {
+        u[A.p] += r0;
+    } else {
+        u[A.p + 1] += r1;
+    }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_prolong_colour32(Geom g, float *__restrict__ u, Geom gc,
+                                                          const float *__restrict__ e, int color, const int *act) {
+    PairAt A;
+    if (!colour_pair32<BATCH>(g, color, act, A)) return;
+    u += A.base;
+    e += BATCH ? (long long)A.smp * gc.sb : 0;
+    switch (A.par | ((A.j & 1) << 1) | ((A.k & 1) << 2)) {
+    case 0: prolong_colour_pair32<0, 0, 0>(u, gc, e, A); break;
+    case 1: prolong_colour_pair32<1, 0, 0>(u, gc, e, A); break;
+    case 2: prolong_colour_pair32<0, 1, 0>(u, gc, e, A); break;
+    case 3: prolong_colour_pair32<1, 1, 0>(u, gc, e, A); break;
+    case 4: prolong_colour_pair32<0, 0, 1>(u, gc, e, A); break;
+    case 5: prolong_colour_pair32<1, 0, 1>(u, gc, e, A); break;
+    case 6: prolong_colour_pair32<0, 1, 1>(u, gc, e, A); break;
+    default: prolong_colour_pair32<1, 1, 1>(u, gc, e, A); break;
+    }
+}
+
 // Full weighting of a defect that vanishes on one colour: fine vertex
 // (2I+a, 2J+b, 2K+c) has colour (a+b+c) mod 2, so only the 13 (PAR = 0: centre
 // and edges) or 14 (PAR = 1: faces and corners) offsets of that parity carry a
@@ -982,29 +1045,52 @@ __global__ void __launch_bounds__(256) k_gather(Geom g, const double *__restrict
     }
 }
 
+// The contiguous side of k_scatter is written in warp order: lane l of a warp
+// (which holds vertices 4l .. 4l+3 of a 128-vertex run) stores vertices l,
+// l + 32, l + 64, l + 96 of the run, fetched from their holders by shuffles, so
+// each store instruction covers 256 consecutive bytes. blockDim.x = 32.
 __global__ void __launch_bounds__(256) k_scatter(Geom g, const double *__restrict__ src,
                                                  double *__restrict__ dst) {
-    int i0, j, k, smp;
-    if (!row_quad(g, i0, j, k, smp)) return;
-    const long long n = (long long)g.nx * g.ny * g.nz;
-    const long long ps = k * g.sz + (long long)j * g.sy + (i0 >> 1);   // in-sample position of vertex i0
-    src += smp * g.sb + ps;
-    dst += smp * n + ((long long)k * g.ny + j) * g.nx + i0;
-    const int nv = min(4, g.nx - i0);
-    g.check(ps);
-    g.check(ps + g.hx + (nv > 3 ? 1 : 0));
-    DMG_CHECK(smp < g.nb);
-    if (nv == 4) {
-        const double2 e = *reinterpret_cast<const double2 *>(src);
-        const double2 o = *reinterpret_cast<const double2 *>(src + g.hx);
-        dst[0] = e.x;
-        dst[1] = o.x;
-        dst[2] = e.y;
-        dst[3] = o.y;
-    } else {
-        dst[0] = src[0];
-        if (nv > 1) dst[1] = src[g.hx];
-        if (nv > 2) dst[2] = src[1];
+    const int lane = threadIdx.x;
+    const int i0 = 4 * (int)(blockIdx.x * 32 + lane);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k;
+    const int smp = zsplit(g, kAll, k);
+    if (j >= g.ny) return;   // whole warps
+    const int nv = max(0, min(4, g.nx - i0));
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // vertices i0 .. i0+3
+    if (nv > 0) {
+        const long long ps = k * g.sz + (long long)j * g.sy + (i0 >> 1);   // in-sample position of vertex i0
+        g.check(ps);
+        g.check(ps + g.hx + (nv > 3 ? 1 : 0));
+        DMG_CHECK(smp < g.nb);
+        const double *p = src + smp * g.sb + ps;
+        if (nv == 4) {
+            const double2 e = *reinterpret_cast<const double2 *>(p);
+            const double2 o = *reinterpret_cast<const double2 *>(p + g.hx);
+            v[0] = e.x;
+            v[1] = o.x;
+            v[2] = e.y;
+            v[3] = o.y;
+        } else {
+            v[0] = p[0];
+            if (nv > 1) v[1] = p[g.hx];
+            if (nv > 2) v[2] = p[1];
+        }
+    }
+    double *row = dst + smp * ((long long)g.nx * g.ny * g.nz) + ((long long)k * g.ny + j) * g.nx;
+    const int run = 128 * blockIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int from = 8 * q + (lane >> 2);
+        const double w0 = __shfl_sync(0xffffffffu, v[0], from);
+        const double w1 = __shfl_sync(0xffffffffu, v[1], from);
+        const double w2 = __shfl_sync(0xffffffffu, v[2], from);
+        const double w3 = __shfl_sync(0xffffffffu, v[3], from);
+        const int r = lane & 3;
+        const double w = r == 0 ? w0 : (r == 1 ? w1 : (r == 2 ? w2 : w3));
+        const int i = run + 32 * q + lane;
+        if (i < g.nx) row[i] = w;
     }
 }
 
