@@ -938,9 +938,10 @@ def main():
                         traffic=HALF_SWEEP_TRAFFIC["fp32"] if args.size == 257 else None,
                         peak_source=peak_src + " hbm_gbs", launches=pr["launches"], avg_us=dur * 1e6,
                         algorithmic_bytes=byt, bytes_per_vertex=HALF_SWEEP_BYTES_FP32,
-                        timing="CUDA event nodes around each launch of the kernel inside the replayed graphs, in a "
-                               "second pass of the same pairs after the timed one (%.2f ms per pair with the event "
-                               "nodes)" % pr["pass_ms_per_step"],
+                        timing="CUDA event nodes around each run of consecutive launches of the kernel (the "
+                               "half-sweeps of one smoothing step) inside the replayed graphs, divided by the "
+                               "launches in the run, in a second pass of the same pairs after the timed one "
+                               "(%.2f ms per pair with the event nodes)" % pr["pass_ms_per_step"],
                         note="algorithmic bytes: 20 B per interior vertex per full FP32 sweep (read u, f, D, mu; "
                              "write u), 10 B per half-sweep; frac_kernel_bytes charges the 12 B the colour kernel "
                              "moves")
@@ -951,8 +952,8 @@ def main():
                     traffic=HALF_SWEEP_TRAFFIC["fp64"] if args.size == 257 else None,
                     peak_source="dmg_probe_fma FP64 FMA rate, measured in this run", launches=pr["launches"],
                     avg_us=dur * 1e6, algorithmic_fp64_ops=ops,
-                    timing="CUDA event nodes around each launch, second pass (%.2f ms per pair with the event "
-                           "nodes)" % pr["pass_ms_per_step"])
+                    timing="CUDA event nodes around each run of consecutive launches, second pass (%.2f ms per "
+                           "pair with the event nodes)" % pr["pass_ms_per_step"])
 
     def gbs(res, prec):
         # algorithmic HBM bytes of one pair divided by its time (see the design notes for the per-cycle bytes)

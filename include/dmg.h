@@ -498,15 +498,23 @@ dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
  * dmg_launch_count: kernels this context has launched so far.
  * dmg_profile_begin(ctx, kernel, level): from now on, bracket every launch of
  *   `kernel` (a DMG_KERNEL_* id) on `level` with CUDA events on its stream;
- *   at most `max_launches` launches are recorded.
+ *   at most `max_launches` event pairs are recorded. A run of consecutive
+ *   half-sweeps (the nu1 or nu2 sweeps of one smoothing step) takes one event
+ *   pair around the whole run and counts each of its launches, so the
+ *   duration per launch includes the gaps between them but only 1/n of the
+ *   cost of the event nodes themselves (a few microseconds each).
  * dmg_profile_end: waits for the recorded events and returns the number of
  *   recorded launches and their summed duration in milliseconds.
+ * Profiling re-captures the context's graphs with event nodes in them; they
+ * slow the calls down while it is on, so time the calls with it off.
  */
 enum {
     DMG_KERNEL_SMOOTH = 0,     /* one RB-GS half-sweep (one colour) */
     DMG_KERNEL_RESTRICT = 1,   /* defect + full-weighting restriction */
     DMG_KERNEL_PROLONG = 2,    /* prolongation + correction (FP32 3D levels with
-                                  post-smoothing: fused with the first post half-sweep) */
+                                  post-smoothing: fused with the first post half-sweep,
+                                  or, on levels of at least 2^22 vertices, the
+                                  correction on the colour that half-sweep reads) */
     DMG_KERNEL_RESIDUAL = 3,   /* FP64 residual + norm */
     DMG_KERNEL_GRAD = 4        /* coefficient gradients */
 };

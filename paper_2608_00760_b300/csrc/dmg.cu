@@ -192,6 +192,8 @@ struct dmg_ctx {
     std::vector<int> prof_free;         // unused pairs
     std::vector<int> prof_direct;       // pairs recorded by direct launches since the last harvest
     std::vector<int> *prof_sink = nullptr;
+    std::vector<int> prof_n;            // launches each pair brackets
+    int prof_open = -1;                 // the pair of an open group of launches
     long long prof_count = 0;
     double prof_ms = 0.0;
 };
@@ -290,19 +292,36 @@ dmg_status dalloc(dmg_ctx *c, T **p, size_t n) {
 // A ProfScope brackets the launches of one kernel (kind, level, precision)
 // with an event pair; in a graph capture the records become event nodes that
 // every replay re-records, and the pair is harvested after each replay.
+// Brackets launches of the profiled kernel with an event pair. A group scope
+// (around a run of consecutive launches of the kernel, such as the half-sweeps
+// of smooth()) brackets the whole run with one pair, and the scopes of the
+// launches inside it only count them: per-launch event nodes cost a few
+// microseconds each, which a run of n launches spreads over n.
 struct ProfScope {
     dmg_ctx *c;
     cudaStream_t s;
     int idx = -1;
-    ProfScope(dmg_ctx *c_, int kernel, int level, int fp32, cudaStream_t s_) : c(c_), s(s_) {
-        if (c->prof_kernel == kernel && c->prof_level == level && c->prof_fp32 == fp32 && !c->prof_free.empty()) {
+    bool group = false;
+    ProfScope(dmg_ctx *c_, int kernel, int level, int fp32, cudaStream_t s_, bool group_ = false) : c(c_), s(s_) {
+        if (c->prof_kernel == kernel && c->prof_level == level && c->prof_fp32 == fp32) {
+            if (c->prof_open >= 0) {
+                c->prof_n[c->prof_open]++;   // inside an open group
+                return;
+            }
+            if (c->prof_free.empty()) return;
             idx = c->prof_free.back();
             c->prof_free.pop_back();
+            c->prof_n[idx] = group_ ? 0 : 1;
+            if (group_) {
+                group = true;
+                c->prof_open = idx;
+            }
             cudaEventRecordWithFlags(c->prof_ev[2 * idx], s, cudaEventRecordExternal);
         }
     }
     ~ProfScope() {
         if (idx >= 0) {
+            if (group) c->prof_open = -1;
             cudaEventRecordWithFlags(c->prof_ev[2 * idx + 1], s, cudaEventRecordExternal);
             (c->prof_sink ? c->prof_sink : &c->prof_direct)->push_back(idx);
         }
@@ -313,9 +332,10 @@ struct ProfScope {
 void prof_harvest(dmg_ctx *c, std::vector<int> &pairs, bool release) {
     for (int idx : pairs) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->prof_ev[2 * idx], c->prof_ev[2 * idx + 1]) == cudaSuccess) {
+        if (c->prof_n[idx] > 0 &&
+            cudaEventElapsedTime(&ms, c->prof_ev[2 * idx], c->prof_ev[2 * idx + 1]) == cudaSuccess) {
             c->prof_ms += ms;
-            c->prof_count++;
+            c->prof_count += c->prof_n[idx];
         } else {
             cudaGetLastError();
         }
@@ -476,6 +496,7 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
 // nsweeps RB-GS sweeps; each sweep is the half-sweep of colour `first` then the other
 template <class T>
 dmg_status smooth(dmg_ctx *c, int lev, int first, int nsweeps, cudaStream_t s) {
+    ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s, true);
     for (int it = 0; it < nsweeps; it++) {
         TRY(half_sweep<T>(c, lev, first, s));
         TRY(half_sweep<T>(c, lev, 1 - first, s));
@@ -549,32 +570,32 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
 }
 
 // levels of at least this many vertices (all samples) take the correction on
-// one colour and a plain half-sweep instead of the fused launch
+// one colour and plain half-sweeps instead of the fused launch
 constexpr long long kSplitProlongVertices = 1LL << 22;
 
-// u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev. Only the
-// other colour's corrected values are ever read (by this half-sweep), so only
-// they are formed: on the fly in one FP32 launch that stores the colour's new
-// values (k_prolong_smooth32), or on the large levels stored by
-// k_prolong_colour32 ahead of a plain half-sweep. The half-sweep of the other
-// colour must follow.
+inline bool split_prolong_level(const Level &l) { return (long long)l.g.sb * l.g.nb >= kSplitProlongVertices; }
+
+// u_lev += P u_{lev+1} on the vertices of `color` only (k_prolong_colour32):
+// the values the half-sweep of the other colour, which must follow, reads.
+dmg_status prolong_colour32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
+    Level &l = c->L[lev];
+    Level cl = coarse_of(c, lev);
+    ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
+    const dim3 b = c->tb[1][lev];
+    if (c->nb == 1)
+        dmgk::k_prolong_colour32<false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, color, nullptr);
+    else
+        dmgk::k_prolong_colour32<true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, color, c->mask);
+    return check_launch(c, "prolong_colour");
+}
+
+// u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev, in one
+// FP32 launch that stores only the colour's new values (k_prolong_smooth32):
+// only the other colour's corrected values are ever read (by this half-sweep),
+// so they are formed on the fly. The half-sweep of the other colour must follow.
 dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
     Level &l = c->L[lev];
     Level cl = coarse_of(c, lev);
-    if ((long long)l.g.sb * l.g.nb >= kSplitProlongVertices) {
-        {
-            ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
-            const dim3 b = c->tb[1][lev];
-            if (c->nb == 1)
-                dmgk::k_prolong_colour32<false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, 1 - color,
-                                                                                 nullptr);
-            else
-                dmgk::k_prolong_colour32<true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, 1 - color,
-                                                                                c->mask);
-            TRY(check_launch(c, "prolong_colour"));
-        }
-        return half_sweep<float>(c, lev, color, s);
-    }
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
     return with_coef32(c, l, [&](auto cf) {
         constexpr bool H = decltype(cf)::harmonic;
@@ -675,6 +696,11 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
     TRY(restrict_defect<T>(c, lev, npre > 0 ? 1 - pre_first : -1, s));
     TRY(vcycle<T>(c, lev + 1, transposed, s));
     if (sizeof(T) == 4 && c->dim == 3 && npost > 0 && !c->p.split_prolong) {
+        if (split_prolong_level(c->L[lev])) {
+            // the correction on the colour the first post half-sweep reads
+            TRY(prolong_colour32(c, lev, 1 - postf, s));
+            return smooth<T>(c, lev, postf, npost, s);
+        }
         // correction fused into the first post half-sweep; its other half next
         TRY(prolong_smooth32(c, lev, postf, s));
         TRY(half_sweep<T>(c, lev, 1 - postf, s));
@@ -906,10 +932,16 @@ dmg_status iterate64(dmg_ctx *c, bool transposed, int fixed, dmg_info *info, cud
         const int m = use_mask(c, P);
         Graph &G = c->g_fix[t][m];
         TRY(capture(c, G, [&](cudaStream_t cs) { return vcycle<double>(c, 0, transposed, cs); }));
-        for (int cyc = 1; cyc <= fixed; cyc++) TRY(replay(c, G, s));
+        for (int cyc = 1; cyc <= fixed; cyc++) {
+            TRY(replay(c, G, s));
+            if (c->prof_kernel >= 0 && !G.prof.empty()) {
+                // each replay records the graph's event nodes anew: read them before the next
+                CUDA_TRY(c, cudaStreamSynchronize(s));
+                prof_harvest(c, G.prof, false);
+            }
+        }
         TRY(resid_norm_async(c, l.u, l.f, nullptr, 0, c->mask, s));
         TRY(finish_reduce(c, s));
-        prof_harvest(c, G.prof, false);
         TRY(progress_step(c, P, 1, fixed, true, nullptr, done, s));
         if (info) { info->cycles = fixed; info->outer = fixed; }
         double worst = 0.0;
@@ -2746,6 +2778,8 @@ dmg_status dmg_profile_begin(dmg_ctx *c, int kernel, int level, int precision_fp
     graphs_reset(c);   // graphs are re-captured with event nodes
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.assign(2 * (size_t)max_launches, nullptr);
+    c->prof_n.assign((size_t)max_launches, 0);
+    c->prof_open = -1;
     for (auto &e : c->prof_ev) CUDA_TRY(c, cudaEventCreate(&e));
     c->prof_free.clear();
     for (int i = max_launches - 1; i >= 0; i--) c->prof_free.push_back(i);
