@@ -516,7 +516,9 @@ enum {
                                   or, on levels of at least 2^22 vertices, the
                                   correction on the colour that half-sweep reads) */
     DMG_KERNEL_RESIDUAL = 3,   /* FP64 residual + norm */
-    DMG_KERNEL_GRAD = 4        /* coefficient gradients */
+    DMG_KERNEL_GRAD = 4,       /* coefficient gradients */
+    DMG_KERNEL_TAIL = 5        /* the single-CTA V-cycle of the small levels; `level`
+                                  is the first level it covers */
 };
 unsigned long long dmg_launch_count(const dmg_ctx *ctx);
 

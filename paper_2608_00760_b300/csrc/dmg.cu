@@ -316,13 +316,18 @@ struct ProfScope {
                 group = true;
                 c->prof_open = idx;
             }
-            cudaEventRecordWithFlags(c->prof_ev[2 * idx], s, cudaEventRecordExternal);
+            record(c->prof_ev[2 * idx]);
         }
+    }
+    // an event node inside a capture (prof_sink set), a plain record outside
+    void record(cudaEvent_t e) const {
+        if (c->prof_sink) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
     }
     ~ProfScope() {
         if (idx >= 0) {
             if (group) c->prof_open = -1;
-            cudaEventRecordWithFlags(c->prof_ev[2 * idx + 1], s, cudaEventRecordExternal);
+            record(c->prof_ev[2 * idx + 1]);
             (c->prof_sink ? c->prof_sink : &c->prof_direct)->push_back(idx);
         }
     }
@@ -639,6 +644,7 @@ template <class T>
 dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_first, cudaStream_t s) {
     const int t = sizeof(T) == 4;
     const int l0 = c->tail_first[t];
+    ProfScope ps(c, DMG_KERNEL_TAIL, l0, t, s);
     return dispatch<T>(c, c->L[l0], [&](auto cf0) -> dmg_status {
         using C = decltype(cf0);
         dmgk::TailArgs<T, C> a;

@@ -35,7 +35,8 @@ DMG_OK, DMG_EINVAL, DMG_ENOMEM, DMG_ECUDA, DMG_ENOCONV, DMG_ENAN, DMG_ETIMEOUT =
 DMG_FP64, DMG_MIXED = 0, 1
 DMG_FACE_ARITHMETIC, DMG_FACE_HARMONIC = 0, 1
 DMG_COARSEN_FULL_WEIGHTING, DMG_COARSEN_INJECTION = 0, 1
-DMG_KERNEL_SMOOTH, DMG_KERNEL_RESTRICT, DMG_KERNEL_PROLONG, DMG_KERNEL_RESIDUAL, DMG_KERNEL_GRAD = range(5)
+(DMG_KERNEL_SMOOTH, DMG_KERNEL_RESTRICT, DMG_KERNEL_PROLONG, DMG_KERNEL_RESIDUAL, DMG_KERNEL_GRAD,
+ DMG_KERNEL_TAIL) = range(6)
 DMG_HIST_LEN = 64
 DMG_PHASE_FORWARD, DMG_PHASE_TANGENT, DMG_PHASE_ADJOINT = range(3)
 

@@ -54,6 +54,31 @@ def test_fp64_fixed_cycles_counts(dmg):
     S.close()
 
 
+def test_direct_launches_are_timed(dmg):
+    # the gradient kernel runs outside the captured graphs: its events are plain records
+    w = inputs.tissue(33, seed=63)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"])
+    u = S.solve(T(w["q"]))
+    ref = S.vjp(u, T(w["w"]))
+    out, n, ms = profiled(dmg, S, dmg.DMG_KERNEL_GRAD, False, lambda: S.vjp(u, T(w["w"])))
+    assert n == 1 and ms > 0
+    for a, b in zip(out, ref):
+        assert torch.equal(a, b)
+    # the tail (inside the graphs) is counted on its first level only, once per V-cycle
+    q = T(w["q"])
+    S.solve(q)
+    cycles = S.last_info.cycles
+    counts = []
+    for lev in range(dmg.dmg_levels(S.ctx)):
+        assert dmg.dmg_profile_begin(S.ctx, dmg.DMG_KERNEL_TAIL, lev, 0) == dmg.DMG_OK
+        S.solve(q)
+        st, n, ms = dmg.dmg_profile_end(S.ctx)
+        assert st == dmg.DMG_OK and (n == 0 or ms > 0)
+        counts.append(n)
+    assert sorted(counts)[-1] == cycles and sum(counts) == cycles
+    S.close()
+
+
 def test_mixed_fused_level_counts(dmg):
     w = inputs.tissue(65, seed=61)   # 65^3: a fused level
     S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=dmg.DMG_MIXED)
