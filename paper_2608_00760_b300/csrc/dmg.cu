@@ -126,6 +126,9 @@ struct dmg_ctx {
     int nc = 0;                       // coarsest interior unknowns
     int tail_first[2] = {0, 0};       // first level of the single-CTA tail: [0] FP64, [1] FP32 (nlev: none)
     size_t tail_smem[2] = {0, 0};     // its dynamic shared memory in bytes
+    int tail_img[2] = {0, 0};         // elements of one sample's operator image of the tail levels
+    double *timg64 = nullptr;         // the images, FP64 tail (every sample)
+    float *timg32 = nullptr;          // FP32 tail
     double *Ainv = nullptr;           // coarsest inverse (FP64), nc x nc per sample
     double *M = nullptr;              // Gauss-Jordan work matrix [A | I], nc x 2nc per sample
     int *gj_status = nullptr;         // Gauss-Jordan status per sample (device)
@@ -638,6 +641,50 @@ inline dmgk::VertCoef<float, H> make_coef(const Level &l, dmgk::VertCoef<float, 
     return dmgk::VertCoef<float, H>{l.Dh32, l.mu32};
 }
 
+template <class T>
+T *tail_image(dmg_ctx *c);
+template <>
+double *tail_image<double>(dmg_ctx *c) { return c->timg64; }
+template <>
+float *tail_image<float>(dmg_ctx *c) { return c->timg32; }
+
+// the arguments of the tail kernels of precision T (levels tail_first .. nlev-1)
+template <class T, class C>
+void tail_args(dmg_ctx *c, C cf0, dmgk::TailArgs<T, C> &a) {
+    const int t = sizeof(T) == 4;
+    const int l0 = c->tail_first[t];
+    a.nl = c->nlev - l0;
+    for (int l = 0; l < a.nl; l++) {
+        Level &lv = c->L[l0 + l];
+        a.L[l].g = lv.g;
+        a.L[l].gs = smem_geom(lv.g);
+        a.L[l].u = U<T>(lv);
+        a.L[l].f = F<T>(lv);
+        a.L[l].c = make_coef(lv, cf0);
+        a.L[l].dv = tail_div(lv.g);
+    }
+    a.img = tail_image<T>(c);
+    a.img_elems = c->tail_img[t];
+    a.Ainv = AINV<T>(c);
+    a.nc = c->nc;
+    a.act = c->mask;
+}
+
+// the operator images of the tail levels of samples first .. first+count-1
+// (after their coefficients are built)
+template <class T>
+dmg_status build_tail_image(dmg_ctx *c, int first, int count, cudaStream_t s) {
+    const int t = sizeof(T) == 4;
+    if (c->tail_first[t] >= c->nlev || !tail_image<T>(c)) return DMG_OK;
+    return dispatch<T>(c, c->L[c->tail_first[t]], [&](auto cf0) -> dmg_status {
+        using C = decltype(cf0);
+        dmgk::TailArgs<T, C> a{};
+        tail_args<T>(c, cf0, a);
+        dmgk::k_tail_image<T, C><<<count, 1024, 0, s>>>(a, tail_image<T>(c), first);
+        return check_launch(c, "tail_image");
+    });
+}
+
 // The levels tail_first .. nlev-1 of one V-cycle (descent, exact coarsest
 // solve, ascent) in a launch of one block per sample working in shared memory.
 template <class T>
@@ -647,24 +694,12 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
     ProfScope ps(c, DMG_KERNEL_TAIL, l0, t, s);
     return dispatch<T>(c, c->L[l0], [&](auto cf0) -> dmg_status {
         using C = decltype(cf0);
-        dmgk::TailArgs<T, C> a;
-        a.nl = c->nlev - l0;
-        for (int l = 0; l < a.nl; l++) {
-            Level &lv = c->L[l0 + l];
-            a.L[l].g = lv.g;
-            a.L[l].gs = smem_geom(lv.g);
-            a.L[l].u = U<T>(lv);
-            a.L[l].f = F<T>(lv);
-            a.L[l].c = make_coef(lv, cf0);
-            a.L[l].dv = tail_div(lv.g);
-        }
-        a.Ainv = AINV<T>(c);
-        a.nc = c->nc;
+        dmgk::TailArgs<T, C> a{};
+        tail_args<T>(c, cf0, a);
         a.npre = npre;
         a.npost = npost;
         a.pre_first = pre_first;
         a.post_first = post_first;
-        a.act = c->mask;
         a.load_u = l0 == 0;   // the V-cycle of the finest level continues from the current iterate
         dmgk::k_vcycle_tail<T, C><<<c->nb, 1024, c->tail_smem[t], s>>>(a);
         return check_launch(c, "vcycle_tail");
@@ -1334,6 +1369,8 @@ dmg_status build_coefficients(dmg_ctx *c, int slot, const double *D, const doubl
     TRY(check_launch(c, "gauss_jordan"));
     CUDA_TRY(c, cudaMemcpyAsync(c->hstatus + first, c->gj_status + first, count * sizeof(int),
                                 cudaMemcpyDeviceToHost, s));
+    TRY(build_tail_image<double>(c, first, count, s));
+    if (mixed) TRY(build_tail_image<float>(c, first, count, s));
     return DMG_OK;
 }
 
@@ -1489,12 +1526,22 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
     // single-CTA tail: the small levels, as many as fit the shared-memory budget
     for (int t = 0; t < 2; t++) {
         const size_t esz = t ? sizeof(float) : sizeof(double);
-        const int ncoef = t ? 2 : 5;
-        auto bytes = [&](int first) {
-            size_t e = (size_t)c->nc + 16;
+        const int nops = t ? 4 : 5;   // operator arrays per level in the tail's image
+        // the image of one sample (a multiple of 16 bytes) and the tail's shared memory
+        auto img = [&](int first) {
+            size_t e = 0;
             for (int l = first; l < c->nlev; l++) {
                 Geom gs = smem_geom(c->L[l].g);
-                e += (size_t)gs.sz * gs.nz * (3 + ncoef);
+                e += (size_t)gs.sz * gs.nz * nops;
+            }
+            const size_t q = 16 / esz;
+            return (e + q - 1) / q * q;
+        };
+        auto bytes = [&](int first) {
+            size_t e = (size_t)c->nc + 16 + img(first);
+            for (int l = first; l < c->nlev; l++) {
+                Geom gs = smem_geom(c->L[l].g);
+                e += (size_t)gs.sz * gs.nz * 3;
             }
             return e * esz;
         };
@@ -1509,7 +1556,10 @@ dmg_status setup_impl(dmg_ctx *c, const dmg_params *p, const double *D, const do
         if (c->dim == 2) first = c->nlev;   // the shared-memory tail is 3D only
         c->tail_first[t] = first;
         c->tail_smem[t] = first < c->nlev ? bytes(first) : 0;
+        c->tail_img[t] = first < c->nlev ? (int)img(first) : 0;
     }
+    if (c->tail_first[0] < c->nlev) TRY(dalloc(c, &c->timg64, (size_t)c->tail_img[0] * nb));
+    if (mixed && c->tail_first[1] < c->nlev) TRY(dalloc(c, &c->timg32, (size_t)c->tail_img[1] * nb));
     if (c->pyramid) {
         // every slot's finest level lies above the single-CTA tail (which stages
         // the levels below from the coarse defects) and the coarsest level

@@ -802,8 +802,8 @@ __global__ void k_coarse_solve(Geom g, const T *__restrict__ Ainv, int n, const 
 // ---------------------------------------------------------------------------
 // Single-CTA tail of the V-cycle: the levels from the first tail level down to
 // the coarsest are small (a few thousand vertices at most), where one launch
-// per operation costs more than the work. One block copies their coefficients
-// and the first tail level's right-hand side into shared memory (same split
+// per operation costs more than the work. One block stages their operators
+// and the first tail level's right-hand side in shared memory (same split
 // layout, unpadded rows), runs the whole descent (smoothing, defect,
 // restriction), the exact coarsest solve and the ascent (prolongation,
 // smoothing) there with a block barrier between operations, and writes the
@@ -845,6 +845,8 @@ template <class T, class C>
 struct TailArgs {
     TailLevel<T, C> L[kTailMaxLevels];
     int nl;      // levels in the tail; L[nl-1] is the coarsest
+    const T *img;    // the staged operators of every sample (k_tail_image), img_elems apart
+    int img_elems;
     const T *Ainv;
     int nc;
     int npre, npost, pre_first, post_first;
@@ -853,147 +855,308 @@ struct TailArgs {
                  // begins at the finest level); 0: from zero (a coarse level, Sec. 2.3.1)
 };
 
-// shared-memory coefficient copies
+// One tail level in shared memory: the operator in a form the phases read
+// with one load per term, then u, f and r. The operator: for every vertex p the
+// couplings to its +x, +y and +z neighbours (cx, cy, cz; the -x, -y, -z
+// couplings are the neighbours' entries), the diagonal dg and, for
+// face-coefficient levels (FP64), its reciprocal iv. For vertex-coefficient
+// levels (FP32) the couplings are formed from Dh: face(a, b) is symmetric bit
+// for bit (a + b, and 2ab / (a + b) with the exact doubling), and dg sums them
+// in the order of the grid kernels, so the tail's arithmetic is theirs. The
+// operators of all tail levels of a sample are formed once per setup into an
+// image in global memory (k_tail_image) that each tail launch copies in one
+// contiguous pass. Every array has n = sz * nz elements in the level's
+// unpadded split layout.
+struct TailLv {
+    int nx, ny, nz;        // vertices per axis
+    int hx, sy, sz, n;     // shared-memory split layout
+    int img;               // cx at img; cy, cz, dg (, iv) follow, n apart
+    int base;              // u at base; f, r follow, n apart
+    int lx;                // 2^lx colour slots per interior row
+    unsigned dnx, dny, dnxi, dnyi, dcx, dcy;   // magic divisors (TailDiv)
+};
+
+template <class C>
+struct TailInv;
 template <class T>
-__device__ __forceinline__ FaceCoef<T, false> stage_coef(const FaceCoef<T, true> &cg, const Geom &g, const Geom &gs,
-                                                         const TailDiv &dv, T *&cur) {
-    const int n = (int)(gs.sz * gs.nz);
-    T *cx = cur, *cy = cur + n, *cz = cur + 2 * n, *dg = cur + 3 * n, *iv = cur + 4 * n;
-    cur += 5 * n;
-    for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-        int i, j, k;
-        tail_decode(t, g.nx, dv.nx, g.ny, dv.ny, i, j, k);
-        const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
-        cx[ps] = cg.cx[pg]; cy[ps] = cg.cy[pg]; cz[ps] = cg.cz[pg]; dg[ps] = cg.diag[pg]; iv[ps] = cg.invd[pg];
-    }
-    return FaceCoef<T, false>{cx, cy, cz, dg, iv};
-}
-
+struct TailInv<FaceCoef<T, true>> {
+    static constexpr bool value = true;   // finish = s * iv
+};
 template <class T, bool H>
-__device__ __forceinline__ VertCoef<T, H, false> stage_coef(const VertCoef<T, H, true> &cg, const Geom &g,
-                                                            const Geom &gs, const TailDiv &dv, T *&cur) {
-    const int n = (int)(gs.sz * gs.nz);
-    T *dh = cur, *mu = cur + n;
-    cur += 2 * n;
-    for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-        int i, j, k;
-        tail_decode(t, g.nx, dv.nx, g.ny, dv.ny, i, j, k);
-        const long long pg = g.pos(i, j, k), ps = gs.pos(i, j, k);
-        dh[ps] = cg.Dh[pg]; mu[ps] = cg.mu[pg];
-    }
-    return VertCoef<T, H, false>{dh, mu};
+struct TailInv<VertCoef<T, H, true>> {
+    static constexpr bool value = false;  // finish = s / dg (the fast FP32 divide of the grid kernels)
+};
+
+// shared-memory geometry of a level as a Geom (for the transfer operators)
+__device__ __forceinline__ Geom tail_geom(const TailLv &L) {
+    Geom g{};
+    g.nx = L.nx; g.ny = L.ny; g.nz = L.nz;
+    g.hx = L.hx; g.sy = L.sy; g.sz = L.sz; g.sb = L.n; g.nb = 1;
+    return g;
 }
 
-// The vertices of one colour only: 2^lx slots per interior row (2^lx >= the
-// colour's ceil(nxi / 2) vertices in a row), slot x of row (j, k) being
-// i = 2x + 2 - parity as in the grid kernels; one division per slot.
-template <class T, class CS>
-__device__ __forceinline__ void tail_half(const Geom &g, const TailDiv &dv, T *u, const T *f, const CS &c,
-                                          int color) {
-    const int nxi = g.nx - 2, nyi = g.ny - 2;
-    int lx = 0;
-    while ((1 << lx) < (nxi + 1) / 2) lx++;
-    const int nslot = (nyi * (g.nz - 2)) << lx;
+// the operator of one level: face coefficients copied
+template <class T>
+__device__ __forceinline__ void tail_stage_op(const FaceCoef<T, true> &cg, const Geom &g, const TailLv &L, T *cx) {
+    const int N = L.nx * L.ny * L.nz;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        int i, j, k;
+        tail_decode(t, L.nx, L.dnx, L.ny, L.dny, i, j, k);
+        const long long pg = g.pos(i, j, k);
+        const int ps = k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1);
+        const T x = __ldg(cg.cx + pg), y = __ldg(cg.cy + pg), z = __ldg(cg.cz + pg), d = __ldg(cg.diag + pg),
+                v = __ldg(cg.invd + pg);
+        cx[ps] = x;
+        cx[L.n + ps] = y;
+        cx[2 * L.n + ps] = z;
+        cx[3 * L.n + ps] = d;
+        cx[4 * L.n + ps] = v;
+    }
+}
+
+// the operator of one level: couplings and diagonal formed from Dh, mu
+template <class T, bool H>
+__device__ __forceinline__ void tail_stage_op(const VertCoef<T, H, true> &cg, const Geom &g, const TailLv &L, T *cx) {
+    using CV = VertCoef<T, H, true>;
+    const int N = L.nx * L.ny * L.nz;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        int i, j, k;
+        tail_decode(t, L.nx, L.dnx, L.ny, L.dny, i, j, k);
+        const long long pg = g.pos(i, j, k);
+        const int ps = k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1);
+        const bool ix = i < L.nx - 1, iy = j < L.ny - 1, iz = k < L.nz - 1;
+        const bool in = i > 0 && j > 0 && k > 0 && ix && iy && iz;
+        const T d = __ldg(cg.Dh + pg);
+        const T dxp = ix ? __ldg(cg.Dh + pg + g.xp(i)) : T(0);
+        const T dyp = iy ? __ldg(cg.Dh + pg + g.sy) : T(0);
+        const T dzp = iz ? __ldg(cg.Dh + pg + g.sz) : T(0);
+        T dg = T(0);
+        if (in) {
+            const T a0 = CV::face(d, __ldg(cg.Dh + pg + g.xm(i))), a1 = CV::face(d, dxp);
+            const T a2 = CV::face(d, __ldg(cg.Dh + pg - g.sy)), a3 = CV::face(d, dyp);
+            const T a4 = CV::face(d, __ldg(cg.Dh + pg - g.sz)), a5 = CV::face(d, dzp);
+            dg = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + __ldg(cg.mu + pg));
+        }
+        cx[ps] = ix ? CV::face(d, dxp) : T(0);
+        cx[L.n + ps] = iy ? CV::face(d, dyp) : T(0);
+        cx[2 * L.n + ps] = iz ? CV::face(d, dzp) : T(0);
+        cx[3 * L.n + ps] = dg;
+    }
+}
+
+// f + sum_q a_q u_q over the six neighbours of p (xm: offset of the -x
+// neighbour), in the pairing of coupled_sum; a from the staged couplings
+template <class T>
+__device__ __forceinline__ T tail_coupled(T s, const T *u, const T *cx, int n, int p, int xm, int sy, int sz) {
+    const T *cy = cx + n, *cz = cx + 2 * n;
+    const T a0 = cx[p + xm], a1 = cx[p], a2 = cy[p - sy], a3 = cy[p], a4 = cz[p - sz], a5 = cz[p];
+    if constexpr (sizeof(T) == 8) {
+        s = fma(a0, u[p + xm], s);
+        s = fma(a1, u[p + xm + 1], s);
+        s = fma(a2, u[p - sy], s);
+        s = fma(a3, u[p + sy], s);
+        s = fma(a4, u[p - sz], s);
+        return fma(a5, u[p + sz], s);
+    } else {
+        T s0 = fmaf(a0, u[p + xm], s);
+        T s1 = a2 * u[p - sy];
+        T s2 = a4 * u[p - sz];
+        s0 = fmaf(a1, u[p + xm + 1], s0);
+        s1 = fmaf(a3, u[p + sy], s1);
+        s2 = fmaf(a5, u[p + sz], s2);
+        return (s0 + s1) + s2;
+    }
+}
+
+// Red-black half-sweep of one colour on a staged level: 2^lx slots per
+// interior row (2^lx >= the colour's ceil(nxi / 2) vertices in a row), slot x
+// of row (j, k) being i = 2x + 2 - parity as in the grid kernels.
+template <class T, bool INV>
+__device__ __forceinline__ void tail_half(const TailLv &L, T *S, int color) {
+    T *u = S + L.base, *f = u + L.n;
+    const T *cx = S + L.img;
+    const int nyi = L.ny - 2;
+    const int nslot = (nyi * (L.nz - 2)) << L.lx;
     for (int s = threadIdx.x; s < nslot; s += blockDim.x) {
-        const int row = s >> lx, k = mdiv(row, dv.nyi) + 1, j = row - (k - 1) * nyi + 1;
-        const int i = 2 * (s & ((1 << lx) - 1)) + 2 - ((color + j + k) & 1);
-        if (i <= g.nx - 2) smooth_point(g, u, f, c, i, j, k);
+        const int row = s >> L.lx, k = mdiv(row, L.dnyi) + 1, j = row - (k - 1) * nyi + 1;
+        const int i = 2 * (s & ((1 << L.lx) - 1)) + 2 - ((color + j + k) & 1);
+        if (i > L.nx - 2) continue;
+        const int p = k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1);
+        const int xm = (i & 1) ? -L.hx : L.hx - 1;
+        DMG_CHECK(p - L.sz >= 0 && p + L.sz < L.n);
+        const T sum = tail_coupled(f[p], u, cx, L.n, p, xm, L.sy, L.sz);
+        if constexpr (INV) u[p] = sum * cx[4 * L.n + p];
+        else u[p] = __fdividef(sum, cx[3 * L.n + p]);
     }
     __syncthreads();
+}
+
+// r = f - A u on the interior of a staged level
+template <class T>
+__device__ __forceinline__ void tail_residual(const TailLv &L, T *S) {
+    T *u = S + L.base, *f = u + L.n, *r = u + 2 * L.n;
+    const T *cx = S + L.img;
+    const int nxi = L.nx - 2, nyi = L.ny - 2, n = nxi * nyi * (L.nz - 2);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int i, j, k;
+        tail_decode(t, nxi, L.dnxi, nyi, L.dnyi, i, j, k);
+        i++, j++, k++;
+        const int p = k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1);
+        const int xm = (i & 1) ? -L.hx : L.hx - 1;
+        DMG_CHECK(p - L.sz >= 0 && p + L.sz < L.n);
+        r[p] = tail_coupled(fma(-cx[3 * L.n + p], u[p], f[p]), u, cx, L.n, p, xm, L.sy, L.sz);
+    }
+    __syncthreads();
+}
+
+// the level table (thread 0): operator images first, then u, f, r per level
+template <class T, class C>
+__device__ __forceinline__ void tail_levels(const TailArgs<T, C> &a, TailLv *sL) {
+    constexpr int nops = TailInv<C>::value ? 5 : 4;
+    int img = 0;
+    for (int l = 0; l < a.nl; l++) {
+        const Geom &gs = a.L[l].gs;
+        TailLv &L = sL[l];
+        L.nx = gs.nx; L.ny = gs.ny; L.nz = gs.nz;
+        L.hx = gs.hx; L.sy = gs.sy; L.sz = (int)gs.sz; L.n = (int)(gs.sz * gs.nz);
+        L.img = img;
+        img += nops * L.n;
+        int lx = 0;
+        while ((1 << lx) < (gs.nx - 1) / 2) lx++;
+        L.lx = lx;
+        const TailDiv &dv = a.L[l].dv;
+        L.dnx = dv.nx; L.dny = dv.ny; L.dnxi = dv.nxi; L.dnyi = dv.nyi; L.dcx = dv.cx; L.dcy = dv.cy;
+    }
+    int base = a.img_elems;
+    for (int l = 0; l < a.nl; l++) {
+        sL[l].base = base;
+        base += 3 * sL[l].n;
+    }
+}
+
+// the operator image of samples first .. first + gridDim.x - 1 (one block each)
+template <class T, class C>
+__global__ void __launch_bounds__(1024) k_tail_image(const __grid_constant__ TailArgs<T, C> a, T *img, int first) {
+    __shared__ TailLv sL[kTailMaxLevels];
+    const int smp = first + blockIdx.x;
+    if (threadIdx.x == 0) tail_levels(a, sL);
+    __syncthreads();
+    T *dst = img + (long long)smp * a.img_elems;
+    for (int l = 0; l < a.nl; l++)
+        tail_stage_op(a.L[l].c.shifted(smp * a.L[l].g.sb), a.L[l].g, sL[l], dst + sL[l].img);
 }
 
 // one block per sample
 template <class T, class C>
-__global__ void __launch_bounds__(1024) k_vcycle_tail(TailArgs<T, C> a) {
-    using CS = decltype(stage_coef(a.L[0].c, a.L[0].g, a.L[0].gs, a.L[0].dv, *(T **)nullptr));
+__global__ void __launch_bounds__(1024) k_vcycle_tail(const __grid_constant__ TailArgs<T, C> a) {
+    constexpr bool INV = TailInv<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TailLv sL[kTailMaxLevels];
+    T *S = reinterpret_cast<T *>(smem_raw);
     const int smp = blockIdx.x;
     if (inactive(a.act, smp)) return;
-    T *cur = reinterpret_cast<T *>(smem_raw);
-    T *su[kTailMaxLevels], *sf[kTailMaxLevels], *sr[kTailMaxLevels];
-    CS sc[kTailMaxLevels];
-    for (int l = 0; l < a.nl; l++) {
-        const int n = (int)(a.L[l].gs.sz * a.L[l].gs.nz);
-        su[l] = cur; sf[l] = cur + n; sr[l] = cur + 2 * n;
-        cur += 3 * n;
-        // u starts at zero (boundary included); f and r are read on interior
-        // vertices only, after they are written there
-        for (int t = threadIdx.x; t < n; t += blockDim.x) su[l][t] = T(0);
-        sc[l] = stage_coef(a.L[l].c.shifted(smp * a.L[l].g.sb), a.L[l].g, a.L[l].gs, a.L[l].dv, cur);
-    }
-    T *fs = cur;   // coarsest right-hand side for the dense solve
+    if (threadIdx.x == 0) tail_levels(a, sL);
     {
-        const Geom &g = a.L[0].g, &gs = a.L[0].gs;
-        __syncthreads();
-        for (int t = threadIdx.x; t < g.nx * g.ny * g.nz; t += blockDim.x) {
-            int i, j, k;
-            tail_decode(t, g.nx, a.L[0].dv.nx, g.ny, a.L[0].dv.ny, i, j, k);
-            sf[0][gs.pos(i, j, k)] = a.L[0].f[smp * g.sb + g.pos(i, j, k)];
-            if (a.load_u) su[0][gs.pos(i, j, k)] = a.L[0].u[smp * g.sb + g.pos(i, j, k)];
+        // the sample's operator image: img_elems * sizeof(T) is a multiple of 16 bytes;
+        // four 16-byte loads in flight per thread
+        const float4 *src = reinterpret_cast<const float4 *>(a.img + (long long)smp * a.img_elems);
+        float4 *dst = reinterpret_cast<float4 *>(S);
+        const int n4 = (int)((long long)a.img_elems * sizeof(T) / 16);
+        for (int t0 = threadIdx.x; t0 < n4; t0 += 4 * blockDim.x) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int t = t0 + q * blockDim.x;
+                if (t < n4) v[q] = __ldg(src + t);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int t = t0 + q * blockDim.x;
+                if (t < n4) dst[t] = v[q];
+            }
         }
     }
     __syncthreads();
-    for (int l = 0; l < a.nl - 1; l++) {
-        const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
-        const TailDiv &dv = a.L[l].dv, &dvc = a.L[l + 1].dv;
-        for (int sw = 0; sw < a.npre; sw++) {
-            tail_half(g, dv, su[l], sf[l], sc[l], a.pre_first);
-            tail_half(g, dv, su[l], sf[l], sc[l], 1 - a.pre_first);
-        }
-        const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            int i, j, k;
-            tail_decode(t, nxi, dv.nxi, nyi, dv.nyi, i, j, k);
-            i++, j++, k++;
-            const long long p = g.pos(i, j, k);
-            sr[l][p] = residual_at(su[l], sf[l], sc[l], p, neighbours(g, i));
-        }
+    const int nl = a.nl;
+    T *fs = S + sL[nl - 1].base + 3 * sL[nl - 1].n;   // coarsest right-hand side for the dense solve
+    // u starts at zero (boundary included); f and r are read on interior
+    // vertices only, after they are written there
+    for (int l = 0; l < nl; l++)
+        for (int t = threadIdx.x; t < sL[l].n; t += blockDim.x) S[sL[l].base + t] = T(0);
+    {
+        const Geom &g = a.L[0].g;
+        const TailLv &L = sL[0];
+        T *u = S + L.base, *f = u + L.n;
+        const T *fg = a.L[0].f + smp * g.sb, *ug = a.L[0].u + smp * g.sb;
         __syncthreads();
-        const int cxi = gc.nx - 2, cyi = gc.ny - 2, nc = cxi * cyi * (gc.nz - 2);
+        const int N = L.nx * L.ny * L.nz;
+        for (int t = threadIdx.x; t < N; t += blockDim.x) {
+            int i, j, k;
+            tail_decode(t, L.nx, L.dnx, L.ny, L.dny, i, j, k);
+            const long long pg = g.pos(i, j, k);
+            const int ps = k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1);
+            f[ps] = fg[pg];
+            if (a.load_u) u[ps] = ug[pg];
+        }
+    }
+    __syncthreads();
+    for (int l = 0; l < nl - 1; l++) {
+        const TailLv &L = sL[l], &Lc = sL[l + 1];
+        for (int sw = 0; sw < a.npre; sw++) {
+            tail_half<T, INV>(L, S, a.pre_first);
+            tail_half<T, INV>(L, S, 1 - a.pre_first);
+        }
+        tail_residual(L, S);
+        const Geom g = tail_geom(L), gc = tail_geom(Lc);
+        const T *r = S + L.base + 2 * L.n;
+        T *uc = S + Lc.base, *fc = uc + Lc.n;
+        const int cxi = Lc.nx - 2, cyi = Lc.ny - 2, nc = cxi * cyi * (Lc.nz - 2);
         for (int t = threadIdx.x; t < nc; t += blockDim.x) {
             int I, J, K;
-            tail_decode(t, cxi, dvc.nxi, cyi, dvc.nyi, I, J, K);
+            tail_decode(t, cxi, Lc.dnxi, cyi, Lc.dnyi, I, J, K);
             I++, J++, K++;
-            restrict_point(g, sr[l], gc, sf[l + 1], I, J, K);
-            su[l + 1][gc.pos(I, J, K)] = T(0);
+            restrict_point(g, r, gc, fc, I, J, K);
+            uc[gc.pos(I, J, K)] = T(0);
         }
         __syncthreads();
     }
-    coarse_solve_block(a.L[a.nl - 1].gs, a.Ainv + (long long)smp * a.nc * a.nc, a.nc, sf[a.nl - 1], su[a.nl - 1],
-                       fs);
+    {
+        const TailLv &L = sL[nl - 1];
+        coarse_solve_block(tail_geom(L), a.Ainv + (long long)smp * a.nc * a.nc, a.nc, S + L.base + L.n, S + L.base,
+                           fs);
+    }
     __syncthreads();
-    for (int l = a.nl - 2; l >= 0; l--) {
-        const Geom &g = a.L[l].gs, &gc = a.L[l + 1].gs;
-        const TailDiv &dv = a.L[l].dv, &dvc = a.L[l + 1].dv;
-        const int cx = gc.nx - 1, cy = gc.ny - 1, ncell = cx * cy * (gc.nz - 1);
+    for (int l = nl - 2; l >= 0; l--) {
+        const TailLv &L = sL[l], &Lc = sL[l + 1];
+        const Geom g = tail_geom(L), gc = tail_geom(Lc);
+        const T *ec = S + Lc.base;
+        T *u = S + L.base;
+        const int cx = Lc.nx - 1, cy = Lc.ny - 1, ncell = cx * cy * (Lc.nz - 1);
         for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
             int I, J, K;
-            tail_decode(t, cx, dvc.cx, cy, dvc.cy, I, J, K);
-            prolong_cell(gc, su[l + 1], g, su[l], I, J, K);
+            tail_decode(t, cx, Lc.dcx, cy, Lc.dcy, I, J, K);
+            prolong_cell(gc, ec, g, u, I, J, K);
         }
         __syncthreads();
         for (int sw = 0; sw < a.npost; sw++) {
-            tail_half(g, dv, su[l], sf[l], sc[l], a.post_first);
-            tail_half(g, dv, su[l], sf[l], sc[l], 1 - a.post_first);
+            tail_half<T, INV>(L, S, a.post_first);
+            tail_half<T, INV>(L, S, 1 - a.post_first);
         }
     }
     // the first tail level's solution back to global memory (interior)
-    const Geom &g = a.L[0].g, &gs = a.L[0].gs;
-    const int nxi = g.nx - 2, nyi = g.ny - 2, n = nxi * nyi * (g.nz - 2);
+    const Geom &g = a.L[0].g;
+    const TailLv &L = sL[0];
+    const T *u = S + L.base;
+    T *ug = a.L[0].u + smp * g.sb;
+    const int nxi = L.nx - 2, nyi = L.ny - 2, n = nxi * nyi * (L.nz - 2);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         int i, j, k;
-        tail_decode(t, nxi, a.L[0].dv.nxi, nyi, a.L[0].dv.nyi, i, j, k);
+        tail_decode(t, nxi, L.dnxi, nyi, L.dnyi, i, j, k);
         i++, j++, k++;
-        a.L[0].u[smp * g.sb + g.pos(i, j, k)] = su[0][gs.pos(i, j, k)];
+        ug[g.pos(i, j, k)] = u[k * L.sz + j * L.sy + (i & 1) * L.hx + (i >> 1)];
     }
 }
 
-// shared memory of the tail kernel: u, f, r and the coefficient arrays of every
-// tail level plus the coarsest right-hand side
-template <class T>
-inline size_t tail_smem_elems(const Geom &gs, int ncoef) {
-    return (size_t)gs.sz * gs.nz * (3 + ncoef);
-}
 
 // ---------------------------------------------------------------------------
 // layout conversion between the caller's contiguous [nz][ny][nx] arrays and the
