@@ -67,6 +67,7 @@ VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = None
 
 
 AUTOTUNE = [1]   # set from --autotune
+TWIN = [1]       # set from --twin
 
 
 def percentile(x, p):
@@ -227,13 +228,22 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     D, mu, q, wv = T(w["D"]), T(w["mu"]), T(w["q"]), T(w["w"])
-    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL, inner_cycles=inner, autotune=AUTOTUNE[0])
+    S = dmg.Solver(D, mu, w["h"], precision=precision, rtol=RTOL, inner_cycles=inner, autotune=AUTOTUNE[0],
+                   twin_adjoint=TWIN[0])
     u = torch.empty_like(q)
     qb, Db, mb = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
     info_f, info_a = dmg.dmg_info(), dmg.dmg_info()
     stream = torch.cuda.current_stream(dev)
 
     def step():
+        # one pair through the pair call: the adjoint solve runs beside the
+        # forward one (twin_adjoint, the default)
+        st = dmg.dmg_solve_vjp(S.ctx, q, wv, u, qb, Db, mb, info_f, info_a, stream, n=S.n)
+        if st != dmg.DMG_OK:
+            raise dmg.DMGError(st, dmg.dmg_last_error(S.ctx))
+
+    def step_seq():
+        # the same pair as two calls, one solve after the other
         st = dmg.dmg_solve(S.ctx, q, u, info_f, stream, n=S.n)
         if st != dmg.DMG_OK:
             raise dmg.DMGError(st, dmg.dmg_last_error(S.ctx))
@@ -262,12 +272,25 @@ def run_arm(dmg, torch, w, precision, steps, warmup, world, local, profile=None,
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
     total_ms = ev[0].elapsed_time(ev[steps])
     prof = None
+    seq_ms = None
     if profile is not None:
-        prof = profiled_pass(dmg, torch, S, step, steps, profile[0], profile[1], stream, dev)
+        # kernel durations from the two-call form: no second lane competes for
+        # the GPU while the profiled kernel runs
+        for _ in range(2):
+            step_seq()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step_seq()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms = e0.elapsed_time(e1) / steps
+        prof = profiled_pass(dmg, torch, S, step_seq, steps, profile[0], profile[1], stream, dev)
     res = dict(total_ms=max_over_ranks(world, total_ms), per_ms=per, launches=launches,
                fwd_cycles=info_f.cycles, fwd_outer=info_f.outer, adj_cycles=info_a.cycles,
                adj_outer=info_a.outer, fwd_rel=info_f.rel_residual, adj_rel=info_a.rel_residual,
-               prof=prof, clocks=sampler.summary() if sampler else None, solver=S,
+               prof=prof, seq_ms=seq_ms, clocks=sampler.summary() if sampler else None, solver=S,
                out=(u, qb, Db, mb))
     return res
 
@@ -875,6 +898,9 @@ def main():
     ap.add_argument("--size-2d", type=int, default=4097, help="grid of the 2D solver timing (0: skip)")
     ap.add_argument("--size-513", type=int, default=513, help="larger 3D grid timed next to the headline (0: skip)")
     ap.add_argument("--autotune", type=int, default=1, help="tile autotuner at setup (dmg_params.autotune)")
+    ap.add_argument("--twin", type=int, default=1,
+                    help="dmg_params.twin_adjoint of the headline contexts: 1 runs the adjoint solve of a pair "
+                         "beside the forward one")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     ap.add_argument("--serve-rate-low", type=float, default=100.0,
@@ -888,6 +914,7 @@ def main():
         return
     args.warmup = max(args.warmup, 3)
     AUTOTUNE[0] = args.autotune
+    TWIN[0] = args.twin
     world, rank, local = dist_setup()
 
     import torch
@@ -979,8 +1006,13 @@ def main():
                            adj_outer=head["adj_outer"], fwd_rel=head["fwd_rel"], adj_rel=head["adj_rel"]),
                gpu_launches=head["launches"], gpu_launches_per_step=head["launches"] / args.steps,
                device_memory_gb=dict(context=dmg.dmg_device_bytes(S.ctx) / 1e9,
-                                     note="everything the fwd+VJP pair uses is allocated at setup: the pull-back "
-                                          "adds no device memory to the forward"),
+                                     note="the context and its twin (the adjoint lane dmg_solve_vjp creates on "
+                                          "its first call, outside the timed region); nothing is allocated "
+                                          "inside a pair"),
+               pair_api="dmg_solve_vjp: the adjoint solve (it needs only w) runs in the twin context on its own "
+                        "stream and host thread while the forward one runs; results bit for bit those of "
+                        "dmg_solve + dmg_vjp",
+               sequential_ms_per_step=head["seq_ms"],
                roofline=roofline(head, precisions[0]), clocks=head["clocks"],
                measured_rates=dict(fp64_fma_per_s=FP64_OPS_PEAK[0], fp32_fma_per_s=fp32_rate,
                                    source="dmg_probe_fma (independent FMA chains on every SM, CUDA events)"))

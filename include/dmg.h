@@ -106,12 +106,22 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 reused within the process for the same device, precision,
  *                 grid, batch and face mean, and, if the environment variable
  *                 DMG_TUNE_CACHE names a file, read from and appended to it.
- *   split_prolong 0 (default): on 3D levels of the FP32 V-cycle, the
- *                 prolongation is fused into the first post-smoothing
- *                 half-sweep (the corrected values are formed where that
- *                 half-sweep reads them and never stored); 1: separate
- *                 prolongation and half-sweep kernels. Both give the same
- *                 results bit for bit.
+ *   split_prolong 0 (default): on 3D levels of the FP32 V-cycle, only the
+ *                 corrected values the first post-smoothing half-sweep reads
+ *                 are formed: inside that half-sweep on levels of fewer than
+ *                 2^22 vertices (never stored), by a correction of the other
+ *                 colour alone ahead of a plain half-sweep on larger ones;
+ *                 1: the full prolongation, then the half-sweeps. All give
+ *                 the same results bit for bit.
+ *   twin_adjoint  1 (default): dmg_solve_vjp runs the adjoint solve at the
+ *                 same time as the forward one (it needs only w), on a second
+ *                 context (the "twin": the same parameters and coefficient
+ *                 hierarchy, its own iteration state and streams) that the
+ *                 first dmg_solve_vjp call creates and dmg_set_coefficients
+ *                 keeps in step; it doubles the device memory
+ *                 (dmg_device_bytes counts it). Results are bit for bit those
+ *                 of running the two solves one after the other. 0: one after
+ *                 the other in this context.
  */
 typedef struct {
     int nx, ny, nz;
@@ -128,6 +138,7 @@ typedef struct {
     int batch;
     int autotune;
     int split_prolong;
+    int twin_adjoint;
 } dmg_params;
 
 #define DMG_HIST_LEN 64
@@ -495,7 +506,7 @@ dmg_status dmg_tile(const dmg_ctx *ctx, int level, int fp32, int *bx, int *by);
 /*
  * Instrumentation (for benchmarks; no counterpart in the paper, which times
  * whole calls).
- * dmg_launch_count: kernels this context has launched so far.
+ * dmg_launch_count: kernels this context (and its twin) has launched so far.
  * dmg_profile_begin(ctx, kernel, level): from now on, bracket every launch of
  *   `kernel` (a DMG_KERNEL_* id) on `level` with CUDA events on its stream;
  *   at most `max_launches` event pairs are recorded. A run of consecutive

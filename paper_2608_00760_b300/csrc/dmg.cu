@@ -22,6 +22,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dmg.h"
@@ -137,6 +138,9 @@ struct dmg_ctx {
     double *stage = nullptr;          // contiguous nx*ny*nz buffer for host transfers
     double *stage2 = nullptr;         // a second one, for transfers on the side stream
     cudaStream_t side = nullptr;      // overlaps host transfers with the iteration on the caller's stream
+    dmg_ctx *twin = nullptr;          // dmg_solve_vjp's adjoint lane (twin_adjoint), created on first use
+    cudaStream_t twin_s = nullptr;    // the stream the twin iterates on
+    cudaEvent_t ev_twin = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_aux = nullptr;
     // dmg_solve_vjp_many (allocated on first use): two input staging buffers
     // (q then w, caller layout), two output staging buffers (u, qbar, Dbar,
@@ -1116,6 +1120,7 @@ dmg_status validate(dmg_ctx *c, const dmg_params *p) {
     if (p->batch < 1) return fail(c, DMG_EINVAL, "batch must be >= 1");
     if (p->autotune != 0 && p->autotune != 1) return fail(c, DMG_EINVAL, "autotune must be 0 or 1");
     if (p->split_prolong != 0 && p->split_prolong != 1) return fail(c, DMG_EINVAL, "split_prolong must be 0 or 1");
+    if (p->twin_adjoint != 0 && p->twin_adjoint != 1) return fail(c, DMG_EINVAL, "twin_adjoint must be 0 or 1");
     {
         const Geom g0 = make_geom(p->nx, p->ny, p->nz, 1);
         if (g0.sb > (long long)INT32_MAX)
@@ -1635,6 +1640,8 @@ dmg_status many_alloc(dmg_ctx *c) {
 // buffers one pair ahead; host outputs are laid out on the caller's stream into
 // one of two staging buffers and copied out on the download stream while the
 // next pair iterates. Device arrays are read and written in place.
+dmg_status twin_ready(dmg_ctx *c, cudaStream_t s);
+
 dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, const double *const *w,
                                double *const *u, double *const *qbar, double *const *Dbar, double *const *mubar,
                                dmg_info *info_fwd, dmg_info *info_adj, cudaStream_t s) {
@@ -1642,6 +1649,8 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     for (int i = 0; i < npairs; i++)
         if (!q[i] || !w[i]) return fail(c, DMG_EINVAL, "q[%d] and w[%d] must not be NULL", i, i);
     TRY(many_alloc(c));
+    if (c->p.twin_adjoint) TRY(twin_ready(c, s));
+    dmg_ctx *t = c->twin;
     Level &l = c->L[0];
     const Geom g = geom0(c, -1);
     const size_t n = (size_t)g.nx * g.ny * g.nz * g.nb;
@@ -1691,10 +1700,67 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
         const double *ws = is_device_ptr(w[i]) ? w[i] : c->mi_stage[b] + n;
         dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, qs, l.f, 0);
         TRY(check_launch(c, "gather"));
-        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, ws, c->T3, 0);
+        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, ws, t ? t->L[0].f : c->T3, 0);
         TRY(check_launch(c, "gather"));
         CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
         if (i + 1 < npairs) TRY(upload(i + 1));   // overlaps this pair's iterations
+        if (t) {
+            // the adjoint solve in the twin beside the forward one (see solve_vjp_twin)
+            CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_used[b], 0));
+            dmg_status st2 = DMG_OK;
+            dmg_info *ia = info_adj ? info_adj + i : nullptr;
+            auto adjoint = [&]() { st2 = iterate(t, true, 0, ia, c->twin_s); };
+            std::thread lane;
+            bool threaded = true;
+            try {
+                lane = std::thread(adjoint);
+            } catch (...) {
+                threaded = false;
+            }
+            dmg_status st = iterate(c, false, c->p.fixed_cycles, info_fwd ? info_fwd + i : nullptr, s);
+            if (threaded) lane.join();
+            else adjoint();
+            if (st2 != DMG_OK && st2 != DMG_ENOCONV) {
+                cudaStreamSynchronize(c->twin_s);
+                return abort_all(fail(c, st2, "adjoint solve of pair %d: %s", i, t->err));
+            }
+            if (st != DMG_OK && st != DMG_ENOCONV) {
+                cudaStreamSynchronize(c->twin_s);
+                return abort_all(st);
+            }
+            if (st != DMG_OK || st2 != DMG_OK) worst = DMG_ENOCONV;
+            CUDA_TRY(c, cudaEventRecord(c->ev_twin, c->twin_s));
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_twin, 0));
+            const double *lam = t->L[0].u;
+            double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *qb = out_at(qbar, i), *ud = out_at(u, i);
+            if (Db || mb) {
+                const double ih2 = 1.0 / (l.h * l.h);
+                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+                if (c->dim == 2)
+                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
+                                                                   c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                   Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+                else
+                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
+                                                                 c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                 Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+                TRY(check_launch(c, "grad"));
+            }
+            // the staging slot of pair i-2 must have reached the host
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_out[b], 0));
+            if (ud) TRY(put(l.u, ud, mo));
+            if (qb) TRY(put(lam, qb, mo + n));
+            if (Db) TRY(put(c->T1, Db, mo + 2 * n));
+            if (mb) TRY(put(c->T2, mb, mo + 3 * n));
+            CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready[b], 0));
+            if (ud) TRY(fetch(mo, ud));   // overlap the next pair's iterations
+            if (qb) TRY(fetch(mo + n, qb));
+            if (Db) TRY(fetch(mo + 2 * n, Db));
+            if (mb) TRY(fetch(mo + 3 * n, mb));
+            CUDA_TRY(c, cudaEventRecord(c->ev_out[b], c->down));
+            continue;
+        }
         dmg_status st = iterate(c, false, c->p.fixed_cycles, info_fwd ? info_fwd + i : nullptr, s);
         if (st != DMG_OK && st != DMG_ENOCONV) return abort_all(st);
         if (st != DMG_OK) worst = st;
@@ -1791,6 +1857,10 @@ dmg_status slot_load_impl(dmg_ctx *c, int slot, const double *D, const double *m
 dmg_status set_coefficients_impl(dmg_ctx *c, const double *D, const double *mu, cudaStream_t s) {
     if (!D || !mu) return fail(c, DMG_EINVAL, "D and mu must not be NULL");
     TRY(need_whole(c));
+    if (c->twin) {
+        const dmg_status st = set_coefficients_impl(c->twin, D, mu, s);
+        if (st != DMG_OK) return fail(c, st, "%s", c->twin->err);
+    }
     TRY(build_coefficients(c, -1, D, mu, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     for (Slot &sl : c->slots) {
@@ -1805,6 +1875,120 @@ dmg_status set_coefficients_impl(dmg_ctx *c, const double *D, const double *mu, 
                         "coarsest-level matrix of sample %d is not positive definite (need D > 0, mu >= 0)", b);
         }
     return DMG_OK;
+}
+
+dmg_status destroy_impl(dmg_ctx *c);
+
+// The twin of a context: the same parameters and coefficient hierarchy (built
+// again from level 0's D and mu), its own iteration state, graphs and streams,
+// so that an adjoint solve can run in it while the context solves forward.
+dmg_status twin_ready(dmg_ctx *c, cudaStream_t s) {
+    if (c->twin) return DMG_OK;
+    const Geom g = c->L[0].g;
+    const size_t n = (size_t)g.nx * g.ny * g.nz * g.nb;
+    double *Dd = nullptr, *md = nullptr;
+    cudaError_t e = cudaMalloc(&Dd, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&md, n * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(Dd);
+        return fail(c, DMG_ENOMEM, "twin context: cudaMalloc of %zu bytes failed", 2 * n * sizeof(double));
+    }
+    dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, c->L[0].D, Dd);
+    dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, c->L[0].mu, md);
+    dmg_status st = check_launch(c, "scatter");
+    dmg_ctx *t = nullptr;
+    if (st == DMG_OK) {
+        t = new (std::nothrow) dmg_ctx();
+        if (!t) st = fail(c, DMG_ENOMEM, "twin context: out of host memory");
+    }
+    if (st == DMG_OK) {
+        dmg_params p = c->p;
+        p.autotune = 0;   // the context's tiles are copied below
+        p.twin_adjoint = 0;
+        st = setup_impl(t, &p, Dd, md, s);
+        if (st != DMG_OK) st = fail(c, st, "twin context: %s", t->err);
+    }
+    if (st == DMG_OK) {
+        memcpy(t->tb, c->tb, sizeof(c->tb));
+        if (cudaStreamCreateWithFlags(&c->twin_s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_twin, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(c, DMG_ECUDA, "twin context: stream or event creation failed");
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(Dd);
+    cudaFree(md);
+    if (st != DMG_OK) {
+        if (t) destroy_impl(t);
+        return st;
+    }
+    c->twin = t;
+    return DMG_OK;
+}
+
+// Forward solve and VJP with the adjoint solve A^T lam = w in the twin, on its
+// own stream and host thread, while the forward one runs here; the gradient
+// kernel then reads u from this context and lam from the twin.
+dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *u, double *qbar, double *Dbar,
+                          double *mubar, dmg_info *info_fwd, dmg_info *info_adj, cudaStream_t s) {
+    dmg_ctx *t = c->twin;
+    Level &l = c->L[0];
+    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));   // the adjoint lane starts after the caller's earlier work
+    CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_fork, 0));
+    dmg_status st2 = DMG_OK;
+    auto adjoint = [&]() {
+        st2 = stage_in(t, w, t->L[0].f, false, c->twin_s);
+        if (st2 == DMG_OK) st2 = iterate(t, true, 0, info_adj, c->twin_s);
+    };
+    std::thread lane;
+    bool threaded = true;
+    try {
+        lane = std::thread(adjoint);
+    } catch (...) {
+        threaded = false;   // no thread: the adjoint runs after the forward solve
+    }
+    dmg_status st = stage_in(c, q, l.f, false, s);
+    if (st == DMG_OK) st = iterate(c, false, c->p.fixed_cycles, info_fwd, s);
+    if (threaded) lane.join();
+    else adjoint();
+    if (st2 != DMG_OK && st2 != DMG_ENOCONV) {
+        cudaStreamSynchronize(c->twin_s);
+        cudaStreamSynchronize(s);
+        return fail(c, st2, "adjoint solve: %s", t->err);
+    }
+    if (st != DMG_OK && st != DMG_ENOCONV) {
+        cudaStreamSynchronize(c->twin_s);
+        return st;
+    }
+    if (st == DMG_OK && st2 == DMG_ENOCONV) fail(c, st2, "adjoint solve: %s", t->err);
+    CUDA_TRY(c, cudaEventRecord(c->ev_twin, c->twin_s));
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_twin, 0));
+    const double *lam = t->L[0].u;
+    // u and qbar are read out on the side stream while the gradient kernel runs
+    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    if (u) TRY(stage_out(c, l.u, u, c->side, -1, c->stage2));
+    if (qbar) TRY(stage_out(c, lam, qbar, c->side, -1, c->stage2));
+    CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
+    if (Dbar || mubar) {
+        const double ih2 = 1.0 / (l.h * l.h);
+        ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+        if (c->dim == 2)
+            dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
+                                                           c->p.face_mean == DMG_FACE_HARMONIC,
+                                                           Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+        else
+            dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC,
+                                                         Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
+        TRY(check_launch(c, "grad"));
+        if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
+        if (mubar) TRY(stage_out(c, c->T2, mubar, s));
+    }
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    TRY(end_call(c, s));
+    return st != DMG_OK ? st : st2;
 }
 
 dmg_status slot_begin_impl(dmg_ctx *c, int slot, int phase, const double *a, const double *b, const double *d,
@@ -2269,6 +2453,42 @@ dmg_status guarded(dmg_ctx *c, F fn, const char *name = "dmg") {
     return st;
 }
 
+dmg_status destroy_impl(dmg_ctx *c) {
+    if (!c) return DMG_OK;
+    if (c->twin) destroy_impl(c->twin);
+    if (c->twin_s) {
+        cudaStreamSynchronize(c->twin_s);
+        cudaStreamDestroy(c->twin_s);
+    }
+    if (c->ev_twin) cudaEventDestroy(c->ev_twin);
+    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
+    graphs_reset(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    for (cudaStream_t st : {c->up, c->down})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (int b = 0; b < 2; b++)
+        for (cudaEvent_t e : {c->ev_in[b], c->ev_used[b], c->ev_ready_u[b], c->ev_ready[b], c->ev_out[b]})
+            if (e) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_aux) cudaEventDestroy(c->ev_aux);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    for (void *q : c->dev_allocs) cudaFree(q);
+    if (c->hred) cudaFreeHost(c->hred);
+    if (c->hact) cudaFreeHost(c->hact);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
+    if (c->hact_a) cudaFreeHost(c->hact_a);
+    delete c;
+    return DMG_OK;
+}
+
 }  // namespace
 
 // results of the arithmetic-rate probe land here only if they are impossible
@@ -2298,6 +2518,7 @@ void dmg_default_params(dmg_params *p) {
     p->coarsen = DMG_COARSEN_FULL_WEIGHTING;
     p->inner_cycles = 3;
     p->batch = 1;
+    p->twin_adjoint = 1;
 }
 
 dmg_status dmg_setup(const dmg_params *p, const double *D, const double *mu, void *stream, dmg_ctx **out) {
@@ -2398,6 +2619,10 @@ dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u
         info_reset(info_fwd);
         info_reset(info_adj);
         cudaStream_t s = S(stream);
+        if (c->p.twin_adjoint) {
+            TRY(twin_ready(c, s));
+            return solve_vjp_twin(c, q, w, u, qbar, Dbar, mubar, info_fwd, info_adj, s);
+        }
         Level &l = c->L[0];
         // w goes to T3 on the side stream while the forward iterates
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
@@ -2658,35 +2883,7 @@ dmg_status dmg_residual(dmg_ctx *c, const double *q, const double *u, double *ou
     }, "dmg_residual");
 }
 
-dmg_status dmg_destroy(dmg_ctx *c) {
-    if (!c) return DMG_OK;
-    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
-    graphs_reset(c);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        cudaStreamDestroy(c->side);
-    }
-    for (cudaStream_t st : {c->up, c->down})
-        if (st) {
-            cudaStreamSynchronize(st);
-            cudaStreamDestroy(st);
-        }
-    for (int b = 0; b < 2; b++)
-        for (cudaEvent_t e : {c->ev_in[b], c->ev_used[b], c->ev_ready_u[b], c->ev_ready[b], c->ev_out[b]})
-            if (e) cudaEventDestroy(e);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->ev_aux) cudaEventDestroy(c->ev_aux);
-    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
-    for (void *q : c->dev_allocs) cudaFree(q);
-    if (c->hred) cudaFreeHost(c->hred);
-    if (c->hact) cudaFreeHost(c->hact);
-    if (c->hstatus) cudaFreeHost(c->hstatus);
-    if (c->hact_a) cudaFreeHost(c->hact_a);
-    delete c;
-    return DMG_OK;
-}
+dmg_status dmg_destroy(dmg_ctx *c) { return destroy_impl(c); }
 
 const char *dmg_strerror(dmg_status s) {
     switch (s) {
@@ -2782,7 +2979,7 @@ dmg_status dmg_slot_read(dmg_ctx *c, int slot, double *u, double *x, double *Dba
     return guarded(c, [&]() { return slot_read_impl(c, slot, u, x, Dbar, mubar, S(stream)); }, "dmg_slot_read");
 }
 
-size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes : 0; }
+size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes + (c->twin ? c->twin->dev_bytes : 0) : 0; }
 
 void dmg_debug_fail_alloc(long long n) { g_fail_alloc_at.store(n > 0 ? n : 0); }
 
@@ -2826,7 +3023,9 @@ dmg_status dmg_level_shape(const dmg_ctx *c, int level, int *nx, int *ny, int *n
     return DMG_OK;
 }
 
-unsigned long long dmg_launch_count(const dmg_ctx *c) { return c ? c->launches : 0; }
+unsigned long long dmg_launch_count(const dmg_ctx *c) {
+    return c ? c->launches + (c->twin ? c->twin->launches : 0) : 0;
+}
 
 dmg_status dmg_profile_begin(dmg_ctx *c, int kernel, int level, int precision_fp32, int max_launches) {
     if (!c || max_launches < 1 || level < 0 || level >= c->nlev) return DMG_EINVAL;

@@ -47,7 +47,8 @@ class dmg_params(ctypes.Structure):
                 ("symmetric", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("fixed_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("face_mean", ctypes.c_int),
                 ("coarsen", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("batch", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("split_prolong", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("split_prolong", ctypes.c_int),
+                ("twin_adjoint", ctypes.c_int)]
 
 
 class dmg_info(ctypes.Structure):

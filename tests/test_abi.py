@@ -59,6 +59,7 @@ def test_default_params_and_strerror(dmg):
     dict(nx=9, ny=9, nz=9, h=1.0, max_cycles=0),
     dict(nx=9, ny=9, nz=9, h=1.0, inner_cycles=0),
     dict(nx=9, ny=9, nz=9, h=1.0, split_prolong=2),
+    dict(nx=9, ny=9, nz=9, h=1.0, twin_adjoint=2),
     dict(nx=65, ny=257, nz=257, h=1.0),              # coarsens to 3x9x9: fine; 7x7x513 is not
     dict(nx=7, ny=7, nz=513, h=1.0),                 # 7 -> 4 stops coarsening at 4x4x257: 1020 unknowns
 ])

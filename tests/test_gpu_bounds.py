@@ -102,15 +102,17 @@ def pyramid(prec):
 run("pyramid p0", lambda: pyramid(0))
 run("pyramid p1", lambda: pyramid(1))
 
-def many():
+def many(twin):
     w = inputs.vi_batch(17, 2, seed=7)
-    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=1)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=1, twin_adjoint=twin)
     hq, hw = np.ascontiguousarray(w["q"]), np.ascontiguousarray(w["w"])
     outs = [[np.zeros(w["q"].shape) for _ in range(2)] for _ in range(4)]
     assert dmg.dmg_solve_vjp_many(S.ctx, [hq, hq], [hw, hw], *outs, n=S.n) == dmg.DMG_OK
+    assert dmg.dmg_solve_vjp(S.ctx, hq, hw, *(o[0] for o in outs), n=S.n) == dmg.DMG_OK
     S.set_coefficients(T(w["D"]), T(w["mu"]))
     S.close()
-run("solve_vjp_many, set_coefficients", many)
+run("solve_vjp_many, solve_vjp, set_coefficients (one lane)", lambda: many(0))
+run("solve_vjp_many, solve_vjp, set_coefficients (twin lane)", lambda: many(1))
 torch.cuda.synchronize()
 print(json.dumps(dict(runs=runs, oob=dmg.dmg_debug_oob_count())))
 '''

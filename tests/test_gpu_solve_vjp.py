@@ -1,7 +1,8 @@
 """dmg_solve_vjp (forward solve and converged pull-back in one call, host
-transfers overlapped on a second stream) gives bit for bit the results of
-dmg_solve followed by dmg_vjp, with host or device arrays, FP64 or mixed,
-single problems, batches and 2D grids."""
+transfers overlapped on a second stream, the adjoint solve beside the forward
+one in the twin context) gives bit for bit the results of dmg_solve followed by
+dmg_vjp, with host or device arrays, FP64 or mixed, single problems, batches
+and 2D grids; so does dmg_solve_vjp_many over a stream of pairs."""
 import numpy as np
 import pytest
 
@@ -60,13 +61,15 @@ def test_solve_vjp_is_bitwise_solve_then_vjp(dmg, case, precision, host):
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("where", ["host", "device", "mixed"])
-def test_many_pairs_are_bitwise_single_pairs(dmg, case, precision, where):
+@pytest.mark.parametrize("twin", [0, 1])
+def test_many_pairs_are_bitwise_single_pairs(dmg, case, precision, where, twin):
     # dmg_solve_vjp_many over four pairs (different sources and cotangents, as a
     # sampler streams them): each pair's outputs equal dmg_solve_vjp on that
-    # pair, with host arrays (transfers overlapped), device arrays, or both kinds
+    # pair, with host arrays (transfers overlapped), device arrays, or both
+    # kinds; the adjoint solves in the twin context or after the forward ones
     _, make, dim = case
     w = make()
-    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, dim=dim)
+    S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, dim=dim, twin_adjoint=twin)
     rng = np.random.default_rng(7)
     pairs = [(w["q"] * (1.0 + 0.5 * p), w["w"] * rng.standard_normal(w["q"].shape)) for p in range(4)]
     ref = []
@@ -107,3 +110,40 @@ def test_many_pairs_argument_errors(dmg):
     assert dmg.lib().dmg_solve_vjp_many(S.ctx, 0, None, None, None, None, None, None, None, None, None) == \
         dmg.DMG_EINVAL
     S.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_twin_lane_is_bitwise_one_lane(dmg, precision):
+    # the adjoint solve in the twin context (twin_adjoint = 1, the default) and in
+    # the context itself after the forward one (twin_adjoint = 0)
+    w = inputs.tissue(33, seed=114)
+    D, mu, q, wv = (T(w[k]) for k in ("D", "mu", "q", "w"))
+    A = dmg.Solver(D, mu, w["h"], precision=precision)
+    B = dmg.Solver(D, mu, w["h"], precision=precision, twin_adjoint=0)
+    bytes_before = dmg.dmg_device_bytes(A.ctx)
+    outs = {}
+    for name, S in (("twin", A), ("one", B)):
+        got = [torch.empty_like(q) for _ in range(4)]
+        fi, ai = dmg.dmg_info(), dmg.dmg_info()
+        for _ in range(2):   # the first call creates the twin, the second reuses it
+            assert dmg.dmg_solve_vjp(S.ctx, q, wv, *got, fi, ai, n=S.n) == dmg.DMG_OK
+        outs[name] = (got, fi.cycles, ai.cycles)
+    for a, b in zip(outs["twin"][0], outs["one"][0]):
+        assert torch.equal(a, b)
+    assert outs["twin"][1:] == outs["one"][1:]
+    # the twin holds a second copy of the context's device arrays
+    assert dmg.dmg_device_bytes(A.ctx) >= 2 * bytes_before - 4096
+    assert dmg.dmg_device_bytes(B.ctx) == bytes_before
+    # new coefficients reach the twin as well
+    w2 = inputs.tissue(33, seed=115)
+    D2, mu2 = T(w2["D"]), T(w2["mu"])
+    A.set_coefficients(D2, mu2)
+    got = [torch.empty_like(q) for _ in range(4)]
+    assert dmg.dmg_solve_vjp(A.ctx, q, wv, *got, n=A.n) == dmg.DMG_OK
+    F = dmg.Solver(D2, mu2, w["h"], precision=precision, twin_adjoint=0)
+    ref = [torch.empty_like(q) for _ in range(4)]
+    assert dmg.dmg_solve_vjp(F.ctx, q, wv, *ref, n=F.n) == dmg.DMG_OK
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    for S in (A, B, F):
+        S.close()
