@@ -576,6 +576,43 @@ def run_2d(dmg, torch, args, world, local, peaks, peak_src):
     return out
 
 
+def run_levels(dmg, torch, S, w, local):
+    """Where a pair's time goes: for each kernel kind and level of the headline
+    context, the launches per pair and their event-timed duration (dmg_profile;
+    runs of consecutive half-sweeps share one event pair), from the two-call
+    form of the pair so that no second lane runs beside the kernel."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    q, wv = T(w["q"]), T(w["w"])
+    u = torch.empty_like(q)
+    qb, Db, mb = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
+
+    def step():
+        assert dmg.dmg_solve(S.ctx, q, u, None, stream, n=S.n) == dmg.DMG_OK
+        assert dmg.dmg_vjp(S.ctx, u, wv, 0, qb, Db, mb, None, stream, n=S.n) == dmg.DMG_OK
+
+    names = [(dmg.DMG_KERNEL_SMOOTH, "smooth"), (dmg.DMG_KERNEL_RESTRICT, "restrict"),
+             (dmg.DMG_KERNEL_PROLONG, "prolong"), (dmg.DMG_KERNEL_TAIL, "tail"),
+             (dmg.DMG_KERNEL_RESIDUAL, "residual_fp64"), (dmg.DMG_KERNEL_GRAD, "grad")]
+    reps = 3
+    rows, total = {}, 0.0
+    for lev in range(dmg.dmg_levels(S.ctx)):
+        for fp32 in (True, False):
+            for kind, name in names:
+                dmg.dmg_profile_begin(S.ctx, kind, lev, fp32, max_launches=4096)
+                for _ in range(reps):
+                    step()
+                torch.cuda.synchronize(dev)
+                _, n, ms = dmg.dmg_profile_end(S.ctx)
+                if n:
+                    key = "L%d %s %s" % (lev, "fp32" if fp32 else "fp64", name)
+                    rows[key] = dict(launches_per_pair=n / reps, avg_us=1e3 * ms / n, us_per_pair=1e3 * ms / reps)
+                    total += 1e3 * ms / reps
+    return dict(note="event-timed inside the replayed graphs (a few us of event-node cost per run of launches "
+                     "included); two-call pair", kernels=rows, sum_us_per_pair=total)
+
+
 def run_setup(dmg, torch, args, world, local):
     """The cost of row a1 (the coefficient hierarchy): dmg_setup (allocation, hierarchy, coarsest inverse, no
     autotuning), dmg_set_coefficients (the hierarchy rebuilt in place for new coefficients) and dmg_slot_load (one
@@ -906,6 +943,7 @@ def main():
     ap.add_argument("--serve-rate-low", type=float, default=100.0,
                     help="arrival rate of a second stream below capacity (0: skip it)")
     ap.add_argument("--no-setup", action="store_true", help="skip the setup-cost timings")
+    ap.add_argument("--no-levels", action="store_true", help="skip the per-level kernel timings")
     ap.add_argument("--serve-pyramid", type=int, default=1,
                     help="also serve the stream with the cube shapes in one pyramid pool (0: skip)")
     args = ap.parse_args()
@@ -1027,6 +1065,8 @@ def main():
         a, b = results["mixed"]["out"], results["fp64"]["out"]
         out["mixed_vs_fp64_rel_err"] = {k: float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
                                         for k, x, y in zip(("u", "qbar", "Dbar", "mubar"), a, b)}
+    out["levels"] = (run_levels(dmg, torch, head["solver"], w, local)
+                     if rank == 0 and world == 1 and not args.no_levels else None)
     for r in results.values():
         r["solver"].close()
         r.pop("out", None)
