@@ -1072,7 +1072,7 @@ def main():
         r.pop("out", None)
 
     if not args.no_e2e:
-        ns = max(6, args.steps // 2)
+        ns = max(6, args.steps)
         e = run_e2e(dmg, torch, w, dmg.DMG_MIXED if precisions[0] == "mixed" else dmg.DMG_FP64,
                     ns, 1, world, local, inner=args.inner)
         out["e2e"] = dict(value=world * ns / e["seconds"], unit=UNIT, h2d_bytes_per_step=e["h2d"],

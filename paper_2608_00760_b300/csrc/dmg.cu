@@ -1669,20 +1669,22 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     };
     // lay src out into dst (device) or into the output staging slot, whose copy to
     // the host follows on the download stream
-    auto put = [&](const double *src, double *dst, double *stage_slot) -> dmg_status {
+    auto put_on = [&](const double *src, double *dst, double *stage_slot, cudaStream_t st) -> dmg_status {
         if (is_device_ptr(dst)) {
-            dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, dst);
+            dmgk::k_scatter<<<quad_grid(g), blk(), 0, st>>>(g, src, dst);
             return check_launch(c, "scatter");
         }
-        dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, stage_slot);
+        dmgk::k_scatter<<<quad_grid(g), blk(), 0, st>>>(g, src, stage_slot);
         return check_launch(c, "scatter");
     };
+    auto put = [&](const double *src, double *dst, double *stage_slot) { return put_on(src, dst, stage_slot, s); };
     auto fetch = [&](const double *stage_slot, double *dst) -> dmg_status {
         if (dst && !is_device_ptr(dst))
             CUDA_TRY(c, cudaMemcpyAsync(dst, stage_slot, bytes, cudaMemcpyDeviceToHost, c->down));
         return DMG_OK;
     };
     auto abort_all = [&](dmg_status st) {
+        cudaStreamSynchronize(c->side);
         cudaStreamSynchronize(c->up);
         cudaStreamSynchronize(c->down);
         return st;
@@ -1731,28 +1733,37 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             if (st != DMG_OK || st2 != DMG_OK) worst = DMG_ENOCONV;
             CUDA_TRY(c, cudaEventRecord(c->ev_twin, c->twin_s));
             CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_twin, 0));
-            const double *lam = t->L[0].u;
+            // u and lam into U0 and T3 (once the side stream is done with pair i-1's),
+            // so that the next pair's solves can start while this pair's gradients and
+            // read-out run on the side stream
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+            TRY(dcopy(c, c->U0, l.u, l.n, s));
+            TRY(dcopy(c, c->T3, t->L[0].u, l.n, s));
+            CUDA_TRY(c, cudaEventRecord(c->ev_aux, s));
+            cudaStream_t sd = c->side;
+            CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_aux, 0));
             double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *qb = out_at(qbar, i), *ud = out_at(u, i);
             if (Db || mb) {
                 const double ih2 = 1.0 / (l.h * l.h);
-                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, sd);
                 if (c->dim == 2)
-                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
-                                                                   c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                   Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2,
+                                                                    c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                    Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
                 else
-                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
-                                                                 c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                 Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
+                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2,
+                                                                  c->p.face_mean == DMG_FACE_HARMONIC,
+                                                                  Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
                 TRY(check_launch(c, "grad"));
             }
             // the staging slot of pair i-2 must have reached the host
-            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_out[b], 0));
-            if (ud) TRY(put(l.u, ud, mo));
-            if (qb) TRY(put(lam, qb, mo + n));
-            if (Db) TRY(put(c->T1, Db, mo + 2 * n));
-            if (mb) TRY(put(c->T2, mb, mo + 3 * n));
-            CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], s));
+            CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_out[b], 0));
+            if (ud) TRY(put_on(c->U0, ud, mo, sd));
+            if (qb) TRY(put_on(c->T3, qb, mo + n, sd));
+            if (Db) TRY(put_on(c->T1, Db, mo + 2 * n, sd));
+            if (mb) TRY(put_on(c->T2, mb, mo + 3 * n, sd));
+            CUDA_TRY(c, cudaEventRecord(c->ev_join, sd));   // U0, T3, T1, T2 free again
+            CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], sd));
             CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready[b], 0));
             if (ud) TRY(fetch(mo, ud));   // overlap the next pair's iterations
             if (qb) TRY(fetch(mo + n, qb));
@@ -1801,6 +1812,7 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
         if (mb) TRY(fetch(mo + 3 * n, mb));
         CUDA_TRY(c, cudaEventRecord(c->ev_out[b], c->down));
     }
+    CUDA_TRY(c, cudaStreamSynchronize(c->side));
     CUDA_TRY(c, cudaStreamSynchronize(c->up));
     CUDA_TRY(c, cudaStreamSynchronize(c->down));
     TRY(end_call(c, s));
