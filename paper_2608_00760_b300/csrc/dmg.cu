@@ -1953,6 +1953,18 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
     auto adjoint = [&]() {
         st2 = stage_in(t, w, t->L[0].f, false, c->twin_s);
         if (st2 == DMG_OK) st2 = iterate(t, true, 0, info_adj, c->twin_s);
+        if (st2 != DMG_OK && st2 != DMG_ENOCONV) return;
+        // lam is ready for the gradient kernel; qbar = lam leaves while the forward
+        // lane still iterates (the adjoint solve is the shorter one)
+        if (cudaEventRecord(c->ev_twin, c->twin_s) != cudaSuccess) {
+            cudaGetLastError();
+            st2 = fail(t, DMG_ECUDA, "event record failed");
+            return;
+        }
+        if (qbar) {
+            const dmg_status so = stage_out(t, t->L[0].u, qbar, c->twin_s);
+            if (so != DMG_OK) st2 = so;
+        }
     };
     std::thread lane;
     bool threaded = true;
@@ -1975,14 +1987,13 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
         return st;
     }
     if (st == DMG_OK && st2 == DMG_ENOCONV) fail(c, st2, "adjoint solve: %s", t->err);
-    CUDA_TRY(c, cudaEventRecord(c->ev_twin, c->twin_s));
-    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_twin, 0));
+    CUDA_TRY(c, cudaEventRecord(c->ev_aux, c->twin_s));   // the lane's read-out of qbar ends
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_twin, 0));   // lam ready
     const double *lam = t->L[0].u;
-    // u and qbar are read out on the side stream while the gradient kernel runs
+    // u is read out on the side stream while the gradient kernel runs
     CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
     CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     if (u) TRY(stage_out(c, l.u, u, c->side, -1, c->stage2));
-    if (qbar) TRY(stage_out(c, lam, qbar, c->side, -1, c->stage2));
     CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
     if (Dbar || mubar) {
         const double ih2 = 1.0 / (l.h * l.h);
@@ -1999,6 +2010,7 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
         if (mubar) TRY(stage_out(c, c->T2, mubar, s));
     }
     CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_aux, 0));
     TRY(end_call(c, s));
     return st != DMG_OK ? st : st2;
 }
