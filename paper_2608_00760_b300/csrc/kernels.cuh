@@ -411,7 +411,7 @@ __device__ __forceinline__ bool colour_pair32(const Geom &g, int color, const in
     P.q = row + (1 - par) * g.hx + m;
     g.check(P.p - g.sz);
     g.check(P.p + g.sz + 1);
-    g.check(P.q - 1 + 2 * par);   // the third x neighbour: q - 1 (par 0) or q + 2 (par 1)
+    g.check(par ? P.q + 2 : P.q - 1);   // the third x neighbour: q - 1 (par 0) or q + 2 (par 1)
     g.check(P.q + 1);
     return true;
 }
