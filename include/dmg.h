@@ -119,7 +119,8 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 hierarchy, its own iteration state and streams) that the
  *                 first dmg_solve_vjp call creates and dmg_set_coefficients
  *                 keeps in step; it doubles the device memory
- *                 (dmg_device_bytes counts it). Results are bit for bit those
+ *                 (dmg_device_bytes counts it); when that memory cannot be
+ *                 had the pair runs in one lane. Results are bit for bit those
  *                 of running the two solves one after the other. 0: one after
  *                 the other in this context.
  */

@@ -1660,7 +1660,12 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     for (int i = 0; i < npairs; i++)
         if (!q[i] || !w[i]) return fail(c, DMG_EINVAL, "q[%d] and w[%d] must not be NULL", i, i);
     TRY(many_alloc(c));
-    if (c->p.twin_adjoint) TRY(twin_ready(c, s));
+    if (c->p.twin_adjoint) {
+        // without device memory for the twin the pairs run in one lane
+        const dmg_status tw = twin_ready(c, s);
+        if (tw != DMG_OK && tw != DMG_ENOMEM) return tw;
+        c->err[0] = 0;
+    }
     dmg_ctx *t = c->twin;
     Level &l = c->L[0];
     const Geom g = geom0(c, -1);
@@ -2655,8 +2660,11 @@ dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u
         info_reset(info_adj);
         cudaStream_t s = S(stream);
         if (c->p.twin_adjoint) {
-            TRY(twin_ready(c, s));
-            return solve_vjp_twin(c, q, w, u, qbar, Dbar, mubar, info_fwd, info_adj, s);
+            // without device memory for the twin the pair runs in one lane
+            const dmg_status tw = twin_ready(c, s);
+            if (tw == DMG_OK) return solve_vjp_twin(c, q, w, u, qbar, Dbar, mubar, info_fwd, info_adj, s);
+            if (tw != DMG_ENOMEM) return tw;
+            c->err[0] = 0;
         }
         Level &l = c->L[0];
         // w goes to T3 on the side stream while the forward iterates

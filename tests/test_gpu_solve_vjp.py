@@ -147,3 +147,31 @@ def test_twin_lane_is_bitwise_one_lane(dmg, precision):
         assert torch.equal(a, b)
     for S in (A, B, F):
         S.close()
+
+
+def test_twin_falls_back_to_one_lane_without_memory(dmg):
+    # the twin's first allocation fails (injected): the pair runs in one lane,
+    # with the same results; a later call builds the twin
+    w = inputs.tissue(33, seed=116)
+    D, mu, q, wv = (T(w[k]) for k in ("D", "mu", "q", "w"))
+    ref = dmg.Solver(D, mu, w["h"], precision=1, twin_adjoint=0)
+    want = [torch.empty_like(q) for _ in range(4)]
+    assert dmg.dmg_solve_vjp(ref.ctx, q, wv, *want, n=ref.n) == dmg.DMG_OK
+    S = dmg.Solver(D, mu, w["h"], precision=1)
+    alone = dmg.dmg_device_bytes(S.ctx)
+    got = [torch.empty_like(q) for _ in range(4)]
+    dmg.dmg_debug_fail_alloc(1)
+    try:
+        st = dmg.dmg_solve_vjp(S.ctx, q, wv, *got, n=S.n)
+    finally:
+        dmg.dmg_debug_fail_alloc(0)
+    assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+    assert dmg.dmg_device_bytes(S.ctx) == alone   # no twin
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    assert dmg.dmg_solve_vjp(S.ctx, q, wv, *got, n=S.n) == dmg.DMG_OK
+    assert dmg.dmg_device_bytes(S.ctx) > alone    # the twin now exists
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    S.close()
+    ref.close()
