@@ -63,7 +63,7 @@ HALF_SWEEP_TRAFFIC = {"fp32": 208017152, "fp64": 664092672}
 # DRAM bytes per sample of one batched finest-level FP32 half-sweep at 129^3,
 # from an ncu capture of 8 samples, scaled by the sample count (None: the
 # kernel changed since the last capture)
-VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = None
+VI_HALF_SWEEP_TRAFFIC_PER_SAMPLE_129 = 28567808
 
 
 AUTOTUNE = [1]   # set from --autotune
