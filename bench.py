@@ -535,7 +535,11 @@ def run_2d(dmg, torch, args, world, local, peaks, peak_src):
         qb, Db, mb = torch.empty_like(u), torch.empty_like(u), torch.empty_like(u)
         stream = torch.cuda.current_stream(dev)
 
-        def step():
+        def step():   # one pair through dmg_solve_vjp, as the headline
+            assert dmg.dmg_solve_vjp(S.ctx, w["q"], w["w"], u, qb, Db, mb, None, None, stream,
+                                     n=S.n) == dmg.DMG_OK
+
+        def step_seq():   # the same pair as two calls (for the kernel timing)
             assert dmg.dmg_solve(S.ctx, w["q"], u, None, stream, n=S.n) == dmg.DMG_OK
             assert dmg.dmg_vjp(S.ctx, u, w["w"], 0, qb, Db, mb, None, stream, n=S.n) == dmg.DMG_OK
 
@@ -551,7 +555,7 @@ def run_2d(dmg, torch, args, world, local, peaks, peak_src):
             ev[k + 1].record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
-        pr = profiled_pass(dmg, torch, S, step, steps, dmg.DMG_KERNEL_SMOOTH, prec == "mixed", stream, dev)
+        pr = profiled_pass(dmg, torch, S, step_seq, steps, dmg.DMG_KERNEL_SMOOTH, prec == "mixed", stream, dev)
         nl, pms = pr["launches"], pr["total_ms"]
         S.close()
         total = max_over_ranks(world, ev[0].elapsed_time(ev[steps]))

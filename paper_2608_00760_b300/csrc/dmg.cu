@@ -482,7 +482,15 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
     ProfScope ps(c, DMG_KERNEL_SMOOTH, lev, sizeof(T) == 4, s);
     if (c->dim == 2) {
         return dispatch<T>(c, l, [&](auto cf) {
-            dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color, c->mask);
+            if constexpr (sizeof(T) == 4) {
+                constexpr bool H = decltype(cf)::harmonic;
+                const dim3 b = blk();
+                const dim3 gr(((l.g.nx - 2) / 4 + 1 + b.x - 1) / b.x, (l.g.ny - 2 + b.y - 1) / b.y, l.g.nb);
+                dmgk::k_smooth_half2_pair32<H><<<gr, b, 0, s>>>(l.g, l.u32, l.f32, cf, color, c->mask);
+            } else {
+                dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color,
+                                                                          c->mask);
+            }
             return check_launch(c, "smooth");
         });
     }

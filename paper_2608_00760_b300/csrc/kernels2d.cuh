@@ -89,6 +89,64 @@ __global__ void __launch_bounds__(256) k_smooth_half2(Geom g, T *__restrict__ u,
     u[p] = finish2(c, coupled_sum2(f[p], u, p, xm, g.sy, a), p, a);
 }
 
+// The FP32 half-sweep with two vertices per thread (elements m, m+1 of the
+// colour's half-row, as the 3D pair kernels): every operand is one 8-byte load
+// per pair (own Dh, f, mu; the y neighbours of u and Dh; two of the three x
+// neighbours in the other half) plus one 4-byte load. Each vertex repeats the
+// arithmetic of couplings2 / coupled_sum2 / diag2 / finish2 in their order, so
+// results are bit for bit those of k_smooth_half2<float>.
+template <bool HARM>
+__global__ void __launch_bounds__(256) k_smooth_half2_pair32(Geom g, float *__restrict__ u,
+                                                             const float *__restrict__ f, VertCoef<float, HARM> c,
+                                                             int color, const int *act) {
+    using V = VertCoef<float, HARM>;
+    const int smp = blockIdx.z;
+    if (inactive(act, smp)) return;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (j > g.ny - 2) return;
+    const int par = (color + j) & 1;   // parity of i for this colour in row j
+    const int m = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int i0 = 2 * m + par;
+    const bool v0 = i0 >= 1 && i0 <= g.nx - 2, v1 = i0 + 2 <= g.nx - 2;
+    if (!v0 && !v1) return;
+    const long long o = smp * g.sb;
+    u += o;
+    f += o;
+    const float *Dh = c.Dh + o, *mu = c.mu + o;
+    const int row = j * g.sy, sy = g.sy;
+    const int p = row + par * g.hx + m, q = row + (1 - par) * g.hx + m;
+    const int e = par ? q + 2 : q - 1;   // the third x neighbour
+    DMG_CHECK(smp < g.nb);
+    g.check(p - sy);
+    g.check(p + sy + 1);
+    g.check(e);
+    g.check(q + 1);
+    auto ld = [](const float *x) { return __ldg(reinterpret_cast<const float2 *>(x)); };
+    auto lu = [](const float *x) { return *reinterpret_cast<const float2 *>(x); };
+    const float2 d = ld(Dh + p), dq = ld(Dh + q), uq = lu(u + q);
+    const float de = __ldg(Dh + e), ue = u[e];
+    // x neighbours: par 0 (i = 2m): other half m-1, m | m, m+1; par 1 (i = 2m+1): m, m+1 | m+1, m+2
+    const float dxm0 = par ? dq.x : de, dxp0 = par ? dq.y : dq.x, dxm1 = par ? dq.y : dq.x, dxp1 = par ? de : dq.y;
+    const float uxm0 = par ? uq.x : ue, uxp0 = par ? uq.y : uq.x, uxm1 = par ? uq.y : uq.x, uxp1 = par ? ue : uq.y;
+    const float2 dym = ld(Dh + p - sy), dyp = ld(Dh + p + sy), uym = lu(u + p - sy), uyp = lu(u + p + sy);
+    const float2 ff = lu(f + p), mm = ld(mu + p);
+    auto update = [](float dv, float a0d, float a1d, float a2d, float a3d, float um, float up, float uym_,
+                     float uyp_, float fv, float muv) {
+        const float a0 = V::face(dv, a0d), a1 = V::face(dv, a1d), a2 = V::face(dv, a2d), a3 = V::face(dv, a3d);
+        float s0 = fmaf(a0, um, fv);
+        float s1 = a2 * uym_;
+        s0 = fmaf(a1, up, s0);
+        s1 = fmaf(a3, uyp_, s1);
+        const float s = s0 + s1;
+        return __fdividef(s, (a0 + a1) + ((a2 + a3) + muv));
+    };
+    const float r0 = update(d.x, dxm0, dxp0, dym.x, dyp.x, uxm0, uxp0, uym.x, uyp.x, ff.x, mm.x);
+    const float r1 = update(d.y, dxm1, dxp1, dym.y, dyp.y, uxm1, uxp1, uym.y, uyp.y, ff.y, mm.y);
+    if (v0 && v1) *reinterpret_cast<float2 *>(u + p) = make_float2(r0, r1);
+    else if (v0) u[p] = r0;
+    else u[p + 1] = r1;
+}
+
 // r = f - A u on interior vertices
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_residual2(Geom g, const T *__restrict__ u, const T *__restrict__ f, C c,
