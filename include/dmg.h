@@ -106,13 +106,16 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 reused within the process for the same device, precision,
  *                 grid, batch and face mean, and, if the environment variable
  *                 DMG_TUNE_CACHE names a file, read from and appended to it.
- *   split_prolong 0 (default): on 3D levels of the FP32 V-cycle, only the
- *                 corrected values the first post-smoothing half-sweep reads
- *                 are formed: inside that half-sweep on levels of fewer than
- *                 2^22 vertices (never stored), by a correction of the other
- *                 colour alone ahead of a plain half-sweep on larger ones;
- *                 1: the full prolongation, then the half-sweeps. All give
- *                 the same results bit for bit.
+ *   split_prolong 0 (default): only the corrected values the first
+ *                 post-smoothing half-sweep reads are formed: on 3D levels of
+ *                 the FP32 V-cycle inside that half-sweep on levels of fewer
+ *                 than 2^22 vertices (never stored), on larger ones and on 2D
+ *                 levels by a correction of the other colour alone ahead of
+ *                 a plain half-sweep (3D FP64 levels keep the full
+ *                 prolongation, whose shared interpolations cost fewer FP64
+ *                 operations); 1: the full
+ *                 prolongation, then the half-sweeps. All give the same
+ *                 results bit for bit.
  *   twin_adjoint  1 (default): dmg_solve_vjp runs the adjoint solve at the
  *                 same time as the forward one (it needs only w), on a second
  *                 context (the "twin": the same parameters and coefficient

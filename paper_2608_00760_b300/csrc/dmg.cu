@@ -241,7 +241,7 @@ inline dim3 grid_int(const Geom &g) {
 // k_update / k_to_f32: elements m, m+1 of one half-row per thread; pairs
 // 0 .. (nx - 2) / 4 cover the interior vertices of either parity
 inline dim3 grid_int_pair(const Geom &g) {
-    return dim3(2 * (((g.nx - 2) / 4 + 1 + 31) / 32), (g.ny - 2 + 7) / 8, g.nb * (g.nz - 2));
+    return dim3(2 * (((g.nx - 2) / 4 + 1 + 31) / 32), (g.ny - 2 + 7) / 8, g.nz == 1 ? g.nb : g.nb * (g.nz - 2));
 }
 inline dim3 grid_all(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb * g.nz); }
 // half-sweeps: x covers the (nx-1)/2 vertices of one colour in a row
@@ -542,6 +542,22 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
     Level &l = c->L[lev];
     Level cl = coarse_of(c, lev);
     ProfScope ps(c, DMG_KERNEL_RESTRICT, lev, sizeof(T) == 4, s);
+    if (c->dim == 2 && zero_colour >= 0) {
+        // the defect on one colour and its 9-point full weighting
+        const int nz = 1 - zero_colour;
+        TRY(dispatch<T>(c, l, [&](auto cf) {
+            dmgk::k_residual_colour2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz,
+                                                                          c->mask);
+            return check_launch(c, "residual_colour");
+        }));
+        if (nz == 0)
+            dmgk::k_restrict_colour2<T, 0><<<grid_int2(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
+                                                                             c->mask);
+        else
+            dmgk::k_restrict_colour2<T, 1><<<grid_int2(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
+                                                                             c->mask);
+        return check_launch(c, "restrict_colour");
+    }
     if (c->dim == 2) {   // full defect and 9-point full weighting
         TRY(dispatch<T>(c, l, [&](auto cf) {
             dmgk::k_residual2<T><<<grid_int2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), c->mask);
@@ -748,6 +764,18 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
     // after pre-smoothing the defect is zero on the colour updated last
     TRY(restrict_defect<T>(c, lev, npre > 0 ? 1 - pre_first : -1, s));
     TRY(vcycle<T>(c, lev + 1, transposed, s));
+    if (c->dim == 2 && npost > 0 && !c->p.split_prolong) {
+        // the correction on the colour the first post half-sweep reads
+        Level &l = c->L[lev];
+        Level cl = coarse_of(c, lev);
+        {
+            ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
+            dmgk::k_prolong_colour2<T><<<grid_half2(l.g), blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), 1 - postf,
+                                                                         c->mask);
+            TRY(check_launch(c, "prolong_colour"));
+        }
+        return smooth<T>(c, lev, postf, npost, s);
+    }
     if (sizeof(T) == 4 && c->dim == 3 && npost > 0 && !c->p.split_prolong) {
         if (split_prolong_level(c->L[lev])) {
             // the correction on the colour the first post half-sweep reads
@@ -1029,10 +1057,7 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
     TRY(norm2_async(c, l.f, 0, s));
     dmgk::k_mix_init<<<(c->nb + 127) / 128, 128, 0, s>>>(c->red, 0, c->ms, c->nb);
     TRY(check_launch(c, "mix_init"));
-    if (c->dim == 2)
-        dmgk::k_to_f32_2<<<grid_int2(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
-    else
-        dmgk::k_to_f32<<<grid_int_pair(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
+    dmgk::k_to_f32<<<grid_int_pair(l.g), blk(), 0, s>>>(l.g, l.f, c->ms, l.f32);
     TRY(check_launch(c, "to_f32"));
     TRY(finish_reduce(c, s));
     Progress P;
@@ -1044,10 +1069,7 @@ dmg_status iterate_mixed(dmg_ctx *c, bool transposed, dmg_info *info, cudaStream
         TRY(capture(c, G, [&](cudaStream_t cs) -> dmg_status {
             CUDA_TRY(c, cudaMemsetAsync(l.u32, 0, l.n * sizeof(float), cs));
             for (int ic = 0; ic < c->p.inner_cycles; ic++) TRY(vcycle<float>(c, 0, transposed, cs));
-            if (c->dim == 2)
-                dmgk::k_update2<<<grid_int2(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
-            else
-                dmgk::k_update<<<grid_int_pair(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
+            dmgk::k_update<<<grid_int_pair(l.g), blk(), 0, cs>>>(l.g, l.u, l.u32, c->ms, c->mask);
             TRY(check_launch(c, "update"));
             TRY(resid_norm_async(c, l.u, l.f, l.f32, 0, c->mask, cs));
             dmgk::k_mix_next<<<(c->nb + 127) / 128, 128, 0, cs>>>(c->red, 0, c->ms, c->nb, c->mask);

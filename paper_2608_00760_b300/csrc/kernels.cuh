@@ -1664,17 +1664,23 @@ __global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u
     f[p] -= v;
 }
 
-// Elementwise kernels on the interior of level 0: one thread takes elements m,
-// m+1 (m even) of one half-row, vertices i = 2m + par and 2m + 2 + par, as one
-// 16-byte (FP64) and one 8-byte (FP32) access; blockIdx.x = 2 * chunk + par.
+// Elementwise kernels on the interior of level 0 (3D, or 2D with nz = 1): one
+// thread takes elements m, m+1 (m even) of one half-row, vertices i = 2m + par
+// and 2m + 2 + par, as one 16-byte (FP64) and one 8-byte (FP32) access;
+// blockIdx.x = 2 * chunk + par.
 __device__ __forceinline__ bool interior_pair(const Geom &g, const int *act, long long &p, int &smp, bool &v0,
                                               bool &v1) {
     const int par = blockIdx.x & 1;
     const int m = 2 * (int)((blockIdx.x >> 1) * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k;
-    smp = zsplit(g, kInterior, k);
-    k += 1;
+    if (g.nz == 1) {   // 2D: one plane per sample, blockIdx.z = sample
+        smp = blockIdx.z;
+        k = 0;
+    } else {
+        smp = zsplit(g, kInterior, k);
+        k += 1;
+    }
     const int i0 = 2 * m + par;
     v0 = i0 >= 1 && i0 <= g.nx - 2;
     v1 = i0 + 2 <= g.nx - 2;

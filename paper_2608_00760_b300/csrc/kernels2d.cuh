@@ -223,6 +223,93 @@ __global__ void __launch_bounds__(256) k_prolong_add2(Geom gc, const T *__restri
     }
 }
 
+// After a half-sweep the defect vanishes on the colour it updated (as in 3D):
+// r = f - A u is formed on the other colour only (colour = (i + j) mod 2, one
+// vertex per thread as k_smooth_half2), and the restriction below reads only
+// that colour.
+template <class T, class C>
+__global__ void __launch_bounds__(256) k_residual_colour2(Geom g, const T *__restrict__ u, const T *__restrict__ f,
+                                                          C c, T *__restrict__ r, int color, const int *act) {
+    const int smp = blockIdx.z;
+    if (inactive(act, smp)) return;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int par = (color + j) & 1;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;
+    if (j > g.ny - 2 || i > g.nx - 2) return;
+    const long long o = smp * g.sb;
+    u += o;
+    f += o;
+    r += o;
+    c = c.shifted(o);
+    const long long p = g.pos(i, j, 0);
+    const int xm = g.xm(i);
+    DMG_CHECK(smp < g.nb);
+    g.check(p - g.sy);
+    g.check(p + g.sy);
+    g.check(p + xm);
+    g.check(p + xm + 1);
+    T a[4];
+    couplings2(c, p, xm, g.sy, a);
+    r[p] = coupled_sum2(fma(-diag2(c, p, a), u[p], f[p]), u, p, xm, g.sy, a);
+}
+
+// 9-point full weighting of a defect that lives on one colour: fine vertex
+// (2I+a, 2J+b) has colour (a+b) mod 2, so in row b either the centre (a = 0)
+// or the two sides (a = -1, +1) carry it (PAR: the colour of the defect).
+template <class T, int PAR>
+__global__ void __launch_bounds__(256) k_restrict_colour2(Geom gf, const T *__restrict__ r, Geom gc,
+                                                          T *__restrict__ fc, T *__restrict__ uc, const int *act) {
+    const int smp = blockIdx.z;
+    if (inactive(act, smp)) return;
+    const int I = vertex_i();
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    if (I < 1 || I > gc.nx - 2 || J > gc.ny - 2) return;
+    r += smp * gf.sb;
+    const long long pc = gc.pos(I, J, 0) + smp * gc.sb;
+    const long long p = gf.pos(2 * I, 2 * J, 0);
+    const int om = gf.xm(2 * I), op = gf.xp(2 * I);
+    gf.check(p - gf.sy + om);
+    gf.check(p + gf.sy + op);
+    gc.check(gc.pos(I, J, 0));
+    T s = T(0);
+#pragma unroll
+    for (int b = -1; b <= 1; b++) {
+        const long long q = p + b * gf.sy;
+        const T row = ((b & 1) == PAR) ? T(2) * r[q] : r[q + om] + r[q + op];
+        s += (b == 0 ? T(2) : T(1)) * row;
+    }
+    fc[pc] = s * T(1.0 / 16.0);
+    uc[pc] = T(0);
+}
+
+// u += P e on the vertices of one colour only (the values the half-sweep of the
+// other colour, which must follow, reads); each vertex gets the interpolation
+// of k_prolong_add2 in its order, so the level ends bit for bit where the full
+// correction and two half-sweeps end.
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong_colour2(Geom gc, const T *__restrict__ e, Geom gf,
+                                                         T *__restrict__ u, int color, const int *act) {
+    const int smp = blockIdx.z;
+    if (inactive(act, smp)) return;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int par = (color + j) & 1;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + 2 - par;
+    if (j > gf.ny - 2 || i > gf.nx - 2) return;
+    e += smp * gc.sb;
+    u += smp * gf.sb;
+    const int I = i >> 1, J = j >> 1, x = i & 1, y = j & 1;
+    gc.check(gc.pos(I + x, J + y, 0));
+    // the coarse values of the cell (I, J) that k_prolong_add2 reads for this vertex
+    const T c00 = e[gc.pos(I, J, 0)];
+    T row0 = c00, row1 = T(0);
+    if (y) row0 = T(0.5) * (c00 + e[gc.pos(I, J + 1, 0)]);
+    if (x) {
+        const T c01 = e[gc.pos(I + 1, J, 0)];
+        row1 = y ? T(0.5) * (c01 + e[gc.pos(I + 1, J + 1, 0)]) : c01;
+    }
+    u[gf.pos(i, j, 0)] += x ? T(0.5) * (row0 + row1) : row0;
+}
+
 // exact coarsest solve u = Ainv f on the (nx-2)(ny-2) interior unknowns (x fastest), one block per sample
 template <class T>
 __global__ void k_coarse_solve2(Geom g, const T *__restrict__ Ainv, int n, const T *__restrict__ f,
@@ -370,27 +457,6 @@ __global__ void __launch_bounds__(256) k_norm2_2d(Geom g, const double *__restri
     }
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// mixed precision: u += e32 2^e_cur (update) or y = x 2^-e_cur (to FP32) on interior vertices
-__global__ void __launch_bounds__(256) k_update2(Geom g, double *__restrict__ u, const float *__restrict__ e,
-                                                 const MixScalars *ms, const int *act) {
-    const int smp = blockIdx.z;
-    const int i = vertex_i();
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2 || inactive(act, smp)) return;
-    const long long p = g.pos(i, j, 0) + smp * g.sb;
-    u[p] += f32_to_f64_shift(e[p], ms[smp].e_cur);
-}
-
-__global__ void __launch_bounds__(256) k_to_f32_2(Geom g, const double *__restrict__ x, const MixScalars *ms,
-                                                  float *__restrict__ y) {
-    const int smp = blockIdx.z;
-    const int i = vertex_i();
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    if (i < 1 || i > g.nx - 2 || j > g.ny - 2) return;
-    const long long p = g.pos(i, j, 0) + smp * g.sb;
-    y[p] = f64_to_f32_shift(x[p], -ms[smp].e_cur);
 }
 
 // gradients of <w, u> from u and lam = A^{-1} w on every vertex (u, lam zero on the boundary):
