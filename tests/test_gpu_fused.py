@@ -1,4 +1,6 @@
-"""Prolongation fused into the first post-smoothing half-sweep (FP32 3D levels).
+"""Prolongation fused into the first post-smoothing half-sweep (FP32 3D levels),
+or, on large FP32 levels and in 2D, applied to the one colour that half-sweep
+reads.
 
 A red-black half-sweep never reads the old values of the colour it updates,
 and the next half-sweep overwrites the other colour without reading it, so the
@@ -103,3 +105,37 @@ def test_split_prolong_is_validated(dmg):
     w = inputs.tissue(seed=85, shape=(17, 17, 17))
     with pytest.raises(dmg.DMGError):
         dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=1, split_prolong=2)
+
+
+def test_one_colour_correction_on_large_levels(dmg):
+    # 2 x 129^3 (2 x 129 x 129 x 160 padded vertices >= 2^22): the finest level
+    # takes k_prolong_colour32 and a plain half-sweep; the results are those of
+    # the full prolongation
+    w = inputs.vi_batch(129, 2, seed=86)
+    out = {}
+    for split in (0, 1):
+        S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=1, split_prolong=split)
+        u = S.solve(T(w["q"]))
+        out[split] = (u,) + S.vjp(u, T(w["w"])) + (tuple(S.batch_info()[0]),)
+        S.close()
+    assert out[0][-1] == out[1][-1]
+    for a, b in zip(out[0][:-1], out[1][:-1]):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_2d_one_colour_correction_is_bitwise_the_full_one(dmg, precision, batch):
+    # 2D post-smoothing starts from a correction of the colour its first
+    # half-sweep reads (k_prolong_colour2); split_prolong = 1 applies the full
+    # bilinear correction first
+    ws = [inputs.tissue2d(seed=87 + b, shape=(65, 129)) for b in range(batch)]
+    st = lambda k: T(np.stack([x[k] for x in ws])) if batch > 1 else T(ws[0][k])
+    out = {}
+    for split in (0, 1):
+        S = dmg.Solver(st("D"), st("mu"), ws[0]["h"], dim=2, precision=precision, split_prolong=split)
+        u = S.solve(st("q"))
+        out[split] = (u,) + S.vjp(u, st("w"))
+        S.close()
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
