@@ -944,7 +944,7 @@ def main():
                          "beside the forward one")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
-    ap.add_argument("--serve-rate-low", type=float, default=100.0,
+    ap.add_argument("--serve-rate-low", type=float, default=60.0,
                     help="arrival rate of a second stream below capacity (0: skip it)")
     ap.add_argument("--no-setup", action="store_true", help="skip the setup-cost timings")
     ap.add_argument("--no-levels", action="store_true", help="skip the per-level kernel timings")
