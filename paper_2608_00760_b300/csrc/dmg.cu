@@ -148,6 +148,7 @@ struct dmg_ctx {
     double *mi_stage[2] = {nullptr, nullptr}, *mo_stage[2] = {nullptr, nullptr};
     cudaStream_t up = nullptr, down = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_ready_u[2] = {}, ev_ready[2] = {}, ev_out[2] = {};
+    cudaEvent_t ev_in_q[2] = {}, ev_used_w[2] = {}, ev_qb[2] = {};   // two-lane stream of pairs
     bool many_ready = false;
     // pyramid pool (dmg_setup_pyramid): slot b's finest level is top_of[b]; level l
     // holds samples [0, L[l].g.nb), of which [top_first[l], top_first[l] + top_count[l])
@@ -1670,7 +1671,8 @@ dmg_status many_alloc(dmg_ctx *c) {
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking));
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
     for (int b = 0; b < 2; b++)
-        for (cudaEvent_t *e : {&c->ev_in[b], &c->ev_used[b], &c->ev_ready_u[b], &c->ev_ready[b], &c->ev_out[b]})
+        for (cudaEvent_t *e : {&c->ev_in[b], &c->ev_used[b], &c->ev_ready_u[b], &c->ev_ready[b], &c->ev_out[b],
+                               &c->ev_in_q[b], &c->ev_used_w[b], &c->ev_qb[b]})
             CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     c->many_ready = true;
     return DMG_OK;
@@ -1706,8 +1708,10 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     auto upload = [&](int i) -> dmg_status {
         const int b = i % 2;
         CUDA_TRY(c, cudaStreamWaitEvent(c->up, c->ev_used[b], 0));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->up, c->ev_used_w[b], 0));
         if (!is_device_ptr(q[i]))
             CUDA_TRY(c, cudaMemcpyAsync(c->mi_stage[b], q[i], bytes, cudaMemcpyHostToDevice, c->up));
+        CUDA_TRY(c, cudaEventRecord(c->ev_in_q[b], c->up));   // the forward solve can start
         if (!is_device_ptr(w[i]))
             CUDA_TRY(c, cudaMemcpyAsync(c->mi_stage[b] + n, w[i], bytes, cudaMemcpyHostToDevice, c->up));
         CUDA_TRY(c, cudaEventRecord(c->ev_in[b], c->up));
@@ -1743,21 +1747,55 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
         const int b = i % 2;
         double *mo = c->mo_stage[b];
         // inputs of pair i
-        CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
         const double *qs = is_device_ptr(q[i]) ? q[i] : c->mi_stage[b];
         const double *ws = is_device_ptr(w[i]) ? w[i] : c->mi_stage[b] + n;
-        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, qs, l.f, 0);
-        TRY(check_launch(c, "gather"));
-        dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, ws, t ? t->L[0].f : c->T3, 0);
-        TRY(check_launch(c, "gather"));
-        CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
+        if (t) {
+            // two lanes: the forward solve starts once q is in, the adjoint one (in
+            // the twin, on its own stream) once w is
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_in_q[b], 0));
+            dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, qs, l.f, 0);
+            TRY(check_launch(c, "gather"));
+            CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_in[b], 0));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_aux, 0));   // pair i-1's lam copied out
+            dmgk::k_gather<<<quad_grid(g), blk(), 0, c->twin_s>>>(g, ws, t->L[0].f, 0);
+            TRY(check_launch(c, "gather"));
+            CUDA_TRY(c, cudaEventRecord(c->ev_used_w[b], c->twin_s));
+        } else {
+            CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
+            dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, qs, l.f, 0);
+            TRY(check_launch(c, "gather"));
+            dmgk::k_gather<<<quad_grid(g), blk(), 0, s>>>(g, ws, c->T3, 0);
+            TRY(check_launch(c, "gather"));
+            CUDA_TRY(c, cudaEventRecord(c->ev_used[b], s));
+        }
         if (i + 1 < npairs) TRY(upload(i + 1));   // overlaps this pair's iterations
         if (t) {
             // the adjoint solve in the twin beside the forward one (see solve_vjp_twin)
-            CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_used[b], 0));
             dmg_status st2 = DMG_OK;
             dmg_info *ia = info_adj ? info_adj + i : nullptr;
-            auto adjoint = [&]() { st2 = iterate(t, true, 0, ia, c->twin_s); };
+            double *const qb_i = out_at(qbar, i);
+            double *const mo_i = mo;
+            auto adjoint = [&]() {
+                st2 = iterate(t, true, 0, ia, c->twin_s);
+                if (st2 != DMG_OK && st2 != DMG_ENOCONV) return;
+                // qbar = lam leaves as soon as the adjoint solve ends (the forward one is
+                // longer), through its staging slot once pair i-2 has freed it
+                if (!qb_i) return;
+                cudaError_t e = cudaStreamWaitEvent(c->twin_s, c->ev_out[b], 0);
+                const bool dev = is_device_ptr(qb_i);
+                if (e == cudaSuccess) {
+                    dmgk::k_scatter<<<quad_grid(g), blk(), 0, c->twin_s>>>(g, t->L[0].u, dev ? qb_i : mo_i + n);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess && !dev) {
+                    e = cudaEventRecord(c->ev_qb[b], c->twin_s);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->down, c->ev_qb[b], 0);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(qb_i, mo_i + n, bytes, cudaMemcpyDeviceToHost, c->down);
+                }
+                if (e != cudaSuccess) st2 = fail(t, DMG_ECUDA, "read-out of qbar: %s", cudaGetErrorString(e));
+            };
             std::thread lane;
             bool threaded = true;
             try {
@@ -1788,7 +1826,7 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             CUDA_TRY(c, cudaEventRecord(c->ev_aux, s));
             cudaStream_t sd = c->side;
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_aux, 0));
-            double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *qb = out_at(qbar, i), *ud = out_at(u, i);
+            double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *ud = out_at(u, i);
             if (Db || mb) {
                 const double ih2 = 1.0 / (l.h * l.h);
                 ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, sd);
@@ -1805,14 +1843,12 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             // the staging slot of pair i-2 must have reached the host
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_out[b], 0));
             if (ud) TRY(put_on(c->U0, ud, mo, sd));
-            if (qb) TRY(put_on(c->T3, qb, mo + n, sd));
             if (Db) TRY(put_on(c->T1, Db, mo + 2 * n, sd));
             if (mb) TRY(put_on(c->T2, mb, mo + 3 * n, sd));
             CUDA_TRY(c, cudaEventRecord(c->ev_join, sd));   // U0, T3, T1, T2 free again
             CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], sd));
             CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready[b], 0));
             if (ud) TRY(fetch(mo, ud));   // overlap the next pair's iterations
-            if (qb) TRY(fetch(mo + n, qb));
             if (Db) TRY(fetch(mo + 2 * n, Db));
             if (mb) TRY(fetch(mo + 3 * n, mb));
             CUDA_TRY(c, cudaEventRecord(c->ev_out[b], c->down));
@@ -2544,7 +2580,8 @@ dmg_status destroy_impl(dmg_ctx *c) {
             cudaStreamDestroy(st);
         }
     for (int b = 0; b < 2; b++)
-        for (cudaEvent_t e : {c->ev_in[b], c->ev_used[b], c->ev_ready_u[b], c->ev_ready[b], c->ev_out[b]})
+        for (cudaEvent_t e : {c->ev_in[b], c->ev_used[b], c->ev_ready_u[b], c->ev_ready[b], c->ev_out[b],
+                              c->ev_in_q[b], c->ev_used_w[b], c->ev_qb[b]})
             if (e) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
