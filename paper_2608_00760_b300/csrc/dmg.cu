@@ -273,6 +273,31 @@ dmg_status check_launch(dmg_ctx *c, const char *what) {
     return DMG_OK;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while its predecessor in the stream drains, and waits for it in pdl_wait()
+// before its first read (every kernel launched this way calls it first).
+template <class... P, class... A>
+dmg_status launch_pdl(dmg_ctx *c, const char *what, void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    c->launches++;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DMG_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    }
+    return DMG_OK;
+}
+
 // Host-side fault injection for tests: when > 0, the allocation with this
 // ordinal (counting from the next one, process-wide) fails as if the device
 // were out of memory.
@@ -500,12 +525,10 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
             constexpr bool H = decltype(cf)::harmonic;
             const dim3 b = c->tb[1][lev];
             if (c->nb == 1)
-                dmgk::k_smooth_half32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                 nullptr);
-            else
-                dmgk::k_smooth_half32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, color,
-                                                                                c->mask);
-            return check_launch(c, "smooth");
+                return launch_pdl(c, "smooth", dmgk::k_smooth_half32<H, false>, grid_pair(l.g, b), b, 0, s, l.g,
+                                  l.u32, (const float *)l.f32, cf, color, (const int *)nullptr);
+            return launch_pdl(c, "smooth", dmgk::k_smooth_half32<H, true>, grid_pair(l.g, b), b, 0, s, l.g, l.u32,
+                              (const float *)l.f32, cf, color, (const int *)c->mask);
         });
     } else {
         const dim3 b = c->tb[0][lev];
@@ -574,12 +597,12 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
                 constexpr bool H = decltype(cf)::harmonic;
                 const dim3 b = c->tb[1][lev];
                 if (c->nb == 1)
-                    dmgk::k_residual_colour32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
-                                                                                         l.r32, nz, nullptr);
-                else
-                    dmgk::k_residual_colour32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf,
-                                                                                        l.r32, nz, c->mask);
-                return check_launch(c, "residual_colour");
+                    return launch_pdl(c, "residual_colour", dmgk::k_residual_colour32<H, false>, grid_pair(l.g, b), b,
+                                      0, s, l.g, (const float *)l.u32, (const float *)l.f32, cf, l.r32, nz,
+                                      (const int *)nullptr);
+                return launch_pdl(c, "residual_colour", dmgk::k_residual_colour32<H, true>, grid_pair(l.g, b), b, 0,
+                                  s, l.g, (const float *)l.u32, (const float *)l.f32, cf, l.r32, nz,
+                                  (const int *)c->mask);
             }));
         } else {
             const dim3 b = c->tb[0][lev];
@@ -589,12 +612,11 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
         }
         // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
         if (nz == 0)
-            dmgk::k_restrict_colour<T, 0><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
-                                                                           c->mask);
+            TRY(launch_pdl(c, "restrict_colour", dmgk::k_restrict_colour<T, 0>, grid_int(cl.g), blk(), 0, s, l.g,
+                           (const T *)R<T>(l), cl.g, F<T>(cl), U<T>(cl), (const int *)c->mask));
         else
-            dmgk::k_restrict_colour<T, 1><<<grid_int(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
-                                                                           c->mask);
-        TRY(check_launch(c, "restrict_colour"));
+            TRY(launch_pdl(c, "restrict_colour", dmgk::k_restrict_colour<T, 1>, grid_int(cl.g), blk(), 0, s, l.g,
+                           (const T *)R<T>(l), cl.g, F<T>(cl), U<T>(cl), (const int *)c->mask));
     } else {
         TRY(dispatch<T>(c, l, [&](auto cf) {
             dmgk::k_residual<T><<<grid_int(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), c->mask);
@@ -620,10 +642,10 @@ dmg_status prolong_colour32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, 1, s);
     const dim3 b = c->tb[1][lev];
     if (c->nb == 1)
-        dmgk::k_prolong_colour32<false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, color, nullptr);
-    else
-        dmgk::k_prolong_colour32<true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, cl.g, cl.u32, color, c->mask);
-    return check_launch(c, "prolong_colour");
+        return launch_pdl(c, "prolong_colour", dmgk::k_prolong_colour32<false>, grid_pair(l.g, b), b, 0, s, l.g,
+                          l.u32, cl.g, (const float *)cl.u32, color, (const int *)nullptr);
+    return launch_pdl(c, "prolong_colour", dmgk::k_prolong_colour32<true>, grid_pair(l.g, b), b, 0, s, l.g, l.u32,
+                      cl.g, (const float *)cl.u32, color, (const int *)c->mask);
 }
 
 // u_lev += P u_{lev+1}, then the half-sweep of colour `color` on lev, in one
@@ -638,12 +660,11 @@ dmg_status prolong_smooth32(dmg_ctx *c, int lev, int color, cudaStream_t s) {
         constexpr bool H = decltype(cf)::harmonic;
         const dim3 b = c->tb[1][lev];
         if (c->nb == 1)
-            dmgk::k_prolong_smooth32<H, false><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
-                                                                                color, nullptr);
-        else
-            dmgk::k_prolong_smooth32<H, true><<<grid_pair(l.g, b), b, 0, s>>>(l.g, l.u32, l.f32, cf, cl.g, cl.u32,
-                                                                               color, c->mask);
-        return check_launch(c, "prolong_smooth");
+            return launch_pdl(c, "prolong_smooth", dmgk::k_prolong_smooth32<H, false>, grid_pair(l.g, b), b, 0, s,
+                              l.g, l.u32, (const float *)l.f32, cf, cl.g, (const float *)cl.u32, color,
+                              (const int *)nullptr);
+        return launch_pdl(c, "prolong_smooth", dmgk::k_prolong_smooth32<H, true>, grid_pair(l.g, b), b, 0, s, l.g,
+                          l.u32, (const float *)l.f32, cf, cl.g, (const float *)cl.u32, color, (const int *)c->mask);
     });
 }
 
@@ -730,8 +751,8 @@ dmg_status launch_tail(dmg_ctx *c, int npre, int npost, int pre_first, int post_
         a.pre_first = pre_first;
         a.post_first = post_first;
         a.load_u = l0 == 0;   // the V-cycle of the finest level continues from the current iterate
-        dmgk::k_vcycle_tail<T, C><<<c->nb, 1024, c->tail_smem[t], s>>>(a);
-        return check_launch(c, "vcycle_tail");
+        return launch_pdl(c, "vcycle_tail", dmgk::k_vcycle_tail<T, C>, dim3(c->nb), dim3(1024), c->tail_smem[t], s,
+                          a);
     });
 }
 

@@ -78,6 +78,13 @@ __device__ __forceinline__ int zsplit(const Geom &g, int which, int &plane) {
     return smp;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may start while the kernel before it in the
+// stream drains; it waits here, before its first read, until that kernel has
+// completed and its writes are visible. Without the attribute this returns at
+// once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool inactive(const int *act, int smp) { return act != nullptr && __ldg(act + smp) == 0; }
 
 // Thread mapping shared by the per-vertex kernels: blockIdx.x = 2*b + parity,
@@ -481,6 +488,7 @@ __device__ __forceinline__ void pair_store32(float *x, int p, bool v0, bool v1, 
 template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_smooth_half32(Geom g, float *__restrict__ u, const float *__restrict__ f,
                                                        VertCoef<float, HARM> c, int color, const int *act) {
+    pdl_wait();
     PairAt A;
     if (!colour_pair32<BATCH>(g, color, act, A)) return;
     u += A.base;
@@ -496,6 +504,7 @@ template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_residual_colour32(Geom g, const float *__restrict__ u,
                                                            const float *__restrict__ f, VertCoef<float, HARM> c,
                                                            float *__restrict__ r, int color, const int *act) {
+    pdl_wait();
     PairAt A;
     if (!colour_pair32<BATCH>(g, color, act, A)) return;
     u += A.base;
@@ -637,6 +646,7 @@ template <bool HARM, bool BATCH>
 __global__ void __launch_bounds__(256) k_prolong_smooth32(Geom g, float *__restrict__ u, const float *__restrict__ f,
                                                           VertCoef<float, HARM> c, Geom gc,
                                                           const float *__restrict__ e, int color, const int *act) {
+    pdl_wait();
     PairAt A;
     if (!colour_pair32<BATCH>(g, color, act, A)) return;
     u += A.base;
@@ -702,6 +712,7 @@ __device__ __forceinline__ void prolong_colour_pair32(float *u, const Geom &gc, 
 template <bool BATCH>
 __global__ void __launch_bounds__(256) k_prolong_colour32(Geom g, float *__restrict__ u, Geom gc,
                                                           const float *__restrict__ e, int color, const int *act) {
+    pdl_wait();
     PairAt A;
     if (!colour_pair32<BATCH>(g, color, act, A)) return;
     u += A.base;
@@ -725,6 +736,7 @@ __global__ void __launch_bounds__(256) k_prolong_colour32(Geom g, float *__restr
 template <class T, int PAR>
 __global__ void __launch_bounds__(256) k_restrict_colour(Geom gf, const T *__restrict__ r, Geom gc,
                                                          T *__restrict__ fc, T *__restrict__ uc, const int *act) {
+    pdl_wait();
     const int I = vertex_i();
     const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int K;
@@ -1049,6 +1061,7 @@ __global__ void __launch_bounds__(1024) k_tail_image(const __grid_constant__ Tai
 // one block per sample
 template <class T, class C>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(const __grid_constant__ TailArgs<T, C> a) {
+    pdl_wait();
     constexpr bool INV = TailInv<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TailLv sL[kTailMaxLevels];
