@@ -512,12 +512,12 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
                 constexpr bool H = decltype(cf)::harmonic;
                 const dim3 b = blk();
                 const dim3 gr(((l.g.nx - 2) / 4 + 1 + b.x - 1) / b.x, (l.g.ny - 2 + b.y - 1) / b.y, l.g.nb);
-                dmgk::k_smooth_half2_pair32<H><<<gr, b, 0, s>>>(l.g, l.u32, l.f32, cf, color, c->mask);
+                return launch_pdl(c, "smooth", dmgk::k_smooth_half2_pair32<H>, gr, b, 0, s, l.g, l.u32,
+                                  (const float *)l.f32, cf, color, (const int *)c->mask);
             } else {
-                dmgk::k_smooth_half2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, color,
-                                                                          c->mask);
+                return launch_pdl(c, "smooth", dmgk::k_smooth_half2<T, decltype(cf)>, grid_half2(l.g), blk(), 0, s,
+                                  l.g, U<T>(l), (const T *)F<T>(l), cf, color, (const int *)c->mask);
             }
-            return check_launch(c, "smooth");
         });
     }
     if constexpr (sizeof(T) == 4) {
@@ -532,8 +532,8 @@ dmg_status half_sweep(dmg_ctx *c, int lev, int color, cudaStream_t s) {
         });
     } else {
         const dim3 b = c->tb[0][lev];
-        dmgk::k_smooth_half<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), color, c->mask);
-        return check_launch(c, "smooth");
+        return launch_pdl(c, "smooth", dmgk::k_smooth_half<T, dmgk::FaceCoef<T>>, grid_half(l.g, b), b, 0, s, l.g,
+                          U<T>(l), (const T *)F<T>(l), coef64(l), color, (const int *)c->mask);
     }
 }
 
@@ -570,17 +570,15 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
         // the defect on one colour and its 9-point full weighting
         const int nz = 1 - zero_colour;
         TRY(dispatch<T>(c, l, [&](auto cf) {
-            dmgk::k_residual_colour2<T><<<grid_half2(l.g), blk(), 0, s>>>(l.g, U<T>(l), F<T>(l), cf, R<T>(l), nz,
-                                                                          c->mask);
-            return check_launch(c, "residual_colour");
+            return launch_pdl(c, "residual_colour", dmgk::k_residual_colour2<T, decltype(cf)>, grid_half2(l.g), blk(),
+                              0, s, l.g, (const T *)U<T>(l), (const T *)F<T>(l), cf, R<T>(l), nz,
+                              (const int *)c->mask);
         }));
         if (nz == 0)
-            dmgk::k_restrict_colour2<T, 0><<<grid_int2(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
-                                                                             c->mask);
-        else
-            dmgk::k_restrict_colour2<T, 1><<<grid_int2(cl.g), blk(), 0, s>>>(l.g, R<T>(l), cl.g, F<T>(cl), U<T>(cl),
-                                                                             c->mask);
-        return check_launch(c, "restrict_colour");
+            return launch_pdl(c, "restrict_colour", dmgk::k_restrict_colour2<T, 0>, grid_int2(cl.g), blk(), 0, s, l.g,
+                              (const T *)R<T>(l), cl.g, F<T>(cl), U<T>(cl), (const int *)c->mask);
+        return launch_pdl(c, "restrict_colour", dmgk::k_restrict_colour2<T, 1>, grid_int2(cl.g), blk(), 0, s, l.g,
+                          (const T *)R<T>(l), cl.g, F<T>(cl), U<T>(cl), (const int *)c->mask);
     }
     if (c->dim == 2) {   // full defect and 9-point full weighting
         TRY(dispatch<T>(c, l, [&](auto cf) {
@@ -606,9 +604,9 @@ dmg_status restrict_defect(dmg_ctx *c, int lev, int zero_colour, cudaStream_t s)
             }));
         } else {
             const dim3 b = c->tb[0][lev];
-            dmgk::k_residual_colour<T><<<grid_half(l.g, b), b, 0, s>>>(l.g, U<T>(l), F<T>(l), coef64(l), R<T>(l), nz,
-                                                                       c->mask);
-            TRY(check_launch(c, "residual_colour"));
+            TRY(launch_pdl(c, "residual_colour", dmgk::k_residual_colour<T, dmgk::FaceCoef<T>>, grid_half(l.g, b), b,
+                           0, s, l.g, (const T *)U<T>(l), (const T *)F<T>(l), coef64(l), R<T>(l), nz,
+                           (const int *)c->mask));
         }
         // fine vertex 2I+offset has colour parity(offset); the defect lives on colour nz
         if (nz == 0)
@@ -675,12 +673,12 @@ dmg_status prolong(dmg_ctx *c, int lev, cudaStream_t s) {
     ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
     if (c->dim == 2) {
         dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, l.g.nb);   // coarse cells
-        dmgk::k_prolong_add2<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
-        return check_launch(c, "prolong");
+        return launch_pdl(c, "prolong", dmgk::k_prolong_add2<T>, grid, blk(), 0, s, cl.g, (const T *)U<T>(cl), l.g,
+                          U<T>(l), (const int *)c->mask);
     }
     dim3 grid((cl.g.nx - 1 + 31) / 32, (cl.g.ny - 1 + 7) / 8, l.g.nb * (cl.g.nz - 1));   // coarse cells
-    dmgk::k_prolong_add<T><<<grid, blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), c->mask);
-    return check_launch(c, "prolong");
+    return launch_pdl(c, "prolong", dmgk::k_prolong_add<T>, grid, blk(), 0, s, cl.g, (const T *)U<T>(cl), l.g,
+                      U<T>(l), (const int *)c->mask);
 }
 
 
@@ -792,9 +790,8 @@ dmg_status vcycle(dmg_ctx *c, int lev, bool transposed, cudaStream_t s) {
         Level cl = coarse_of(c, lev);
         {
             ProfScope ps(c, DMG_KERNEL_PROLONG, lev, sizeof(T) == 4, s);
-            dmgk::k_prolong_colour2<T><<<grid_half2(l.g), blk(), 0, s>>>(cl.g, U<T>(cl), l.g, U<T>(l), 1 - postf,
-                                                                         c->mask);
-            TRY(check_launch(c, "prolong_colour"));
+            TRY(launch_pdl(c, "prolong_colour", dmgk::k_prolong_colour2<T>, grid_half2(l.g), blk(), 0, s, cl.g,
+                           (const T *)U<T>(cl), l.g, U<T>(l), 1 - postf, (const int *)c->mask));
         }
         return smooth<T>(c, lev, postf, npost, s);
     }

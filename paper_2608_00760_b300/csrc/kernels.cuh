@@ -286,6 +286,7 @@ __device__ __forceinline__ void prolong_cell(const Geom &gc, const T *e, const G
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_smooth_half(Geom g, T *__restrict__ u, const T *__restrict__ f, C c,
                                                      int color, const int *act) {
+    pdl_wait();
     int k;
     const int smp = zsplit(g, kInterior, k);
     k += 1;
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, const T *__restrict__
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_residual_colour(Geom g, const T *__restrict__ u, const T *__restrict__ f,
                                                          C c, T *__restrict__ r, int color, const int *act) {
+    pdl_wait();
     int k;
     const int smp = zsplit(g, kInterior, k);
     k += 1;
@@ -769,6 +771,7 @@ __global__ void __launch_bounds__(256) k_restrict_colour(Geom gf, const T *__res
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong_add(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u,
                                                      const int *act) {
+    pdl_wait();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     int K;

@@ -67,6 +67,7 @@ __device__ __forceinline__ T coupled_sum2(T s, const T *u, long long p, int xm, 
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_smooth_half2(Geom g, T *__restrict__ u, const T *__restrict__ f, C c,
                                                       int color, const int *act) {
+    pdl_wait();
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -99,6 +100,7 @@ template <bool HARM>
 __global__ void __launch_bounds__(256) k_smooth_half2_pair32(Geom g, float *__restrict__ u,
                                                              const float *__restrict__ f, VertCoef<float, HARM> c,
                                                              int color, const int *act) {
+    pdl_wait();
     using V = VertCoef<float, HARM>;
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(256) k_restrict2(Geom gf, const T *__restrict_
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong_add2(Geom gc, const T *__restrict__ e, Geom gf, T *__restrict__ u,
                                                       const int *act) {
+    pdl_wait();
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(256) k_prolong_add2(Geom gc, const T *__restri
 template <class T, class C>
 __global__ void __launch_bounds__(256) k_residual_colour2(Geom g, const T *__restrict__ u, const T *__restrict__ f,
                                                           C c, T *__restrict__ r, int color, const int *act) {
+    pdl_wait();
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -259,6 +263,7 @@ __global__ void __launch_bounds__(256) k_residual_colour2(Geom g, const T *__res
 template <class T, int PAR>
 __global__ void __launch_bounds__(256) k_restrict_colour2(Geom gf, const T *__restrict__ r, Geom gc,
                                                           T *__restrict__ fc, T *__restrict__ uc, const int *act) {
+    pdl_wait();
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
     const int I = vertex_i();
@@ -289,6 +294,7 @@ __global__ void __launch_bounds__(256) k_restrict_colour2(Geom gf, const T *__re
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong_colour2(Geom gc, const T *__restrict__ e, Geom gf,
                                                          T *__restrict__ u, int color, const int *act) {
+    pdl_wait();
     const int smp = blockIdx.z;
     if (inactive(act, smp)) return;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
