@@ -84,7 +84,8 @@ def test_batch_plane_split_is_exact_division(tmp_path):
     dev = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "kernels.cuh")).read()
     host = open(os.path.join(ROOT, "paper_2608_00760_b300", "csrc", "dmg.cu")).read()
     code = "\n".join([_extract_struct(dev, "Geom"), "enum { kInterior = 0, kCells = 1, kAll = 2 };",
-                      _extract_device_function(host, "make_geom"), _extract_device_function(dev, "zsplit")])
+                      _extract_device_function(host, "half_row_pitch"), _extract_device_function(host, "make_geom"),
+                      _extract_device_function(dev, "zsplit")])
     assert "Geom make_geom(int nx, int ny, int nz, int nb)" in code
     tmpl = open(os.path.join(ROOT, "tests", "host", "zsplit_check.cpp")).read()
     cpp = tmp_path / "zsplit.cpp"
