@@ -288,11 +288,17 @@ dmg_status dmg_response_vjp(dmg_ctx *ctx, const double *u, const double *rbar, d
  * dmg_solve_vjp -- dmg_solve followed by dmg_vjp (converged adjoint) in one
  * call: u = S(q) (Eq. 2), then (qbar, Dbar, mubar) of <w, u> through the
  * transposed V-cycle (Sec. 2.4, Eq. 18). Fusing the two calls has no
- * counterpart in the paper; it exists to overlap host transfers. The forward solution
- * stays on the device for the gradients, and host transfers run on a second
- * stream where they overlap the iterations: w is uploaded during the forward
- * solve, u is read out during the adjoint solve, qbar during the gradient
- * kernel. Results are bit for bit those of the two calls. u, qbar, Dbar,
+ * counterpart in the paper; it exists to run the two solves side by side and
+ * to overlap host transfers. The adjoint solve needs w alone, so with
+ * twin_adjoint = 1 (the default) it runs in the context's twin (created by the
+ * first call: same parameters and hierarchy, own iteration state) on its own
+ * stream and on a host thread the call starts and joins, while the forward
+ * solve runs here; qbar is read out as soon as the adjoint solve ends. With
+ * twin_adjoint = 0 the two solves run one after the other, w is uploaded
+ * during the forward solve, u read out during the adjoint solve and qbar
+ * during the gradient kernel. The forward solution stays on the device for
+ * the gradients either way. The call waits for its work on `stream` before it
+ * returns. Results are bit for bit those of the two calls. u, qbar, Dbar,
  * mubar may each be NULL; info_fwd / info_adj report the two iterations.
  * Returns the first non-OK status of the two (DMG_ENOCONV still writes every
  * output).
