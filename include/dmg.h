@@ -321,6 +321,9 @@ dmg_status dmg_solve_vjp(dmg_ctx *ctx, const double *q, const double *w, double 
  *   u, qbar, Dbar, mubar arrays of npairs output pointers, or NULL (that output
  *                        is skipped for every pair); an entry may be NULL.
  *   info_fwd, info_adj   arrays of npairs reports, or NULL.
+ * With twin_adjoint = 1 each pair's adjoint solve runs in the twin beside its
+ * forward solve (as in dmg_solve_vjp), and its gradients and read-out run on a
+ * side stream while the next pair's solves start.
  * Host outputs are complete when the call returns (it synchronises). Results
  * are bit for bit those of dmg_solve_vjp on each pair. The first call
  * allocates the staging buffers (12 fields of the level-0 size) and two
