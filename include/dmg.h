@@ -123,9 +123,13 @@ enum { DMG_COARSEN_FULL_WEIGHTING = 0, DMG_COARSEN_INJECTION = 1 };
  *                 first dmg_solve_vjp call creates and dmg_set_coefficients
  *                 keeps in step; it doubles the device memory
  *                 (dmg_device_bytes counts it); when that memory cannot be
- *                 had the pair runs in one lane. Results are bit for bit those
- *                 of running the two solves one after the other. 0: one after
- *                 the other in this context.
+ *                 had the pair runs in one lane. The forward solve (the longer
+ *                 one) is queued on a stream of the device's highest priority
+ *                 and the adjoint one on a stream of the lowest, so that the
+ *                 forward kernels take the SMs first where both lanes have
+ *                 blocks waiting. Results are bit for bit those of running
+ *                 the two solves one after the other. 0: one after the other
+ *                 in this context.
  */
 typedef struct {
     int nx, ny, nz;

@@ -139,7 +139,9 @@ struct dmg_ctx {
     double *stage2 = nullptr;         // a second one, for transfers on the side stream
     cudaStream_t side = nullptr;      // overlaps host transfers with the iteration on the caller's stream
     dmg_ctx *twin = nullptr;          // dmg_solve_vjp's adjoint lane (twin_adjoint), created on first use
-    cudaStream_t twin_s = nullptr;    // the stream the twin iterates on
+    cudaStream_t twin_s = nullptr;    // the stream the twin iterates on (lowest priority)
+    cudaStream_t lead_s = nullptr;    // the forward solve of a two-lane pair (highest priority)
+    cudaEvent_t ev_lead = nullptr;
     cudaEvent_t ev_twin = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_aux = nullptr;
     // dmg_solve_vjp_many (allocated on first use): two input staging buffers
@@ -1751,15 +1753,22 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             CUDA_TRY(c, cudaMemcpyAsync(dst, stage_slot, bytes, cudaMemcpyDeviceToHost, c->down));
         return DMG_OK;
     };
+    const cudaStream_t caller = s;
     auto abort_all = [&](dmg_status st) {
         cudaStreamSynchronize(c->side);
         cudaStreamSynchronize(c->up);
         cudaStreamSynchronize(c->down);
+        if (t) cudaStreamSynchronize(c->lead_s);
         return st;
     };
     dmg_status worst = DMG_OK;
     CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));   // the uploads start after the caller's earlier work
     CUDA_TRY(c, cudaStreamWaitEvent(c->up, c->ev_fork, 0));
+    if (t) {
+        // with two lanes the forward solves run on the high-priority stream
+        CUDA_TRY(c, cudaStreamWaitEvent(c->lead_s, c->ev_fork, 0));
+        s = c->lead_s;
+    }
     TRY(upload(0));
     for (int i = 0; i < npairs; i++) {
         const int b = i % 2;
@@ -1915,7 +1924,11 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
     CUDA_TRY(c, cudaStreamSynchronize(c->side));
     CUDA_TRY(c, cudaStreamSynchronize(c->up));
     CUDA_TRY(c, cudaStreamSynchronize(c->down));
-    TRY(end_call(c, s));
+    if (t) {
+        CUDA_TRY(c, cudaEventRecord(c->ev_lead, c->lead_s));
+        CUDA_TRY(c, cudaStreamWaitEvent(caller, c->ev_lead, 0));
+    }
+    TRY(end_call(c, caller));
     return worst;
 }
 
@@ -2023,8 +2036,14 @@ dmg_status twin_ready(dmg_ctx *c, cudaStream_t s) {
     }
     if (st == DMG_OK) {
         memcpy(t->tb, c->tb, sizeof(c->tb));
-        if (cudaStreamCreateWithFlags(&c->twin_s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_twin, cudaEventDisableTiming) != cudaSuccess) {
+        // the forward solve is the longer lane: its kernels go first where both lanes
+        // have blocks waiting, and the adjoint lane fills the rest of the GPU
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->twin_s, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->lead_s, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_twin, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_lead, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             st = fail(c, DMG_ECUDA, "twin context: stream or event creation failed");
         }
@@ -2047,8 +2066,9 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
                           double *mubar, dmg_info *info_fwd, dmg_info *info_adj, cudaStream_t s) {
     dmg_ctx *t = c->twin;
     Level &l = c->L[0];
-    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));   // the adjoint lane starts after the caller's earlier work
+    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));   // both lanes start after the caller's earlier work
     CUDA_TRY(c, cudaStreamWaitEvent(c->twin_s, c->ev_fork, 0));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->lead_s, c->ev_fork, 0));
     dmg_status st2 = DMG_OK;
     auto adjoint = [&]() {
         st2 = stage_in(t, w, t->L[0].f, false, c->twin_s);
@@ -2073,17 +2093,20 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
     } catch (...) {
         threaded = false;   // no thread: the adjoint runs after the forward solve
     }
-    dmg_status st = stage_in(c, q, l.f, false, s);
-    if (st == DMG_OK) st = iterate(c, false, c->p.fixed_cycles, info_fwd, s);
+    dmg_status st = stage_in(c, q, l.f, false, c->lead_s);
+    if (st == DMG_OK) st = iterate(c, false, c->p.fixed_cycles, info_fwd, c->lead_s);
     if (threaded) lane.join();
     else adjoint();
+    if (cudaEventRecord(c->ev_lead, c->lead_s) == cudaSuccess) cudaStreamWaitEvent(s, c->ev_lead, 0);
     if (st2 != DMG_OK && st2 != DMG_ENOCONV) {
         cudaStreamSynchronize(c->twin_s);
+        cudaStreamSynchronize(c->lead_s);
         cudaStreamSynchronize(s);
         return fail(c, st2, "adjoint solve: %s", t->err);
     }
     if (st != DMG_OK && st != DMG_ENOCONV) {
         cudaStreamSynchronize(c->twin_s);
+        cudaStreamSynchronize(c->lead_s);
         return st;
     }
     if (st == DMG_OK && st2 == DMG_ENOCONV) fail(c, st2, "adjoint solve: %s", t->err);
@@ -2585,6 +2608,11 @@ dmg_status destroy_impl(dmg_ctx *c) {
         cudaStreamDestroy(c->twin_s);
     }
     if (c->ev_twin) cudaEventDestroy(c->ev_twin);
+    if (c->lead_s) {
+        cudaStreamSynchronize(c->lead_s);
+        cudaStreamDestroy(c->lead_s);
+    }
+    if (c->ev_lead) cudaEventDestroy(c->ev_lead);
     if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     graphs_reset(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
