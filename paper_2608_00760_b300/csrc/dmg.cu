@@ -255,6 +255,23 @@ inline dim3 grid_half(const Geom &g) {
 inline dim3 grid_half2(const Geom &g) { return dim3(((g.nx - 1) / 2 + 31) / 32, (g.ny - 2 + 7) / 8, g.nb); }
 inline dim3 grid_int2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nb); }
 inline dim3 grid_all2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb); }
+
+// Dbar and mubar of <w, u> from u and lam on a 3D level, in the level's
+// layout: the tiled kernel for the arithmetic face mean (bitwise k_grad, fewer
+// FP64 operations), k_grad for the harmonic one. dnat / mnat: that output is
+// written in the natural layout (tiled kernel only).
+inline void launch_grad(cudaStream_t s, const Geom &g, const double *u, const double *lam, const double *D,
+                        double ih2, bool harm, double *Dbar, double *mubar, bool dnat = false, bool mnat = false) {
+    if (harm) {
+        dmgk::k_grad<<<grid_all(g), blk(), 0, s>>>(g, u, lam, D, ih2, 1, Dbar, mubar);
+        return;
+    }
+    const int nzb = (g.nz + dmgk::kGradTZ - 1) / dmgk::kGradTZ;
+    const dim3 grid((g.nx + dmgk::kGradTX - 1) / dmgk::kGradTX, (g.ny + dmgk::kGradTY - 1) / dmgk::kGradTY,
+                    g.nb * nzb);
+    dmgk::k_grad_am<<<grid, dim3(dmgk::kGradTX, dmgk::kGradTY, dmgk::kGradTZ), 0, s>>>(g, u, lam, nzb, ih2, Dbar,
+                                                                                          dnat, mubar, mnat);
+}
 // the same with a tuned block shape b (b.x threads along the half-row, b.y rows)
 inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
@@ -469,6 +486,30 @@ dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s,
     dmgk::k_scatter<<<quad_grid(g), blk(), 0, s>>>(g, src, st);
     TRY(check_launch(c, "scatter"));
     CUDA_TRY(c, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyDeviceToHost, s));
+    return DMG_OK;
+}
+
+// Dbar and mubar of <w, u> from level-0 u and lam into the caller's arrays
+// (either may be NULL): an array on the device is written directly by the
+// tiled kernel (3D, arithmetic face mean), any other through T1 / T2 and
+// stage_out.
+dmg_status grad_out(dmg_ctx *c, const double *u, const double *lam, double *Dbar, double *mubar, cudaStream_t s) {
+    const Level &l = c->L[0];
+    const double ih2 = 1.0 / (l.h * l.h);
+    const bool harm = c->p.face_mean == DMG_FACE_HARMONIC;
+    const bool direct = c->dim == 3 && !harm;
+    const bool dnat = direct && Dbar && is_device_ptr(Dbar), mnat = direct && mubar && is_device_ptr(mubar);
+    double *Dt = Dbar ? (dnat ? Dbar : c->T1) : nullptr, *mt = mubar ? (mnat ? mubar : c->T2) : nullptr;
+    {
+        ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
+        if (c->dim == 2)
+            dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, u, lam, l.D, ih2, harm, Dt, mt);
+        else
+            launch_grad(s, l.g, u, lam, l.D, ih2, harm, Dt, mt, dnat, mnat);
+        TRY(check_launch(c, "grad"));
+    }
+    if (Dbar && !dnat) TRY(stage_out(c, c->T1, Dbar, s));
+    if (mubar && !mnat) TRY(stage_out(c, c->T2, mubar, s));
     return DMG_OK;
 }
 
@@ -1854,24 +1895,25 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             cudaStream_t sd = c->side;
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_aux, 0));
             double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *ud = out_at(u, i);
-            if (Db || mb) {
-                const double ih2 = 1.0 / (l.h * l.h);
-                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, sd);
-                if (c->dim == 2)
-                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2,
-                                                                    c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                    Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
-                else
-                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2,
-                                                                  c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                  Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
-                TRY(check_launch(c, "grad"));
-            }
             // the staging slot of pair i-2 must have reached the host
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_out[b], 0));
+            // the tiled gradient kernel (3D, arithmetic face mean) writes the natural
+            // layout: into a device array itself, or into a host array's staging slot
+            const bool harm = c->p.face_mean == DMG_FACE_HARMONIC, direct = c->dim == 3 && !harm;
+            if (Db || mb) {
+                const double ih2 = 1.0 / (l.h * l.h);
+                double *Dt = Db ? (direct ? (is_device_ptr(Db) ? Db : mo + 2 * n) : c->T1) : nullptr;
+                double *mt = mb ? (direct ? (is_device_ptr(mb) ? mb : mo + 3 * n) : c->T2) : nullptr;
+                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, sd);
+                if (c->dim == 2)
+                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2, harm, Dt, mt);
+                else
+                    launch_grad(sd, l.g, c->U0, c->T3, l.D, ih2, harm, Dt, mt, direct, direct);
+                TRY(check_launch(c, "grad"));
+            }
             if (ud) TRY(put_on(c->U0, ud, mo, sd));
-            if (Db) TRY(put_on(c->T1, Db, mo + 2 * n, sd));
-            if (mb) TRY(put_on(c->T2, mb, mo + 3 * n, sd));
+            if (Db && !direct) TRY(put_on(c->T1, Db, mo + 2 * n, sd));
+            if (mb && !direct) TRY(put_on(c->T2, mb, mo + 3 * n, sd));
             CUDA_TRY(c, cudaEventRecord(c->ev_join, sd));   // U0, T3, T1, T2 free again
             CUDA_TRY(c, cudaEventRecord(c->ev_ready[b], sd));
             CUDA_TRY(c, cudaStreamWaitEvent(c->down, c->ev_ready[b], 0));
@@ -1906,7 +1948,7 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
                                                                c->p.face_mean == DMG_FACE_HARMONIC,
                                                                Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
             else
-                dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                launch_grad(s, l.g, c->U0, l.u, l.D, ih2,
                                                              c->p.face_mean == DMG_FACE_HARMONIC,
                                                              Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
             TRY(check_launch(c, "grad"));
@@ -2118,20 +2160,7 @@ dmg_status solve_vjp_twin(dmg_ctx *c, const double *q, const double *w, double *
     CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     if (u) TRY(stage_out(c, l.u, u, c->side, -1, c->stage2));
     CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
-    if (Dbar || mubar) {
-        const double ih2 = 1.0 / (l.h * l.h);
-        ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
-        if (c->dim == 2)
-            dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2,
-                                                           c->p.face_mean == DMG_FACE_HARMONIC,
-                                                           Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-        else
-            dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, l.u, lam, l.D, ih2, c->p.face_mean == DMG_FACE_HARMONIC,
-                                                         Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-        TRY(check_launch(c, "grad"));
-        if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
-        if (mubar) TRY(stage_out(c, c->T2, mubar, s));
-    }
+    if (Dbar || mubar) TRY(grad_out(c, l.u, lam, Dbar, mubar, s));
     CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_aux, 0));
     TRY(end_call(c, s));
@@ -2356,7 +2385,7 @@ dmg_status slot_read_impl(dmg_ctx *c, int slot, double *u, double *x, double *Db
     if (Dbar || mubar) {
         const double ih2 = 1.0 / (l.h * l.h);
         ProfScope ps(c, DMG_KERNEL_GRAD, top.lev, 0, s);
-        dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, top.U0, l.u, l.D, ih2,
+        launch_grad(s, l.g, top.U0, l.u, l.D, ih2,
                                                      c->p.face_mean == DMG_FACE_HARMONIC,
                                                      Dbar ? top.T1 : nullptr, mubar ? top.T2 : nullptr);
         TRY(check_launch(c, "grad"));
@@ -2812,21 +2841,7 @@ dmg_status dmg_solve_vjp(dmg_ctx *c, const double *q, const double *w, double *u
             TRY(stage_out(c, l.u, qbar, c->side, -1, c->stage2));
         }
         CUDA_TRY(c, cudaEventRecord(c->ev_join, c->side));
-        if (Dbar || mubar) {
-            const double ih2 = 1.0 / (l.h * l.h);
-            ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
-            if (c->dim == 2)
-                dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
-                                                               c->p.face_mean == DMG_FACE_HARMONIC,
-                                                               Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-            else
-                dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
-                                                             c->p.face_mean == DMG_FACE_HARMONIC,
-                                                             Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-            TRY(check_launch(c, "grad"));
-            if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
-            if (mubar) TRY(stage_out(c, c->T2, mubar, s));
-        }
+        if (Dbar || mubar) TRY(grad_out(c, c->U0, l.u, Dbar, mubar, s));
         CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
         TRY(end_call(c, s));
         return st != DMG_OK ? st : st2;
@@ -2880,21 +2895,7 @@ dmg_status dmg_vjp(dmg_ctx *c, const double *u, const double *w, int cycles, dou
             TRY(stage_out(c, l.u, qbar, s));
         }
         if (Dbar || mubar) {
-            double ih2 = 1.0 / (l.h * l.h);
-            {
-                ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
-                if (c->dim == 2)
-                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
-                                                                   c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                   Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-                else
-                    dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
-                                                                 c->p.face_mean == DMG_FACE_HARMONIC,
-                                                                 Dbar ? c->T1 : nullptr, mubar ? c->T2 : nullptr);
-                TRY(check_launch(c, "grad"));
-            }
-            if (Dbar) TRY(stage_out(c, c->T1, Dbar, s));
-            if (mubar) TRY(stage_out(c, c->T2, mubar, s));
+            TRY(grad_out(c, c->U0, l.u, Dbar, mubar, s));
             if (qbar) CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_join, 0));
         }
         TRY(end_call(c, s));
@@ -3003,7 +3004,7 @@ dmg_status dmg_response_vjp(dmg_ctx *c, const double *u, const double *rbar, dou
         if (Dbar || mubar) {
             TRY(stage_in(c, u, c->U0, true, s));
             const double ih2 = 1.0 / (l.h * l.h);
-            dmgk::k_grad<<<grid_all(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+            launch_grad(s, l.g, c->U0, l.u, l.D, ih2,
                                                          c->p.face_mean == DMG_FACE_HARMONIC, Dbar ? c->T1 : nullptr,
                                                          c->T2);
             TRY(check_launch(c, "grad"));

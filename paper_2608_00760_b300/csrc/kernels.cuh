@@ -1646,6 +1646,104 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, const double *__restrict__
     if (mubar) mubar[p] = -lv * uv;
 }
 
+// k_grad for the arithmetic face mean, with fewer FP64 operations. Every face
+// appears in the sums of both its vertices, and the differences that k_grad
+// forms for it on one side are the exact negations of those it forms on the
+// other (IEEE subtraction is antisymmetric); fma(-a, -b, s) = fma(a, b, s). So
+// a block of kGradTX x kGradTY x kGradTZ vertices forms the differences of each
+// vertex's +x, +y and +z faces once, shares them through shared memory, and
+// forms anew only those of the -x, -y, -z faces that cross the tile's lower
+// sides; each vertex then runs k_grad's FMA chain over its six faces in
+// k_grad's order. Bitwise k_grad's results, with about 16 FP64 operations per
+// vertex against 21 (the kernel is bound by the FP64 pipe). A thread's x
+// index runs over consecutive vertices, so an output may also be written
+// straight in the caller's natural layout (x fastest, samples consecutive:
+// dnat, mnat), without the layout copy that follows k_grad.
+constexpr int kGradTX = 16, kGradTY = 4, kGradTZ = 4;
+
+__global__ void __launch_bounds__(kGradTX * kGradTY * kGradTZ) k_grad_am(Geom g, const double *__restrict__ u,
+                                                                         const double *__restrict__ lam, int nzb,
+                                                                         double ih2, double *__restrict__ Dbar,
+                                                                         bool dnat, double *__restrict__ mubar,
+                                                                         bool mnat) {
+    __shared__ double su[kGradTZ][kGradTY][kGradTX], sl[kGradTZ][kGradTY][kGradTX];
+    __shared__ double du3[3][kGradTZ][kGradTY][kGradTX], dl3[3][kGradTZ][kGradTY][kGradTX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int smp = blockIdx.z / nzb;
+    const int i = blockIdx.x * kGradTX + tx, j = blockIdx.y * kGradTY + ty;
+    const int k = (blockIdx.z - smp * nzb) * kGradTZ + tz;
+    const bool in = i < g.nx && j < g.ny && k < g.nz;
+    const long long o = smp * g.sb;
+    u += o;
+    lam += o;
+    const long long p = in ? g.pos(i, j, k) : 0;
+    double uv = 0.0, lv = 0.0;
+    if (in) {
+        g.check(p);
+        uv = u[p];
+        lv = lam[p];
+    }
+    su[tz][ty][tx] = uv;
+    sl[tz][ty][tx] = lv;
+    __syncthreads();
+    // this vertex's +x, +y, +z faces: (lam_v - lam_n, u_v - u_n), as k_grad forms them
+    const bool up[3] = {in && i < g.nx - 1, in && j < g.ny - 1, in && k < g.nz - 1};
+    const bool last[3] = {tx == kGradTX - 1, ty == kGradTY - 1, tz == kGradTZ - 1};
+    const long long po[3] = {g.xp(i), g.sy, g.sz};
+    double dlp[3], dup[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        double un = 0.0, ln = 0.0;
+        if (up[a]) {
+            if (last[a]) {
+                g.check(p + po[a]);
+                un = u[p + po[a]];
+                ln = lam[p + po[a]];
+            } else {
+                un = a == 0 ? su[tz][ty][tx + 1] : a == 1 ? su[tz][ty + 1][tx] : su[tz + 1][ty][tx];
+                ln = a == 0 ? sl[tz][ty][tx + 1] : a == 1 ? sl[tz][ty + 1][tx] : sl[tz + 1][ty][tx];
+            }
+        }
+        dlp[a] = lv - ln;
+        dup[a] = uv - un;
+        du3[a][tz][ty][tx] = dup[a];
+        dl3[a][tz][ty][tx] = dlp[a];
+    }
+    __syncthreads();
+    if (!in) return;
+    // the -x, -y, -z faces: the lower neighbour's +face differences (negated), or
+    // formed here where that neighbour is in another tile
+    const bool dn[3] = {i > 0, j > 0, k > 0};
+    const bool first[3] = {tx == 0, ty == 0, tz == 0};
+    const long long mo[3] = {g.xm(i), -(long long)g.sy, -g.sz};
+    double dlm[3], dum[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        dlm[a] = 0.0;
+        dum[a] = 0.0;
+        if (!dn[a]) continue;
+        if (first[a]) {
+            g.check(p + mo[a]);
+            dlm[a] = lv - lam[p + mo[a]];
+            dum[a] = uv - u[p + mo[a]];
+        } else {
+            dlm[a] = a == 0 ? dl3[0][tz][ty][tx - 1] : a == 1 ? dl3[1][tz][ty - 1][tx] : dl3[2][tz - 1][ty][tx];
+            dum[a] = a == 0 ? du3[0][tz][ty][tx - 1] : a == 1 ? du3[1][tz][ty - 1][tx] : du3[2][tz - 1][ty][tx];
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (dn[a]) s = fma(dlm[a], dum[a], s);
+        if (up[a]) s = fma(dlp[a], dup[a], s);
+    }
+    s *= 0.5;
+    const long long nat = ((long long)(smp * g.nz + k) * g.ny + j) * g.nx + i;
+    DMG_CHECK(nat < (long long)g.nb * g.nz * g.ny * g.nx);
+    if (Dbar) Dbar[dnat ? nat : o + p] = -s * ih2;
+    if (mubar) mubar[mnat ? nat : o + p] = -lv * uv;
+}
+
 // f -= (dA) u on interior vertices: the derivative of the operator in the
 // direction (dD, dmu) applied to u (either tangent may be NULL).
 __global__ void __launch_bounds__(256) k_dA(Geom g, const double *__restrict__ u, const double *__restrict__ dD,
