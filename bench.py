@@ -301,7 +301,11 @@ def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
     host->device and u, qbar, Dbar, mubar device->host inside the call (two
     distinct pinned input and output sets, alternating between pairs, so every
     pair moves its own bytes), with the transfers overlapped with the
-    neighbouring pairs' solves. Single: one dmg_solve_vjp call per pair."""
+    neighbouring pairs' solves. Single: one dmg_solve_vjp call per pair.
+    Device stream: one dmg_solve_vjp_many call over device-resident inputs and
+    outputs (two sets, alternating), so that only the overlap of a pair's
+    gradient and read-out with the next pair's solves differs from the
+    headline's one call per pair."""
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     S = dmg.Solver(T(w["D"]), T(w["mu"]), w["h"], precision=precision, rtol=RTOL, inner_cycles=inner)
@@ -321,11 +325,21 @@ def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
                                stream, n=S.n)
         assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
 
+    qd, wd = [T(w["q"]), T(w["q"] * 1.5)], [T(w["w"]), T(-w["w"])]
+    outd = [[torch.empty(w["shape"], dtype=torch.float64, device=dev) for _ in range(2)] for _ in range(4)]
+
+    def many_device(k):
+        st = dmg.dmg_solve_vjp_many(S.ctx, [qd[i % 2] for i in range(k)], [wd[i % 2] for i in range(k)],
+                                    *[[o[i % 2] for i in range(k)] for o in outd], stream=stream, n=S.n)
+        assert st == dmg.DMG_OK, dmg.dmg_last_error(S.ctx)
+
     many(2)   # allocates the staging buffers, warms up
+    many_device(2)
     for _ in range(warmup):
         single()
     res = {}
-    for name, fn in (("streamed", lambda: many(steps)), ("single", lambda: [single() for _ in range(steps)])):
+    for name, fn in (("streamed", lambda: many(steps)), ("single", lambda: [single() for _ in range(steps)]),
+                     ("device", lambda: many_device(steps))):
         barrier(world)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -336,7 +350,8 @@ def run_e2e(dmg, torch, w, precision, steps, warmup, world, local, inner=1):
         res[name] = max_over_ranks(world, el)
     nbytes = 8 * int(np.prod(w["shape"]))
     S.close()
-    return dict(seconds=res["streamed"], seconds_single=res["single"], h2d=2 * nbytes, d2h=4 * nbytes)
+    return dict(seconds=res["streamed"], seconds_single=res["single"], seconds_device=res["device"],
+                h2d=2 * nbytes, d2h=4 * nbytes)
 
 
 def time_autograd_steps(dmg, torch, w, steps, warmup, world, local, inner, profile=False, w2=None):
@@ -1085,8 +1100,13 @@ def main():
                               "mubar out per pair; transfers overlapped with the neighbouring pairs' solves)" % ns,
                           single_call=dict(value=world * ns / e["seconds_single"], unit=UNIT,
                                            api="dmg_solve_vjp, one call per pair"))
+        out["stream_of_pairs_device"] = dict(
+            value=world * ns / e["seconds_device"], unit=UNIT, steps=ns,
+            api="dmg_solve_vjp_many over %d pairs, inputs and outputs resident on the device (host clock around the "
+                "call): each pair's gradient and read-out overlap the next pair's solves" % ns)
     else:
         out["e2e"] = None
+        out["stream_of_pairs_device"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         m_f = results.get("fp64", head)["fwd_cycles"]
         m_a = results.get("fp64", head)["adj_cycles"]

@@ -272,6 +272,17 @@ inline void launch_grad(cudaStream_t s, const Geom &g, const double *u, const do
     dmgk::k_grad_am<<<grid, dim3(dmgk::kGradTX, dmgk::kGradTY, dmgk::kGradTZ), 0, s>>>(g, u, lam, nzb, ih2, Dbar,
                                                                                           dnat, mubar, mnat);
 }
+
+// the same on a 2D level (k_grad2_am / k_grad2)
+inline void launch_grad2(cudaStream_t s, const Geom &g, const double *u, const double *lam, const double *D,
+                         double ih2, bool harm, double *Dbar, double *mubar, bool dnat = false, bool mnat = false) {
+    if (harm) {
+        dmgk::k_grad2<<<grid_all2(g), blk(), 0, s>>>(g, u, lam, D, ih2, 1, Dbar, mubar);
+        return;
+    }
+    const dim3 grid((g.nx + dmgk::kGrad2TX - 1) / dmgk::kGrad2TX, (g.ny + dmgk::kGrad2TY - 1) / dmgk::kGrad2TY, g.nb);
+    dmgk::k_grad2_am<<<grid, dim3(dmgk::kGrad2TX, dmgk::kGrad2TY), 0, s>>>(g, u, lam, ih2, Dbar, dnat, mubar, mnat);
+}
 // the same with a tuned block shape b (b.x threads along the half-row, b.y rows)
 inline dim3 grid_half(const Geom &g, dim3 b) {
     return dim3(((g.nx - 1) / 2 + b.x - 1) / b.x, (g.ny - 2 + b.y - 1) / b.y, g.nb * (g.nz - 2));
@@ -491,19 +502,18 @@ dmg_status stage_out(dmg_ctx *c, const double *src, double *dst, cudaStream_t s,
 
 // Dbar and mubar of <w, u> from level-0 u and lam into the caller's arrays
 // (either may be NULL): an array on the device is written directly by the
-// tiled kernel (3D, arithmetic face mean), any other through T1 / T2 and
+// tiled kernels (arithmetic face mean), any other through T1 / T2 and
 // stage_out.
 dmg_status grad_out(dmg_ctx *c, const double *u, const double *lam, double *Dbar, double *mubar, cudaStream_t s) {
     const Level &l = c->L[0];
     const double ih2 = 1.0 / (l.h * l.h);
     const bool harm = c->p.face_mean == DMG_FACE_HARMONIC;
-    const bool direct = c->dim == 3 && !harm;
-    const bool dnat = direct && Dbar && is_device_ptr(Dbar), mnat = direct && mubar && is_device_ptr(mubar);
+    const bool dnat = !harm && Dbar && is_device_ptr(Dbar), mnat = !harm && mubar && is_device_ptr(mubar);
     double *Dt = Dbar ? (dnat ? Dbar : c->T1) : nullptr, *mt = mubar ? (mnat ? mubar : c->T2) : nullptr;
     {
         ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
         if (c->dim == 2)
-            dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, u, lam, l.D, ih2, harm, Dt, mt);
+            launch_grad2(s, l.g, u, lam, l.D, ih2, harm, Dt, mt, dnat, mnat);
         else
             launch_grad(s, l.g, u, lam, l.D, ih2, harm, Dt, mt, dnat, mnat);
         TRY(check_launch(c, "grad"));
@@ -1897,16 +1907,16 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             double *Db = out_at(Dbar, i), *mb = out_at(mubar, i), *ud = out_at(u, i);
             // the staging slot of pair i-2 must have reached the host
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_out[b], 0));
-            // the tiled gradient kernel (3D, arithmetic face mean) writes the natural
+            // the tiled gradient kernels (arithmetic face mean) write the natural
             // layout: into a device array itself, or into a host array's staging slot
-            const bool harm = c->p.face_mean == DMG_FACE_HARMONIC, direct = c->dim == 3 && !harm;
+            const bool harm = c->p.face_mean == DMG_FACE_HARMONIC, direct = !harm;
             if (Db || mb) {
                 const double ih2 = 1.0 / (l.h * l.h);
                 double *Dt = Db ? (direct ? (is_device_ptr(Db) ? Db : mo + 2 * n) : c->T1) : nullptr;
                 double *mt = mb ? (direct ? (is_device_ptr(mb) ? mb : mo + 3 * n) : c->T2) : nullptr;
                 ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, sd);
                 if (c->dim == 2)
-                    dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, sd>>>(l.g, c->U0, c->T3, l.D, ih2, harm, Dt, mt);
+                    launch_grad2(sd, l.g, c->U0, c->T3, l.D, ih2, harm, Dt, mt, direct, direct);
                 else
                     launch_grad(sd, l.g, c->U0, c->T3, l.D, ih2, harm, Dt, mt, direct, direct);
                 TRY(check_launch(c, "grad"));
@@ -1944,7 +1954,7 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             const double ih2 = 1.0 / (l.h * l.h);
             ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
             if (c->dim == 2)
-                dmgk::k_grad2<<<grid_all2(l.g), blk(), 0, s>>>(l.g, c->U0, l.u, l.D, ih2,
+                launch_grad2(s, l.g, c->U0, l.u, l.D, ih2,
                                                                c->p.face_mean == DMG_FACE_HARMONIC,
                                                                Db ? c->T1 : nullptr, mb ? c->T2 : nullptr);
             else

@@ -488,6 +488,89 @@ __global__ void __launch_bounds__(256) k_grad2(Geom g, const double *__restrict_
     if (mubar) mubar[o + p] = -lv * uv;
 }
 
+// k_grad2 for the arithmetic face mean with each face's operands formed once:
+// k_grad2 multiplies (1/2)(lam_v - lam_n) by (u_v - u_n) on every face, and the
+// other vertex of the face forms their exact negations (IEEE subtraction and
+// scaling are antisymmetric; fma(-a, -b, s) = fma(a, b, s)). A block of
+// kGrad2TX x kGrad2TY vertices forms its +x and +y faces' operands once and
+// shares them through shared memory; only the -x and -y faces across the
+// tile's lower sides are formed again. Bitwise k_grad2's results with about 12
+// FP64 operations per vertex against 18. dnat, mnat: that output is written in
+// the caller's natural layout (x fastest, samples consecutive).
+constexpr int kGrad2TX = 32, kGrad2TY = 8;
+
+__global__ void __launch_bounds__(kGrad2TX * kGrad2TY) k_grad2_am(Geom g, const double *__restrict__ u,
+                                                                  const double *__restrict__ lam, double ih2,
+                                                                  double *__restrict__ Dbar, bool dnat,
+                                                                  double *__restrict__ mubar, bool mnat) {
+    __shared__ double su[kGrad2TY][kGrad2TX], sl[kGrad2TY][kGrad2TX];
+    __shared__ double hl2[2][kGrad2TY][kGrad2TX], du2[2][kGrad2TY][kGrad2TX];
+    const int tx = threadIdx.x, ty = threadIdx.y, smp = blockIdx.z;
+    const int i = blockIdx.x * kGrad2TX + tx, j = blockIdx.y * kGrad2TY + ty;
+    const bool in = i < g.nx && j < g.ny;
+    const long long o = smp * g.sb;
+    u += o;
+    lam += o;
+    const long long p = in ? g.pos(i, j, 0) : 0;
+    double uv = 0.0, lv = 0.0;
+    if (in) {
+        g.check(p);
+        uv = u[p];
+        lv = lam[p];
+    }
+    su[ty][tx] = uv;
+    sl[ty][tx] = lv;
+    __syncthreads();
+    const bool up[2] = {in && i < g.nx - 1, in && j < g.ny - 1};
+    const bool last[2] = {tx == kGrad2TX - 1, ty == kGrad2TY - 1};
+    const long long po[2] = {g.xp(i), g.sy};
+    double hlp[2], dup[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        double un = 0.0, ln = 0.0;
+        if (up[a]) {
+            if (last[a]) {
+                g.check(p + po[a]);
+                un = u[p + po[a]];
+                ln = lam[p + po[a]];
+            } else {
+                un = a == 0 ? su[ty][tx + 1] : su[ty + 1][tx];
+                ln = a == 0 ? sl[ty][tx + 1] : sl[ty + 1][tx];
+            }
+        }
+        hlp[a] = 0.5 * (lv - ln);
+        dup[a] = uv - un;
+        hl2[a][ty][tx] = hlp[a];
+        du2[a][ty][tx] = dup[a];
+    }
+    __syncthreads();
+    if (!in) return;
+    const bool dn[2] = {i > 0, j > 0};
+    const bool first[2] = {tx == 0, ty == 0};
+    const long long mo[2] = {g.xm(i), -(long long)g.sy};
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        if (dn[a]) {
+            double hm, dm;
+            if (first[a]) {
+                g.check(p + mo[a]);
+                hm = 0.5 * (lv - lam[p + mo[a]]);
+                dm = uv - u[p + mo[a]];
+            } else {
+                hm = a == 0 ? hl2[0][ty][tx - 1] : hl2[1][ty - 1][tx];
+                dm = a == 0 ? du2[0][ty][tx - 1] : du2[1][ty - 1][tx];
+            }
+            s = fma(hm, dm, s);
+        }
+        if (up[a]) s = fma(hlp[a], dup[a], s);
+    }
+    const long long nat = ((long long)smp * g.ny + j) * g.nx + i;
+    DMG_CHECK(nat < (long long)g.nb * g.ny * g.nx);
+    if (Dbar) Dbar[dnat ? nat : o + p] = -s * ih2;
+    if (mubar) mubar[mnat ? nat : o + p] = -lv * uv;
+}
+
 // f -= (dA) u on interior vertices for a coefficient direction (dD, dmu)
 __global__ void __launch_bounds__(256) k_dA2(Geom g, const double *__restrict__ u, const double *__restrict__ dD,
                                              const double *__restrict__ dmu, const double *__restrict__ D, double ih2,
