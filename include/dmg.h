@@ -452,6 +452,13 @@ dmg_status dmg_slot_read(dmg_ctx *ctx, int slot, double *u, double *x, double *D
    DMG_ENOMEM and releases what it had allocated); n <= 0 turns it off. */
 void dmg_debug_fail_alloc(long long n);
 
+/* Testing hook, no counterpart in the paper: on = 1 makes every context of the
+   process form D-bar and mu-bar with the per-vertex gradient kernel, which
+   forms the differences of every face on both of its sides, instead of the
+   tiled kernel that forms them once (arithmetic face mean); the two give the
+   same bits. 0 (the default) turns it off. */
+void dmg_debug_grad_per_vertex(int on);
+
 /* Testing hook, no counterpart in the paper. Bounds-checked builds (compiled
    with -DDMG_BOUNDS_CHECK, the library's stand-in for a memory checker): the
    number of device accesses counted outside their arrays so far (every call

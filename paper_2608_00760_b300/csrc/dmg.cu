@@ -256,14 +256,21 @@ inline dim3 grid_half2(const Geom &g) { return dim3(((g.nx - 1) / 2 + 31) / 32, 
 inline dim3 grid_int2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny - 2 + 7) / 8, g.nb); }
 inline dim3 grid_all2(const Geom &g) { return dim3(2 * ((g.nhalf() + 31) / 32), (g.ny + 7) / 8, g.nb); }
 
+// dmg_debug_grad_per_vertex: the per-vertex gradient kernels for both face means
+std::atomic<int> g_grad_per_vertex{0};
+
 // Dbar and mubar of <w, u> from u and lam on a 3D level, in the level's
 // layout: the tiled kernel for the arithmetic face mean (bitwise k_grad, fewer
 // FP64 operations), k_grad for the harmonic one. dnat / mnat: that output is
-// written in the natural layout (tiled kernel only).
+// written in the natural layout (tiled kernel only: callers ask for it where
+// grad_tiled() held, and the tiled kernel then runs whatever the hook says by
+// now).
+inline bool grad_tiled(bool harm) { return !harm && !g_grad_per_vertex.load(); }
+
 inline void launch_grad(cudaStream_t s, const Geom &g, const double *u, const double *lam, const double *D,
                         double ih2, bool harm, double *Dbar, double *mubar, bool dnat = false, bool mnat = false) {
-    if (harm) {
-        dmgk::k_grad<<<grid_all(g), blk(), 0, s>>>(g, u, lam, D, ih2, 1, Dbar, mubar);
+    if (!dnat && !mnat && !grad_tiled(harm)) {
+        dmgk::k_grad<<<grid_all(g), blk(), 0, s>>>(g, u, lam, D, ih2, harm, Dbar, mubar);
         return;
     }
     const int nzb = (g.nz + dmgk::kGradTZ - 1) / dmgk::kGradTZ;
@@ -276,8 +283,8 @@ inline void launch_grad(cudaStream_t s, const Geom &g, const double *u, const do
 // the same on a 2D level (k_grad2_am / k_grad2)
 inline void launch_grad2(cudaStream_t s, const Geom &g, const double *u, const double *lam, const double *D,
                          double ih2, bool harm, double *Dbar, double *mubar, bool dnat = false, bool mnat = false) {
-    if (harm) {
-        dmgk::k_grad2<<<grid_all2(g), blk(), 0, s>>>(g, u, lam, D, ih2, 1, Dbar, mubar);
+    if (!dnat && !mnat && !grad_tiled(harm)) {
+        dmgk::k_grad2<<<grid_all2(g), blk(), 0, s>>>(g, u, lam, D, ih2, harm, Dbar, mubar);
         return;
     }
     const dim3 grid((g.nx + dmgk::kGrad2TX - 1) / dmgk::kGrad2TX, (g.ny + dmgk::kGrad2TY - 1) / dmgk::kGrad2TY, g.nb);
@@ -508,7 +515,8 @@ dmg_status grad_out(dmg_ctx *c, const double *u, const double *lam, double *Dbar
     const Level &l = c->L[0];
     const double ih2 = 1.0 / (l.h * l.h);
     const bool harm = c->p.face_mean == DMG_FACE_HARMONIC;
-    const bool dnat = !harm && Dbar && is_device_ptr(Dbar), mnat = !harm && mubar && is_device_ptr(mubar);
+    const bool tiled = grad_tiled(harm);
+    const bool dnat = tiled && Dbar && is_device_ptr(Dbar), mnat = tiled && mubar && is_device_ptr(mubar);
     double *Dt = Dbar ? (dnat ? Dbar : c->T1) : nullptr, *mt = mubar ? (mnat ? mubar : c->T2) : nullptr;
     {
         ProfScope ps(c, DMG_KERNEL_GRAD, 0, 0, s);
@@ -1909,7 +1917,7 @@ dmg_status solve_vjp_many_impl(dmg_ctx *c, int npairs, const double *const *q, c
             CUDA_TRY(c, cudaStreamWaitEvent(sd, c->ev_out[b], 0));
             // the tiled gradient kernels (arithmetic face mean) write the natural
             // layout: into a device array itself, or into a host array's staging slot
-            const bool harm = c->p.face_mean == DMG_FACE_HARMONIC, direct = !harm;
+            const bool harm = c->p.face_mean == DMG_FACE_HARMONIC, direct = grad_tiled(harm);
             if (Db || mb) {
                 const double ih2 = 1.0 / (l.h * l.h);
                 double *Dt = Db ? (direct ? (is_device_ptr(Db) ? Db : mo + 2 * n) : c->T1) : nullptr;
@@ -3149,6 +3157,8 @@ dmg_status dmg_slot_read(dmg_ctx *c, int slot, double *u, double *x, double *Dba
 size_t dmg_device_bytes(const dmg_ctx *c) { return c ? c->dev_bytes + (c->twin ? c->twin->dev_bytes : 0) : 0; }
 
 void dmg_debug_fail_alloc(long long n) { g_fail_alloc_at.store(n > 0 ? n : 0); }
+
+void dmg_debug_grad_per_vertex(int on) { g_grad_per_vertex.store(on ? 1 : 0); }
 
 long long dmg_debug_oob_count(void) {
 #ifdef DMG_BOUNDS_CHECK

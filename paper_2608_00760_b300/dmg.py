@@ -66,6 +66,7 @@ EXPORTS = ("dmg_default_params", "dmg_setup", "dmg_solve", "dmg_jvp", "dmg_vjp",
            "dmg_batch_info", "dmg_slot_load", "dmg_slot_begin", "dmg_step_launch", "dmg_step_finish",
            "dmg_slot_result", "dmg_slot_read", "dmg_device_bytes", "dmg_response", "dmg_response_jvp",
            "dmg_response_vjp", "dmg_vjp_unrolled", "dmg_tile", "dmg_debug_fail_alloc", "dmg_solve_vjp",
+           "dmg_debug_grad_per_vertex",
            "dmg_debug_oob_count", "dmg_set_coefficients", "dmg_probe_fma", "dmg_solve_vjp_many",
            "dmg_setup_pyramid")
 
@@ -117,6 +118,7 @@ def lib():
             "dmg_tile": (i, [vp, i, i, P(i), P(i)]),
             "dmg_solve_vjp": (i, [vp, vp, vp, vp, vp, vp, vp, P(dmg_info), P(dmg_info), vp]),
             "dmg_debug_fail_alloc": (None, [ctypes.c_longlong]),
+            "dmg_debug_grad_per_vertex": (None, [ctypes.c_int]),
             "dmg_debug_oob_count": (ctypes.c_longlong, []),
             "dmg_response_jvp": (i, [vp, vp, vp, vp, vp, d, vp, P(dmg_info), vp]),
             "dmg_response_vjp": (i, [vp, vp, vp, d, vp, vp, vp, P(dmg_info), vp]),
@@ -362,6 +364,11 @@ def dmg_level_shape(ctx, level):
 def dmg_debug_fail_alloc(n):
     """Testing hook: the n-th device allocation from now on fails with DMG_ENOMEM (n <= 0: off)."""
     lib().dmg_debug_fail_alloc(int(n))
+
+
+def dmg_debug_grad_per_vertex(on):
+    """Testing hook: 1 forms D-bar and mu-bar with the per-vertex gradient kernels (0: the tiled ones)."""
+    lib().dmg_debug_grad_per_vertex(1 if on else 0)
 
 
 def dmg_debug_oob_count():
