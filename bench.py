@@ -45,7 +45,7 @@ UNIT = "fwd+VJP solves/s"
 N_SIDE = 257
 RTOL = 1e-10
 # Roofline unit: one RB-GS half-sweep launch on the finest level (one colour).
-# Algorithmic bytes (the survey's unit): a full FP32 red-black sweep must read
+# Algorithmic bytes: a full FP32 red-black sweep must read
 # u, f, D and mu once and write u once, 20 B per interior vertex, so one
 # half-sweep is charged 10 B per interior vertex of the grid. The kernel as
 # built moves 12 B per vertex per half-sweep (f and mu of its own colour,
