@@ -2106,6 +2106,17 @@ dmg_status twin_ready(dmg_ctx *c, cudaStream_t s) {
             cudaEventCreateWithFlags(&c->ev_lead, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             st = fail(c, DMG_ECUDA, "twin context: stream or event creation failed");
+            // a later call starts again from none of them
+            for (cudaStream_t *x : {&c->twin_s, &c->lead_s})
+                if (*x) {
+                    cudaStreamDestroy(*x);
+                    *x = nullptr;
+                }
+            for (cudaEvent_t *x : {&c->ev_twin, &c->ev_lead})
+                if (*x) {
+                    cudaEventDestroy(*x);
+                    *x = nullptr;
+                }
         }
     }
     cudaStreamSynchronize(s);
